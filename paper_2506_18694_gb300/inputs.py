@@ -1,0 +1,91 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+This module holds no arithmetic of the solver: it only draws random numbers and
+samples the analytic source f(x) = a exp(-|x - x0|^2 / (2 sigma^2)) at the grid
+nodes (x fastest).  Turning f into a load vector b = M f is the solver's job
+(``rhs_kind = nodal`` in the C-ABI) and the oracle's job, each on its own.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+SOMMERFELD = 0
+DIRICHLET = 1
+
+
+@dataclass(frozen=True)
+class Workload:
+    """One configuration of the solver: grid, wavenumber, shifts, boundary tags, source."""
+
+    name: str
+    dim: int
+    n: int
+    k: float
+    delta: float
+    delta_hat: float
+    bc: tuple
+    centre: tuple
+    sigma: float = 0.05
+    amplitude: complex = 1.0 + 0.0j
+    tol: float = 1e-8
+
+    @property
+    def nodes(self) -> int:
+        return (self.n + 1) ** self.dim
+
+
+def _uniform_centre(seed, dim):
+    rng = np.random.default_rng(seed)
+    return tuple(float(v) for v in rng.uniform(0.0, 1.0, size=dim))
+
+
+def workload(name: str, delta_hat: str | float = "k") -> Workload:
+    """The named configurations (2D 32^2 k=10, 2D 512^2 k=80, 3D 128^3 k=40).
+
+    ``delta_hat`` is ``"k"`` (the shift equal to the wavenumber) or a number
+    (2.0 is the value used throughout the paper's experiments, Sec. 5.1).
+    """
+    if name == "2d_n32_k10":
+        dim, n, k, bc, c = 2, 32, 10.0, (SOMMERFELD,) * 4, (0.5, 0.5)
+    elif name == "2d_n512_k80":
+        dim, n, k, bc, c = 2, 512, 80.0, (SOMMERFELD,) * 4, _uniform_centre(2, 2)
+    elif name == "3d_n128_k40":
+        dim, n, k = 3, 128, 40.0
+        bc = (SOMMERFELD,) * 4 + (DIRICHLET, SOMMERFELD)
+        c = (0.5, 0.5, 0.5)
+    else:
+        raise KeyError(name)
+    dh = k if delta_hat == "k" else float(delta_hat)
+    return Workload(name, dim, n, k, 0.0, dh, bc, c)
+
+
+def node_coords(dim: int, n: int) -> np.ndarray:
+    """(N, dim) float64 coordinates of the nodes of the uniform grid, x fastest."""
+    t = np.arange(n + 1) / n
+    grids = np.meshgrid(*([t] * dim)[::-1], indexing="ij")[::-1]
+    return np.stack([g.ravel() for g in grids], axis=1)
+
+
+def gaussian_source(dim: int, n: int, centre, sigma: float = 0.05,
+                    amplitude: complex = 1.0) -> np.ndarray:
+    """Nodal values of a exp(-|x - x0|^2 / (2 sigma^2)) as complex128, x fastest."""
+    x = node_coords(dim, n)
+    r2 = ((x - np.asarray(centre)[None, :]) ** 2).sum(axis=1)
+    return (amplitude * np.exp(-r2 / (2.0 * sigma * sigma))).astype(np.complex128)
+
+
+def random_complex(N: int, seed: int) -> np.ndarray:
+    """Standard complex normal entries (real and imaginary parts N(0,1)), complex128."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(N) + 1j * rng.standard_normal(N)
+
+
+def batch_sources(count: int = 64, n: int = 256, seed: int = 4):
+    """Batched 2D problems: k drawn from {20, 40, 80}, uniform centres, amplitudes g1 + i g2 with g ~ N(0,1)."""
+    rng = np.random.default_rng(seed)
+    ks = rng.choice(np.array([20.0, 40.0, 80.0]), size=count)
+    centres = rng.uniform(0.0, 1.0, size=(count, 2))
+    amps = rng.standard_normal(count) + 1j * rng.standard_normal(count)
+    return [(float(ks[i]), tuple(centres[i]), complex(amps[i])) for i in range(count)]
