@@ -1,0 +1,196 @@
+/*
+ * hh.h - C ABI of the GB300 shifted-HSS Helmholtz solver.
+ *
+ * The library solves the Q1 finite-element discretisation of the indefinite
+ * Helmholtz problem of Cotter, Hope-Collins & Knook (arXiv 2506.18694, Sec. 1,
+ * Eq. "helmholtz strong primal"):
+ *
+ *     (-delta + i k)^2 u - lap u = f   in the unit square (dim 2) or cube (dim 3),
+ *     u = 0 on the Dirichlet sides, du/dn - (-delta + i k) u = 0 on the Sommerfeld sides,
+ *
+ * in its primal weak form b_delta (Sec. 2) on a uniform grid of n cells per axis.
+ * The discrete operator is B_delta = K + (-delta + i k)^2 M + (delta - i k) M_Gamma with
+ * K the stiffness, M the mass and M_Gamma the boundary mass on Sommerfeld sides.
+ *
+ * Method: flexible GMRES in FP64 (Sec. 5.1) on B_delta u = b, right-preconditioned by
+ * the shifted-HSS operator of Def. 4.1: ceil(k^theta) iterations of
+ *     A_L u_{n+1} = (k-1)/(k+1) A_R u_n + 2k/(k+1) r,   u_0 = 0,
+ *     A_L = K + (dh^2 - k^2 - 2 i dh k^2) M + (dh - i k^2) M_Gamma,
+ *     A_R = -K + (k^2 - dh^2 - 2 i dh k^2) M + (-dh - i k^2) M_Gamma     (dh = delta_hat),
+ * each A_L solve approximated by one multigrid V-cycle (scaled Jacobi smoothing,
+ * full-weighting restriction R = P^T, bi/trilinear prolongation P) in complex FP32
+ * or complex FP64.
+ *
+ * Data layout (every vector argument): (n_l + 1)^dim complex nodal values of level l
+ * (level 0 is the finest, n_l = n / 2^l), lexicographic with x fastest, real and
+ * imaginary parts interleaved: double2 for HH_C128, float2 for HH_C64.  Device
+ * pointers must be 16-byte (c128) or 8-byte (c64) aligned.  Entries at Dirichlet
+ * nodes of inputs are ignored; outputs hold exact zeros there.
+ *
+ * Ownership: the caller owns every vector it passes; the library owns everything it
+ * allocates for a problem (grid hierarchy, Krylov basis, CUDA graphs, streams) and
+ * frees it in hh_destroy.  A problem is not thread-safe; distinct problems are
+ * independent.  All calls are made on the device that was current at
+ * hh_create_problem.
+ *
+ * Errors: every call returns an hh_status; no exception crosses the ABI and no
+ * device code traps.  hh_last_error() returns a message for the last failing call
+ * of the calling thread.
+ */
+#ifndef HH_H
+#define HH_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define HH_API __attribute__((visibility("default")))
+#else
+#define HH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HH_OK = 0,
+    HH_NOT_CONVERGED = 1,   /* max_outer reached; u holds the last iterate           */
+    HH_ERR_INVALID = -1,    /* bad argument (see each call)                           */
+    HH_ERR_OOM = -2,        /* device allocation failed                               */
+    HH_ERR_CUDA = -3,       /* a CUDA runtime call failed                             */
+    HH_ERR_NONFINITE = -4,  /* NaN or Inf met in the right side or the iteration      */
+    HH_ERR_TIMEOUT = -5     /* reserved for bounded device waits                      */
+} hh_status;
+
+/* Boundary tags of Sec. 1: Gamma (radiation condition) and dOmega_0 (u = 0). */
+typedef enum { HH_BC_SOMMERFELD = 0, HH_BC_DIRICHLET = 1 } hh_bc;
+
+/* Arithmetic of the multigrid V-cycles (the outer FGMRES is always FP64). */
+typedef enum { HH_C128 = 0, HH_C64 = 1 } hh_precision;
+
+/* Operators that hh_apply can apply (coefficient triples of the weak forms). */
+typedef enum {
+    HH_OP_K = 0,        /* stiffness                                     (Sec. 2) */
+    HH_OP_M = 1,        /* mass                                          (Sec. 2) */
+    HH_OP_MGAMMA = 2,   /* boundary mass on Sommerfeld sides             (Sec. 2) */
+    HH_OP_AL = 3,       /* left HSS operator of Def. 4.1 (delta_hat)              */
+    HH_OP_AR = 4,       /* right HSS operator of Def. 4.1 (delta_hat)             */
+    HH_OP_B = 5,        /* B_delta of the outer problem                  (Sec. 2) */
+    HH_OP_BHAT = 6      /* B_delta_hat, the shifted operator of Sec. 4            */
+} hh_operator;
+
+/* Uniform grid of the unit square/cube: dim in {2,3}, n cells per axis. */
+typedef struct {
+    int dim;
+    int n;
+} hh_grid;
+
+typedef struct {
+    double theta;        /* ceil(k^theta) inner HSS iterations per preconditioning (Def. 4.1) */
+    int levels;          /* multigrid levels, coarsening factor 2 (Sec. 5.3 uses 4)           */
+    int nu_pre;          /* Jacobi sweeps before restriction                                  */
+    int nu_post;         /* Jacobi sweeps after prolongation                                  */
+    int nu_coarse;       /* Jacobi sweeps on the coarsest level                               */
+    int cycles_per_hss;  /* V-cycles per HSS iteration                                        */
+    double omega;        /* Jacobi damping                                                    */
+    int restart;         /* FGMRES restart length                                             */
+    int max_outer;       /* FGMRES iteration cap                                              */
+    int precision;       /* hh_precision of the V-cycles                                      */
+    int use_graphs;      /* 1: replay each preconditioner application from a CUDA graph       */
+} hh_options;
+
+typedef struct {
+    int outer_its;          /* FGMRES iterations                                 */
+    long long hss_its;      /* inner HSS iterations                              */
+    long long vcycles;      /* V-cycles on the finest level                      */
+    double rel_residual;    /* ||b - B_delta u||_2 / ||b||_2 recomputed in FP64   */
+    double seconds;         /* wall time of the call                             */
+    size_t device_bytes;    /* device memory held by the problem                 */
+    long long kernel_launches; /* kernels this call ran (graph replays counted per node) */
+} hh_info;
+
+typedef struct hh_problem hh_problem;
+
+/* Defaults: theta 1, 4 levels, V(2,2), 8 coarse sweeps, omega 0.6, restart 30,
+ * max_outer 1000, complex FP32 V-cycles, graphs on. */
+HH_API void hh_options_default(hh_options* opts);
+
+/* Device bytes a problem with this grid and these options allocates (0 if invalid). */
+HH_API size_t hh_footprint_bytes(const hh_grid* grid, const hh_options* opts);
+
+/*
+ * Build a problem: validate, compute the operator coefficients of every level and
+ * allocate the device hierarchy and the Krylov basis.
+ *   k > 0, delta >= 0, delta_hat > 0 (H = 2 delta_hat k M + k M_Gamma must be an inner
+ *   product, Sec. 3.1); grid->dim in {2,3}; grid->n >= 2 and divisible by 2^(levels-1);
+ *   bc[2*axis + side] in {HH_BC_SOMMERFELD, HH_BC_DIRICHLET} for -x,+x,-y,+y(,-z,+z).
+ *   cuda_stream: the caller's stream (NULL = legacy default stream); the library
+ *   orders all of its work after the work already queued there and makes that stream
+ *   wait for it.
+ * Returns HH_ERR_INVALID, HH_ERR_OOM or HH_ERR_CUDA on failure (*out is then NULL).
+ */
+HH_API hh_status hh_create_problem(const hh_grid* grid, double k, double delta, double delta_hat,
+                            const int* bc, const hh_options* opts, void* cuda_stream,
+                            hh_problem** out);
+
+HH_API void hh_destroy(hh_problem* p);
+
+/*
+ * Solve B_delta u = rhs to ||rhs - B_delta u||_2 <= tol ||rhs||_2 (true residual,
+ * recomputed in FP64 at the end of every restart cycle).  rhs (load vector), u and the
+ * optional initial guess x0 are device complex128 vectors of level 0.  Blocking: returns
+ * when u is written.  On HH_NOT_CONVERGED u holds the last iterate and info is filled;
+ * on errors u is unspecified and info->rel_residual is NaN.  info may be NULL.
+ */
+HH_API hh_status hh_solve(hh_problem* p, const void* rhs, double tol, void* u, const void* x0,
+                   hh_info* info);
+
+/* As hh_solve, but rhs and u are HOST complex128 arrays; the copies are part of the call. */
+HH_API hh_status hh_solve_host(hh_problem* p, const void* rhs_host, double tol, void* u_host,
+                        hh_info* info);
+
+/* Nodes (n_l + 1)^dim of level l, or 0 if l is out of range. */
+HH_API long long hh_level_nodes(const hh_problem* p, int level);
+
+/* ---- building blocks (same kernels the solver runs; launched on the problem's stream,
+ *      ordered after the caller's stream; non-blocking unless stated) ---- */
+
+/* y = op x on level `level` (Sec. 2 / Def. 4.1 coefficient triples). */
+HH_API hh_status hh_apply(hh_problem* p, int level, int op, int precision, const void* x, void* y);
+
+/* One scaled-Jacobi sweep on A_L of level l: x_out = x_in + omega D^{-1} (b - A_L x_in),
+ * D = diag(A_L).  x_in == NULL means x_in = 0.  x_out must not alias x_in or b. */
+HH_API hh_status hh_jacobi(hh_problem* p, int level, int precision, const void* b, const void* x_in,
+                    void* x_out);
+
+/* rc = P^T (b - A_L x): residual on level l restricted to level l+1. */
+HH_API hh_status hh_residual_restrict(hh_problem* p, int level, int precision, const void* b,
+                               const void* x, void* rc);
+
+/* x += P ec: prolongation of a level-(l+1) correction onto level l. */
+HH_API hh_status hh_prolong_correct(hh_problem* p, int level, int precision, const void* ec, void* x);
+
+/* x = one V-cycle on A_L of level 0 from the zero initial guess (cycles_per_hss ignored). */
+HH_API hh_status hh_vcycle(hh_problem* p, int precision, const void* b, void* x);
+
+/* rhs = (k-1)/(k+1) A_R u + 2k/(k+1) r on level 0 (Def. 4.1); u == NULL means u = 0. */
+HH_API hh_status hh_hss_rhs(hh_problem* p, int precision, const void* u, const void* r, void* rhs);
+
+/* z = shifted-HSS preconditioner applied to r (Def. 4.1), r and z complex128 on level 0;
+ * the inner V-cycles run in the problem's precision.  Blocking. */
+HH_API hh_status hh_precondition(hh_problem* p, const void* r, void* z);
+
+/* b = M f (load vector of a nodal f, Sec. 2), complex128 on level 0. */
+HH_API hh_status hh_load_vector(hh_problem* p, const void* f, void* b);
+
+/* out[0] + i out[1] = x^H y over level-0 complex128 vectors (deterministic order).  Blocking. */
+HH_API hh_status hh_dot(hh_problem* p, const void* x, const void* y, double* out);
+
+HH_API const char* hh_status_string(hh_status s);
+HH_API const char* hh_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HH_H */

@@ -1,0 +1,144 @@
+// FP64 complex vector kernels of the outer flexible GMRES (Sec. 5.1): block-partial
+// inner products with a fixed reduction tree (bitwise reproducible), fused
+// multi-vector updates for classical Gram-Schmidt, scaling by a device-held norm.
+#include "internal.h"
+
+namespace hh {
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+// Block reduction of a double2 (warp shuffles, then one warp over the warp sums).
+__device__ __forceinline__ double2 block_sum(double2 v) {
+    __shared__ double2 warp_sums[32];
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(full, v.x, o);
+        v.y += __shfl_down_sync(full, v.y, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_sums[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? warp_sums[lane] : make_double2(0.0, 0.0);
+    if (wid == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v.x += __shfl_down_sync(full, v.x, o);
+            v.y += __shfl_down_sync(full, v.y, o);
+        }
+    }
+    return v;  // valid in thread 0
+}
+
+// partials[i * gridDim.x + blockIdx.x] = sum over this block's slice of conj(V_i) w.
+// grid = (kRedBlocks, nvec); block slices are fixed so the sum order never changes.
+__global__ void __launch_bounds__(kRedThreads) k_multidot_partial(const double2* __restrict__ V,
+                                                                  long long ld,
+                                                                  const double2* __restrict__ w,
+                                                                  long long N,
+                                                                  double2* __restrict__ partials) {
+    const int vi = blockIdx.y;
+    const double2* __restrict__ v = V + (long long)vi * ld;
+    double2 acc = make_double2(0.0, 0.0);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += stride) {
+        const double2 a = v[p], b = w[p];
+        acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+        acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[(long long)vi * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_multidot_final(const double2* __restrict__ partials,
+                                                                int nblk, double2* __restrict__ out) {
+    const int vi = blockIdx.x;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc = cadd(acc, partials[(long long)vi * nblk + b]);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) out[vi] = acc;
+}
+
+cudaError_t launch_multidot(const double2* V, long long ld, int nvec, const double2* w, long long N,
+                            double2* partials, double2* out, cudaStream_t s) {
+    if (nvec <= 0) return cudaSuccess;
+    dim3 g1(kRedBlocks, nvec);
+    k_multidot_partial<<<g1, kRedThreads, 0, s>>>(V, ld, w, N, partials);
+    k_multidot_final<<<nvec, kRedThreads, 0, s>>>(partials, kRedBlocks, out);
+    g_kernel_launches += 2;
+    return cudaGetLastError();
+}
+
+// w += sign * sum_i coef[i] V_i   (coefficients read from device memory)
+__global__ void __launch_bounds__(256) k_multi_axpy(double2* __restrict__ w, const double2* __restrict__ V,
+                                                    long long ld, int nvec,
+                                                    const double2* __restrict__ coef, double sign,
+                                                    long long N) {
+    __shared__ double2 c[64];
+    for (int t = threadIdx.x; t < nvec && t < 64; t += blockDim.x) {
+        double2 v = coef[t];
+        c[t] = make_double2(sign * v.x, sign * v.y);
+    }
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += stride) {
+        double2 acc = w[p];
+        for (int i = 0; i < nvec; ++i) {
+            const double2 a = V[(long long)i * ld + p];
+            const double2 k = c[i];
+            acc.x = fma(k.x, a.x, fma(-k.y, a.y, acc.x));
+            acc.y = fma(k.x, a.y, fma(k.y, a.x, acc.y));
+        }
+        w[p] = acc;
+    }
+}
+
+static inline unsigned ew_blocks(long long N) {
+    long long b = (N + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+cudaError_t launch_multi_axpy(double2* w, const double2* V, long long ld, int nvec,
+                              const double2* coef, double sign, long long N, cudaStream_t s) {
+    if (nvec <= 0) return cudaSuccess;
+    if (nvec > 64) return cudaErrorInvalidValue;
+    ++g_kernel_launches;
+    k_multi_axpy<<<ew_blocks(N), 256, 0, s>>>(w, V, ld, nvec, coef, sign, N);
+    return cudaGetLastError();
+}
+
+__global__ void k_scale_by_rnorm(double2* __restrict__ x, const double2* __restrict__ nrm2, long long N) {
+    const double n2 = nrm2->x;
+    if (!(n2 > 0.0)) return;
+    const double s = 1.0 / sqrt(n2);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += stride) {
+        double2 v = x[p];
+        x[p] = make_double2(v.x * s, v.y * s);
+    }
+}
+
+cudaError_t launch_scale_by_rnorm(double2* x, const double2* nrm2, long long N, cudaStream_t s) {
+    ++g_kernel_launches;
+    k_scale_by_rnorm<<<ew_blocks(N), 256, 0, s>>>(x, nrm2, N);
+    return cudaGetLastError();
+}
+
+__global__ void k_scale(double2* __restrict__ x, double sc, long long N) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += stride) {
+        double2 v = x[p];
+        x[p] = make_double2(v.x * sc, v.y * sc);
+    }
+}
+
+cudaError_t launch_scale(double2* x, double sc, long long N, cudaStream_t st) {
+    ++g_kernel_launches;
+    k_scale<<<ew_blocks(N), 256, 0, st>>>(x, sc, N);
+    return cudaGetLastError();
+}
+
+}  // namespace hh

@@ -1,0 +1,65 @@
+"""Host-side checks of the C ABI: the library loads, exports every declared symbol and
+validates arguments before touching a device (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2506_18694_gb300 import hh
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hh.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"HH_API[^;]*?\b(hh_\w+)\s*\(", text, flags=re.S)))
+
+
+def test_header_and_binding_agree():
+    assert declared_symbols() == sorted(hh.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(libhh):
+    for name in declared_symbols():
+        assert hasattr(libhh, name), name
+
+
+def test_options_default(libhh):
+    o = hh.default_options()
+    assert (o.theta, o.levels, o.nu_pre, o.nu_post, o.nu_coarse) == (1.0, 4, 2, 2, 8)
+    assert o.cycles_per_hss == 1 and abs(o.omega - 0.6) < 1e-15
+    assert o.restart == 30 and o.precision == hh.HH_C64 and o.use_graphs == 1
+
+
+def test_footprint_bytes(libhh):
+    o = hh.default_options()
+    b2 = hh.footprint_bytes(2, 512, o)
+    # Krylov basis alone: 61 complex128 vectors of 513^2 nodes
+    assert b2 > 61 * 513 * 513 * 16
+    assert hh.footprint_bytes(2, 1024, o) > 3.9 * b2
+    assert hh.footprint_bytes(2, 100, o) == 0  # 100 is not divisible by 2^3
+    assert hh.footprint_bytes(4, 64, o) == 0
+
+
+@pytest.mark.parametrize("dim,n,k,delta,dh,bc", [
+    (4, 16, 10.0, 0.0, 2.0, [0] * 6),      # bad dimension
+    (2, 12, 10.0, 0.0, 2.0, [0] * 4),      # 12 not divisible by 8
+    (2, 16, -1.0, 0.0, 2.0, [0] * 4),      # k <= 0
+    (2, 16, 10.0, -0.1, 2.0, [0] * 4),     # delta < 0
+    (2, 16, 10.0, 0.0, 0.0, [0] * 4),      # delta_hat <= 0: H is not an inner product
+    (2, 16, 10.0, 0.0, 2.0, [0, 2, 0, 0]),  # bad tag
+])
+def test_invalid_arguments_rejected_on_host(libhh, dim, n, k, delta, dh, bc):
+    o = hh.default_options()
+    arr = (ctypes.c_int * 6)(*(bc + [0] * (6 - len(bc))))
+    out = ctypes.c_void_p(1234)
+    st = libhh.hh_create_problem(ctypes.byref(hh.Grid(dim, n)), k, delta, dh, arr, ctypes.byref(o), None,
+                                 ctypes.byref(out))
+    assert st == -1 and not out.value
+    assert libhh.hh_last_error()
+
+
+def test_status_strings(libhh):
+    for s in (0, 1, -1, -2, -3, -4, -5):
+        assert libhh.hh_status_string(s)
