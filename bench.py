@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--delta-hat", default="k")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 / roofline / CPU legs")
+    ap.add_argument("--max-outer", type=int, default=0,
+                    help="cap FGMRES iterations (profiling runs only; 0 = solve to tolerance)")
     return ap.parse_args()
 
 
@@ -202,6 +204,8 @@ def main():
     dev = torch.cuda.current_device()
     w = inputs.workload(WORKLOAD, args.delta_hat)
     opts = hh.default_options(precision=hh.HH_C64)
+    if args.max_outer > 0:
+        opts.max_outer = args.max_outer
     prob = hh.Problem(w.dim, w.n, w.k, w.delta, w.delta_hat, w.bc, opts)
     N = prob.nodes()
     f = torch.from_numpy(inputs.gaussian_source(w.dim, w.n, w.centre, w.sigma)).cuda()

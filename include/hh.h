@@ -97,6 +97,9 @@ typedef struct {
     int max_outer;       /* FGMRES iteration cap                                              */
     int precision;       /* hh_precision of the V-cycles                                      */
     int use_graphs;      /* 1: replay each preconditioner application from a CUDA graph       */
+    int use_pdl;         /* 1: programmatic dependent launch between consecutive kernels      */
+    int coarse_cluster_nodes; /* levels (below the finest) with at most this many nodes run  */
+                              /* together inside one thread-block cluster; 0 = never         */
 } hh_options;
 
 typedef struct {
@@ -112,7 +115,8 @@ typedef struct {
 typedef struct hh_problem hh_problem;
 
 /* Defaults: theta 1, 4 levels, V(2,2), 8 coarse sweeps, omega 0.6, restart 30,
- * max_outer 1000, complex FP32 V-cycles, graphs on. */
+ * max_outer 1000, complex FP32 V-cycles, graphs and programmatic launch on, cluster
+ * levels of at most 20000 nodes. */
 HH_API void hh_options_default(hh_options* opts);
 
 /* Device bytes a problem with this grid and these options allocates (0 if invalid). */

@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot_partial(const double2*
                                                                   const double2* __restrict__ w,
                                                                   long long N,
                                                                   double2* __restrict__ partials) {
+    pdl_entry();
     const int vi = blockIdx.y;
     const double2* __restrict__ v = V + (long long)vi * ld;
     double2 acc = make_double2(0.0, 0.0);
@@ -53,6 +54,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot_partial(const double2*
 
 __global__ void __launch_bounds__(kRedThreads) k_multidot_final(const double2* __restrict__ partials,
                                                                 int nblk, double2* __restrict__ out) {
+    pdl_entry();
     const int vi = blockIdx.x;
     double2 acc = make_double2(0.0, 0.0);
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc = cadd(acc, partials[(long long)vi * nblk + b]);
@@ -64,10 +66,9 @@ cudaError_t launch_multidot(const double2* V, long long ld, int nvec, const doub
                             double2* partials, double2* out, cudaStream_t s) {
     if (nvec <= 0) return cudaSuccess;
     dim3 g1(kRedBlocks, nvec);
-    k_multidot_partial<<<g1, kRedThreads, 0, s>>>(V, ld, w, N, partials);
-    k_multidot_final<<<nvec, kRedThreads, 0, s>>>(partials, kRedBlocks, out);
-    g_kernel_launches += 2;
-    return cudaGetLastError();
+    HH_KRET(klaunch(k_multidot_partial, dim3(g1), dim3(kRedThreads), 0, s, 1, V, ld, w, N, partials));
+    HH_KRET(klaunch(k_multidot_final, dim3(nvec), dim3(kRedThreads), 0, s, 1, partials, kRedBlocks, out));
+    return cudaSuccess;
 }
 
 // w += sign * sum_i coef[i] V_i   (coefficients read from device memory)
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(256) k_multi_axpy(double2* __restrict__ w, con
                                                     long long ld, int nvec,
                                                     const double2* __restrict__ coef, double sign,
                                                     long long N) {
+    pdl_entry();
     __shared__ double2 c[64];
     for (int t = threadIdx.x; t < nvec && t < 64; t += blockDim.x) {
         double2 v = coef[t];
@@ -105,12 +107,12 @@ cudaError_t launch_multi_axpy(double2* w, const double2* V, long long ld, int nv
                               const double2* coef, double sign, long long N, cudaStream_t s) {
     if (nvec <= 0) return cudaSuccess;
     if (nvec > 64) return cudaErrorInvalidValue;
-    ++g_kernel_launches;
-    k_multi_axpy<<<ew_blocks(N), 256, 0, s>>>(w, V, ld, nvec, coef, sign, N);
-    return cudaGetLastError();
+    HH_KRET(klaunch(k_multi_axpy, dim3(ew_blocks(N)), dim3(256), 0, s, 1, w, V, ld, nvec, coef, sign, N));
+    return cudaSuccess;
 }
 
 __global__ void k_scale_by_rnorm(double2* __restrict__ x, const double2* __restrict__ nrm2, long long N) {
+    pdl_entry();
     const double n2 = nrm2->x;
     if (!(n2 > 0.0)) return;
     const double s = 1.0 / sqrt(n2);
@@ -122,12 +124,12 @@ __global__ void k_scale_by_rnorm(double2* __restrict__ x, const double2* __restr
 }
 
 cudaError_t launch_scale_by_rnorm(double2* x, const double2* nrm2, long long N, cudaStream_t s) {
-    ++g_kernel_launches;
-    k_scale_by_rnorm<<<ew_blocks(N), 256, 0, s>>>(x, nrm2, N);
-    return cudaGetLastError();
+    HH_KRET(klaunch(k_scale_by_rnorm, dim3(ew_blocks(N)), dim3(256), 0, s, 1, x, nrm2, N));
+    return cudaSuccess;
 }
 
 __global__ void k_scale(double2* __restrict__ x, double sc, long long N) {
+    pdl_entry();
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += stride) {
         double2 v = x[p];
@@ -136,9 +138,8 @@ __global__ void k_scale(double2* __restrict__ x, double sc, long long N) {
 }
 
 cudaError_t launch_scale(double2* x, double sc, long long N, cudaStream_t st) {
-    ++g_kernel_launches;
-    k_scale<<<ew_blocks(N), 256, 0, st>>>(x, sc, N);
-    return cudaGetLastError();
+    HH_KRET(klaunch(k_scale, dim3(ew_blocks(N)), dim3(256), 0, st, 1, x, sc, N));
+    return cudaSuccess;
 }
 
 }  // namespace hh

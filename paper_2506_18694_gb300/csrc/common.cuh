@@ -7,6 +7,14 @@
 
 namespace hh {
 
+// Programmatic dependent launch: let the next kernel in the stream start launching now,
+// then wait until every kernel this one depends on has finished and flushed its writes.
+// Every kernel calls this before its first global memory access.
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <typename T> struct VecOf;
 template <> struct VecOf<float> { using type = float2; };
 template <> struct VecOf<double> { using type = double2; };

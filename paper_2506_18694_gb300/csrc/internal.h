@@ -9,6 +9,44 @@ namespace hh {
 
 // Kernels launched by this thread through the launchers below (graph captures included).
 extern thread_local long long g_kernel_launches;
+// 1: launch with programmatic stream serialization (overlaps a kernel's launch with the
+// tail of its predecessor; every kernel starts with pdl_entry()).
+extern thread_local int g_use_pdl;
+
+#define HH_KRET(call)                        \
+    do {                                     \
+        cudaError_t e_ = (call);             \
+        if (e_ != cudaSuccess) return e_;    \
+    } while (0)
+
+// Launch `kernel` on stream s (optionally as clusters of `cluster` CTAs along x).
+template <typename... KArgs, typename... Args>
+inline cudaError_t klaunch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                           int cluster, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    int na = 0;
+    if (g_use_pdl) {
+        at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
+    if (cluster > 1) {
+        at[na].id = cudaLaunchAttributeClusterDimension;
+        at[na].val.clusterDim.x = cluster;
+        at[na].val.clusterDim.y = 1;
+        at[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    cfg.attrs = at;
+    cfg.numAttrs = na;
+    ++g_kernel_launches;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 enum StencilMode {
     MODE_APPLY = 0,   // y = op x
@@ -38,6 +76,60 @@ cudaError_t launch_prolong(const GridDesc& gf, const vec2<T>* ec, vec2<T>* x, cu
 // x += e elementwise
 template <typename T>
 cudaError_t launch_add(vec2<T>* x, const vec2<T>* e, long long N, cudaStream_t s);
+
+// ---- bottom of the V-cycle inside one thread-block cluster (coarse.cu) ----
+constexpr int kMaxClusterLevels = 4;
+constexpr int kClusterThreads = 512;
+
+template <typename T> struct CoarseArgs {
+    int nlev;                           // levels handled; the last one is the coarsest
+    GridDesc g[kMaxClusterLevels];
+    vec2<T>* b[kMaxClusterLevels];      // right sides (b[0] given, the others restricted)
+    vec2<T>* xa[kMaxClusterLevels];     // iterates (ping-pong); the result ends in xa[0]
+    vec2<T>* xb[kMaxClusterLevels];
+    vec2<T>* t[kMaxClusterLevels];      // residual scratch
+    OpCoef<T> op;
+    T omega;
+    int nu_pre, nu_post, nu_coarse;
+};
+
+template <typename T>
+cudaError_t launch_coarse_cluster(const CoarseArgs<T>& a, cudaStream_t s);
+// CTAs per cluster used by launch_coarse_cluster (queried once; call before stream capture)
+template <typename T>
+int cluster_size_for();
+
+// ---- fused 2D marching kernels (march2.cu) ----
+enum MarchMode {
+    M_APPLY = 0,          // y = op x
+    M_AXPBY = 1,          // y = alpha (op x) + beta z
+    M_JACOBI = 2,         // y = x + omega D^{-1} (z - op x),          D = diag(op)
+    M_HSS_FIRST = 3,      // y = alpha (op x) + beta z;  y2 = omega diag(opd)^{-1} y
+    M_JACOBI2_ZERO = 4,   // two sweeps from x = 0 reading only z:  x1 = omega D^{-1} z,
+                          // y = x1 + omega D^{-1} (z - op x1)
+    M_PROLONG_JACOBI = 5, // x~ = x + P ec;  y = x~ + omega D^{-1} (z - op x~)
+    M_RESID_RESTRICT = 6  // y (coarse) = P^T (z - op x)
+};
+
+template <typename T> struct MArgs {
+    GridDesc g;          // grid of the level the stencil runs on
+    OpCoef<T> op;        // stencil operator
+    OpCoef<T> opd;       // operator whose diagonal scales the HSS-first Jacobi step (A_L)
+    const vec2<T>* x;    // stencil input (ignored for M_JACOBI2_ZERO; nullptr = 0 when xzero)
+    const vec2<T>* z;    // right side / second vector
+    const vec2<T>* ec;   // coarse correction (M_PROLONG_JACOBI)
+    vec2<T>* y;          // output
+    vec2<T>* y2;         // second output (M_HSS_FIRST)
+    Cx<T> alpha, beta;
+    T omega;
+    int xzero;           // 1: x is identically zero
+    // filled by the launcher
+    T h, ih;
+    int rows;
+};
+
+template <typename T>
+cudaError_t launch_march2(int mode, const MArgs<T>& a, cudaStream_t s);
 
 cudaError_t launch_cast_d2f(const double2* a, float2* b, long long N, cudaStream_t s);
 cudaError_t launch_cast_f2d(const float2* a, double2* b, long long N, cudaStream_t s);

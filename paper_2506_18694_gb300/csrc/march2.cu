@@ -1,0 +1,228 @@
+// 2D fused V-cycle kernels: one warp owns a strip of 32 consecutive x-nodes (30 outputs,
+// one halo lane on each side) and marches along y.  Each step loads one row of the
+// stencil field with a single coalesced 256-byte access per warp, takes the x-neighbours
+// from the adjacent lanes with warp shuffles, forms the x-direction mass and stiffness
+// passes once per row and keeps them for the three output rows that use them.  The Q1
+// row weights (1D stiffness/mass triples per axis, Dirichlet elimination, Sommerfeld
+// side mass) are the same as in stencil.cu; the modes below fuse the V-cycle's vector
+// updates into the stencil pass so that each fine-level sweep reads and writes each
+// vector once.
+#include "internal.h"
+
+namespace hh {
+
+template <typename T>
+__device__ __forceinline__ Cx<T> shfl_up(Cx<T> v) {
+    return Cx<T>{__shfl_up_sync(0xffffffffu, v.re, 1), __shfl_up_sync(0xffffffffu, v.im, 1)};
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> shfl_dn(Cx<T> v) {
+    return Cx<T>{__shfl_down_sync(0xffffffffu, v.re, 1), __shfl_down_sync(0xffffffffu, v.im, 1)};
+}
+
+template <typename T>
+__device__ __forceinline__ Cx<T> diag2(const Row1<T>& rx, const Row1<T>& ry, const OpCoef<T>& op) {
+    const T dr = op.cK * (rx.kc * ry.mc + rx.mc * ry.kc);
+    const T dm = rx.mc * ry.mc;
+    const T dg = (rx.face ? ry.mc : T(0)) + (ry.face ? rx.mc : T(0));
+    return cx<T>(dr + op.cM.re * dm + op.cG.re * dg, op.cM.im * dm + op.cG.im * dg);
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Value of the stencil field at node (i, r) (both clamped into the grid).
+template <typename T, int MODE>
+__device__ __forceinline__ Cx<T> field2(const MArgs<T>& a, int ic, int rc, const Row1<T>& rx, T h, T ih,
+                                        Cx<T>* bval) {
+    const long long p = (long long)rc * a.g.nn + ic;
+    if (MODE == M_JACOBI2_ZERO) {
+        // first sweep from x = 0: x1 = omega D^{-1} b (zero at Dirichlet nodes)
+        const Row1<T> ry = row1<T>(rc, a.g.n, a.g.dir[2], a.g.dir[3], h, ih);
+        const Cx<T> b = ld<T>(a.z, p);
+        *bval = b;
+        if (rx.masked || ry.masked) return cx<T>(0, 0);
+        return a.omega * cmul(cinv(diag2(rx, ry, a.op)), b);
+    } else if (MODE == M_PROLONG_JACOBI) {
+        // x + P e_c: bilinear interpolation of the coarse correction (coarse Dirichlet
+        // nodes carry no basis function and are skipped)
+        const Row1<T> ry = row1<T>(rc, a.g.n, a.g.dir[2], a.g.dir[3], h, ih);
+        if (rx.masked || ry.masked) return cx<T>(0, 0);
+        const int nc = a.g.n >> 1, nnc = nc + 1;
+        const int I0 = ic >> 1, J0 = rc >> 1;
+        const bool oi = ic & 1, oj = rc & 1;
+        Cx<T> e = cx<T>(0, 0);
+#pragma unroll
+        for (int bj = 0; bj < 2; ++bj) {
+            if (bj == 1 && !oj) break;
+            const int J = J0 + bj;
+            if ((J == 0 && a.g.dir[2]) || (J == nc && a.g.dir[3])) continue;
+            const T wj = oj ? T(0.5) : T(1);
+#pragma unroll
+            for (int ai = 0; ai < 2; ++ai) {
+                if (ai == 1 && !oi) break;
+                const int I = I0 + ai;
+                if ((I == 0 && a.g.dir[0]) || (I == nc && a.g.dir[1])) continue;
+                const T w = oi ? T(0.5) * wj : wj;
+                e = fma_r(w, ld<T>(a.ec, (long long)J * nnc + I), e);
+            }
+        }
+        return ld<T>(a.x, p) + e;
+    } else {
+        return a.xzero ? cx<T>(0, 0) : ld<T>(a.x, p);
+    }
+}
+
+// One warp: a strip of 30 output columns (lanes 1..30; lanes 0 and 31 are the halo) and
+// ROWS consecutive output rows (RESID_RESTRICT: ROWS coarse rows, 2 ROWS + 1 residual
+// rows, 28 fine columns per strip).  All stencil rows of the chunk are loaded before any
+// arithmetic so that every load of the warp is in flight at once.
+template <typename T, int MODE, int ROWS>
+__global__ void __launch_bounds__(128) k_march2(MArgs<T> a) {
+    pdl_entry();
+    constexpr bool RR = MODE == M_RESID_RESTRICT;
+    constexpr int NR = RR ? 2 * ROWS + 3 : ROWS + 2;  // stencil rows
+    constexpr int NZ = NR - 2;                         // rows whose right side is read
+    constexpr bool NEEDZ = MODE != M_APPLY && MODE != M_JACOBI2_ZERO;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int n = a.g.n;
+    const int nc = n >> 1;
+    const T h = a.h, ih = a.ih;
+    const int i = blockIdx.x * (RR ? 28 : 30) + lane - (RR ? 2 : 1);
+    const int base = (blockIdx.y * 4 + warp) * ROWS;  // first output row (coarse row if RR)
+    if (base > (RR ? nc : n)) return;
+    const int rfirst = RR ? 2 * base - 2 : base - 1;
+    const int ic = clampi(i, 0, n);
+    const bool col_in = (i >= 0 && i <= n);
+    const Row1<T> rx = row1<T>(ic, n, a.g.dir[0], a.g.dir[1], h, ih);
+
+    Cx<T> fv[NR], bv[NR], zv[NZ];
+#pragma unroll
+    for (int t = 0; t < NR; ++t) {
+        bv[t] = cx<T>(0, 0);
+        fv[t] = field2<T, MODE>(a, ic, clampi(rfirst + t, 0, n), rx, h, ih, &bv[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < NZ; ++t)
+        zv[t] = NEEDZ ? ld<T>(a.z, (long long)clampi(rfirst + 1 + t, 0, n) * a.g.nn + ic) : cx<T>(0, 0);
+
+    Cx<T> mx[NR], kx[NR];
+#pragma unroll
+    for (int t = 0; t < NR; ++t) {
+        const Cx<T> lft = shfl_up(fv[t]), rgt = shfl_dn(fv[t]);
+        mx[t] = fma_r(rx.mr, rgt, fma_r(rx.mc, fv[t], rx.ml * lft));
+        kx[t] = fma_r(rx.kr, rgt, fma_r(rx.kc, fv[t], rx.kl * lft));
+    }
+
+    Cx<T> acc = cx<T>(0, 0);  // restriction accumulator of the coarse row in progress
+#pragma unroll
+    for (int t = 1; t < NR - 1; ++t) {
+        const int j = rfirst + t;
+        const bool row_in = (j >= 0 && j <= n);
+        const int jc = clampi(j, 0, n);
+        const Row1<T> ry = row1<T>(jc, n, a.g.dir[2], a.g.dir[3], h, ih);
+        Cx<T> Mx = fma_r(ry.mr, mx[t + 1], fma_r(ry.mc, mx[t], ry.ml * mx[t - 1]));
+        Cx<T> Kx = fma_r(ry.mr, kx[t + 1], fma_r(ry.mc, kx[t], ry.ml * kx[t - 1]));
+        Kx = fma_r(ry.kr, mx[t + 1], fma_r(ry.kc, mx[t], fma_r(ry.kl, mx[t - 1], Kx)));
+        Cx<T> F = cx<T>(0, 0);
+        if (rx.face) F = fma_r(ry.mr, fv[t + 1], fma_r(ry.mc, fv[t], ry.ml * fv[t - 1]));
+        if (ry.face) F = F + mx[t];
+        Cx<T> ax = a.op.cK * Kx;
+        ax = fma_c(a.op.cM, Mx, ax);
+        ax = fma_c(a.op.cG, F, ax);
+        const bool masked = rx.masked || ry.masked;
+        const long long p = (long long)jc * a.g.nn + ic;
+        if (RR) {
+            const Cx<T> res = (row_in && col_in && !masked) ? zv[t - 1] - ax : cx<T>(0, 0);
+            // full weighting along x: r(i) + (r(i-1) + r(i+1)) / 2
+            const Cx<T> rr = fma_r(T(0.5), shfl_up(res) + shfl_dn(res), res);
+            if ((t & 1) == 0) {  // j = 2 base - 1 + t - 1 is even: centre row of coarse row j/2
+                acc = acc + rr;
+            } else {
+                if (t >= 3) {  // odd row closes coarse row (j - 1)/2
+                    acc = fma_r(T(0.5), rr, acc);
+                    const int J = (j - 1) >> 1;
+                    const int I = blockIdx.x * 14 + ((lane - 2) >> 1);
+                    if (lane >= 2 && lane <= 28 && !(lane & 1) && I <= nc && J <= nc) {
+                        const bool cm = (I == 0 && a.g.dir[0]) || (I == nc && a.g.dir[1]) ||
+                                        (J == 0 && a.g.dir[2]) || (J == nc && a.g.dir[3]);
+                        st<T>(a.y, (long long)J * (nc + 1) + I, cm ? cx<T>(0, 0) : acc);
+                    }
+                }
+                acc = T(0.5) * rr;
+            }
+            continue;
+        }
+        if (!(lane >= 1 && lane <= 30 && col_in && row_in)) continue;
+        if (masked) {
+            st<T>(a.y, p, cx<T>(0, 0));
+            if (MODE == M_HSS_FIRST) st<T>(a.y2, p, cx<T>(0, 0));
+            continue;
+        }
+        if (MODE == M_APPLY) {
+            st<T>(a.y, p, ax);
+        } else if (MODE == M_AXPBY) {
+            st<T>(a.y, p, fma_c(a.alpha, ax, cmul(a.beta, zv[t - 1])));
+        } else if (MODE == M_HSS_FIRST) {
+            const Cx<T> rhs = fma_c(a.alpha, ax, cmul(a.beta, zv[t - 1]));
+            st<T>(a.y, p, rhs);
+            st<T>(a.y2, p, a.omega * cmul(cinv(diag2(rx, ry, a.opd)), rhs));
+        } else {
+            // Jacobi update of the field: field + omega D^{-1} (b - op field)
+            const Cx<T> b = (MODE == M_JACOBI2_ZERO) ? bv[t] : zv[t - 1];
+            const Cx<T> d = diag2(rx, ry, a.op);
+            st<T>(a.y, p, fma_c(cinv(d), a.omega * (b - ax), fv[t]));
+        }
+    }
+}
+
+// Rows per warp: the largest that still leaves about 24 warps per SM (loads in flight).
+template <typename T, int MODE>
+static cudaError_t go2(MArgs<T> a, cudaStream_t s) {
+    a.h = T(a.g.h);
+    a.ih = T(1.0 / a.g.h);
+    const long long want = 152LL * 24;
+    if constexpr (MODE == M_RESID_RESTRICT) {
+        const int nnc = a.g.n / 2 + 1;
+        const long long strips = (nnc + 13) / 14;
+        const int rows = (strips * ((nnc + 3) / 4) >= want) ? 4 : 2;
+        const int chunks = (nnc + rows - 1) / rows;
+        dim3 grd((unsigned)strips, (unsigned)((chunks + 3) / 4), 1);
+        if (rows == 4) return klaunch(k_march2<T, MODE, 4>, dim3(grd), dim3(128), 0, s, 1, a);
+        return klaunch(k_march2<T, MODE, 2>, dim3(grd), dim3(128), 0, s, 1, a);
+    } else {
+        const long long strips = (a.g.nn + 29) / 30;
+        int rows = 2;
+        if (sizeof(T) == 4 && strips * ((a.g.nn + 7) / 8) >= want) rows = 8;
+        else if (strips * ((a.g.nn + 3) / 4) >= want) rows = 4;
+        const int chunks = (a.g.nn + rows - 1) / rows;
+        dim3 grd((unsigned)strips, (unsigned)((chunks + 3) / 4), 1);
+        if constexpr (sizeof(T) == 4) {
+            if (rows == 8) {
+                return klaunch(k_march2<T, MODE, 8>, dim3(grd), dim3(128), 0, s, 1, a);
+            }
+        }
+        if (rows == 4) return klaunch(k_march2<T, MODE, 4>, dim3(grd), dim3(128), 0, s, 1, a);
+        return klaunch(k_march2<T, MODE, 2>, dim3(grd), dim3(128), 0, s, 1, a);
+    }
+}
+
+template <typename T>
+cudaError_t launch_march2(int mode, const MArgs<T>& a, cudaStream_t s) {
+    if (a.g.dim != 2) return cudaErrorInvalidValue;
+    switch (mode) {
+        case M_APPLY: return go2<T, M_APPLY>(a, s);
+        case M_AXPBY: return go2<T, M_AXPBY>(a, s);
+        case M_JACOBI: return go2<T, M_JACOBI>(a, s);
+        case M_HSS_FIRST: return go2<T, M_HSS_FIRST>(a, s);
+        case M_JACOBI2_ZERO: return go2<T, M_JACOBI2_ZERO>(a, s);
+        case M_PROLONG_JACOBI: return go2<T, M_PROLONG_JACOBI>(a, s);
+        case M_RESID_RESTRICT: return go2<T, M_RESID_RESTRICT>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_march2<float>(int, const MArgs<float>&, cudaStream_t);
+template cudaError_t launch_march2<double>(int, const MArgs<double>&, cudaStream_t);
+
+}  // namespace hh

@@ -185,12 +185,17 @@ hh_status ensure_hier(hh_problem* p, int prec) {
     HH_TRY(dmalloc(p, &H.ca, n0));
     HH_TRY(dmalloc(p, &H.cb, n0));
     HH_TRY(dmalloc(p, &H.cres, n0));
+    // query the cluster shape now: nothing below may call into the runtime's
+    // configuration API while the stream is being captured
+    if (prec == HH_C64) hh::cluster_size_for<float>();
+    else hh::cluster_size_for<double>();
     H.ready = true;
     return HH_OK;
 }
 
 // Order work on the problem stream after the caller's stream, and back.
 hh_status join_in(hh_problem* p) {
+    hh::g_use_pdl = p->o.use_pdl ? 1 : 0;
     HH_CUDA(cudaEventRecord(p->ev_in, p->user));
     HH_CUDA(cudaStreamWaitEvent(p->s, p->ev_in, 0));
     return HH_OK;
@@ -202,6 +207,12 @@ hh_status join_out(hh_problem* p) {
 }
 
 // ------------------------------------------------------------------ V-cycle
+#define HH_LAUNCH(call)                                                                  \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) return fail(HH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
 template <typename T>
 struct MG {
     using V2 = hh::vec2<T>;
@@ -211,75 +222,219 @@ struct MG {
     OpCoef<T> al;
     T omega;
 
+    bool d2() const { return p->grid.dim == 2; }
+
+    hh::MArgs<T> margs(int l, const OpCoef<T>& op) const {
+        hh::MArgs<T> a{};
+        a.g = p->lv[l];
+        a.op = op;
+        a.opd = al;
+        a.omega = omega;
+        return a;
+    }
+
+    // ---- level kernels: fused 2D marching kernels, composed generic kernels in 3D ----
+    // x_out = x_in + omega D^{-1} (b - A_L x_in); x_in == nullptr means 0
     hh_status jacobi(int l, const V2* b, const V2* xin, V2* xout) {
-        cudaError_t e = hh::launch_stencil<T>(hh::MODE_JACOBI, p->lv[l], al, xin, b, xout, Cx<T>{0, 0},
-                                              Cx<T>{0, 0}, omega, s);
-        if (e != cudaSuccess) return fail(HH_ERR_CUDA, std::string("jacobi launch: ") + cudaGetErrorString(e));
-        return HH_OK;
-    }
-
-    // nsweeps Jacobi sweeps from x = 0 on level l; returns the buffer holding x.
-    hh_status smooth_from_zero(int l, const V2* b, int nsweeps, V2** out) {
-        V2* cur = (V2*)H->xa[l];
-        V2* oth = (V2*)H->xb[l];
-        if (nsweeps == 0) {
-            HH_CUDA(cudaMemsetAsync(cur, 0, (size_t)p->lv[l].N * sizeof(V2), s));
+        if (d2()) {
+            hh::MArgs<T> a = margs(l, al);
+            a.x = xin;
+            a.xzero = xin == nullptr;
+            a.z = b;
+            a.y = xout;
+            HH_LAUNCH(hh::launch_march2<T>(hh::M_JACOBI, a, s));
         } else {
-            HH_TRY(jacobi(l, b, nullptr, cur));
-            for (int k = 1; k < nsweeps; ++k) {
-                HH_TRY(jacobi(l, b, cur, oth));
-                V2* t = cur; cur = oth; oth = t;
-            }
+            HH_LAUNCH(hh::launch_stencil<T>(hh::MODE_JACOBI, p->lv[l], al, xin, b, xout, Cx<T>{0, 0}, Cx<T>{0, 0},
+                                            omega, s));
         }
-        *out = cur;
+        return HH_OK;
+    }
+    // two sweeps from x = 0
+    hh_status jacobi2_zero(int l, const V2* b, V2* xout) {
+        if (d2()) {
+            hh::MArgs<T> a = margs(l, al);
+            a.z = b;
+            a.y = xout;
+            HH_LAUNCH(hh::launch_march2<T>(hh::M_JACOBI2_ZERO, a, s));
+            return HH_OK;
+        }
+        V2* tmp = (V2*)H->t[l];
+        HH_TRY(jacobi(l, b, nullptr, tmp));
+        return jacobi(l, b, tmp, xout);
+    }
+    // rc = P^T (b - A_L x)
+    hh_status resid_restrict(int l, const V2* b, const V2* x, V2* rc) {
+        if (d2()) {
+            hh::MArgs<T> a = margs(l, al);
+            a.x = x;
+            a.z = b;
+            a.y = rc;
+            HH_LAUNCH(hh::launch_march2<T>(hh::M_RESID_RESTRICT, a, s));
+        } else {
+            HH_LAUNCH(hh::launch_residual_restrict<T>(p->lv[l], p->lv[l + 1], al, b, x, rc, (V2*)H->t[l], s));
+        }
+        return HH_OK;
+    }
+    // xout = x~ + omega D^{-1} (b - A_L x~), x~ = x + P ec   (x is clobbered in 3D)
+    hh_status prolong_jacobi(int l, V2* x, const V2* ec, const V2* b, V2* xout) {
+        if (d2()) {
+            hh::MArgs<T> a = margs(l, al);
+            a.x = x;
+            a.ec = ec;
+            a.z = b;
+            a.y = xout;
+            HH_LAUNCH(hh::launch_march2<T>(hh::M_PROLONG_JACOBI, a, s));
+            return HH_OK;
+        }
+        HH_LAUNCH(hh::launch_prolong<T>(p->lv[l], ec, x, s));
+        return jacobi(l, b, x, xout);
+    }
+    // rhs = c1 A_R u + c2 r and the first Jacobi sweep x1 = omega D^{-1} rhs (u == nullptr: u = 0)
+    hh_status hss_first(const V2* u, const V2* r, V2* rhs, V2* x1, T c1, T c2) {
+        const OpCoef<T> ar = to_coef<T>(p->AR);
+        if (d2()) {
+            hh::MArgs<T> a = margs(0, ar);
+            a.x = u;
+            a.xzero = u == nullptr;
+            a.z = r;
+            a.y = rhs;
+            a.y2 = x1;
+            a.alpha = Cx<T>{c1, 0};
+            a.beta = Cx<T>{c2, 0};
+            HH_LAUNCH(hh::launch_march2<T>(hh::M_HSS_FIRST, a, s));
+            return HH_OK;
+        }
+        HH_LAUNCH(hh::launch_stencil<T>(hh::MODE_AXPBY, p->lv[0], ar, u, r, rhs, Cx<T>{c1, 0}, Cx<T>{c2, 0}, T(0), s));
+        return jacobi(0, rhs, nullptr, x1);
+    }
+    hh_status hss_rhs(const V2* u, const V2* r, V2* rhs, T c1, T c2) {
+        const OpCoef<T> ar = to_coef<T>(p->AR);
+        if (d2()) {
+            hh::MArgs<T> a = margs(0, ar);
+            a.x = u;
+            a.xzero = u == nullptr;
+            a.z = r;
+            a.y = rhs;
+            a.alpha = Cx<T>{c1, 0};
+            a.beta = Cx<T>{c2, 0};
+            HH_LAUNCH(hh::launch_march2<T>(hh::M_AXPBY, a, s));
+            return HH_OK;
+        }
+        HH_LAUNCH(hh::launch_stencil<T>(hh::MODE_AXPBY, p->lv[0], ar, u, r, rhs, Cx<T>{c1, 0}, Cx<T>{c2, 0}, T(0), s));
         return HH_OK;
     }
 
+    V2* other(int l, V2* x) { return x == (V2*)H->xa[l] ? (V2*)H->xb[l] : (V2*)H->xa[l]; }
+
+    // nsweeps more sweeps starting from the iterate in *x (ping-pong within level l)
     hh_status smooth(int l, const V2* b, int nsweeps, V2** x) {
         V2* cur = *x;
-        V2* oth = (cur == (V2*)H->xa[l]) ? (V2*)H->xb[l] : (V2*)H->xa[l];
         for (int k = 0; k < nsweeps; ++k) {
+            V2* oth = other(l, cur);
             HH_TRY(jacobi(l, b, cur, oth));
-            V2* t = cur; cur = oth; oth = t;
+            cur = oth;
         }
         *x = cur;
         return HH_OK;
     }
 
-    // One V-cycle on level l for right side b (x = 0 start); result buffer in *out.
-    hh_status vcycle(int l, const V2* b, V2** out) {
+    // nsweeps sweeps from x = 0 into the level-l buffers
+    hh_status smooth_from_zero(int l, const V2* b, int nsweeps, V2** out) {
+        V2* cur = (V2*)H->xa[l];
+        if (nsweeps == 0) {
+            HH_CUDA(cudaMemsetAsync(cur, 0, (size_t)p->lv[l].N * sizeof(V2), s));
+        } else if (nsweeps == 1) {
+            HH_TRY(jacobi(l, b, nullptr, cur));
+        } else {
+            HH_TRY(jacobi2_zero(l, b, cur));
+            HH_TRY(smooth(l, b, nsweeps - 2, &cur));
+        }
+        *out = cur;
+        return HH_OK;
+    }
+
+    // First level handled by the cluster kernel (the bottom of the V-cycle), or L if none.
+    int cluster_level() const {
         const int L = p->o.levels;
-        if (l == L - 1) return smooth_from_zero(l, b, p->o.nu_coarse, out);
+        int lc = L;
+        while (lc - 1 >= 1 && p->lv[lc - 1].N <= p->o.coarse_cluster_nodes && L - (lc - 1) <= hh::kMaxClusterLevels)
+            --lc;
+        return lc;
+    }
+
+    hh_status cluster_cycle(int lc, const V2* b, V2** out) {
+        hh::CoarseArgs<T> a{};
+        a.nlev = p->o.levels - lc;
+        for (int i = 0; i < a.nlev; ++i) {
+            a.g[i] = p->lv[lc + i];
+            a.b[i] = (V2*)H->b[lc + i];
+            a.xa[i] = (V2*)H->xa[lc + i];
+            a.xb[i] = (V2*)H->xb[lc + i];
+            a.t[i] = (V2*)H->t[lc + i];
+        }
+        a.b[0] = const_cast<V2*>(b);
+        a.op = al;
+        a.omega = omega;
+        a.nu_pre = p->o.nu_pre;
+        a.nu_post = p->o.nu_post;
+        a.nu_coarse = p->o.nu_coarse;
+        HH_LAUNCH(hh::launch_coarse_cluster<T>(a, s));
+        *out = (V2*)H->xa[lc];
+        return HH_OK;
+    }
+
+    // One V-cycle on level l for right side b from x = 0; result buffer in *out.
+    // xstart: the first pre-smoothing sweep was already done and sits in xstart.
+    hh_status vcycle(int l, const V2* b, V2* xstart, V2** out) {
+        const int L = p->o.levels;
+        if (!xstart && l >= 1 && l == cluster_level()) return cluster_cycle(l, b, out);
+        if (l == L - 1) {
+            V2* x = (V2*)H->xa[l];
+            if (xstart) {
+                x = xstart;
+                HH_TRY(smooth(l, b, p->o.nu_coarse - 1, &x));
+            } else {
+                HH_TRY(smooth_from_zero(l, b, p->o.nu_coarse, &x));
+            }
+            *out = x;
+            return HH_OK;
+        }
         V2* x;
-        HH_TRY(smooth_from_zero(l, b, p->o.nu_pre, &x));
-        cudaError_t e = hh::launch_residual_restrict<T>(p->lv[l], p->lv[l + 1], al, b, x,
-                                                        (V2*)H->b[l + 1], (V2*)H->t[l], s);
-        if (e != cudaSuccess) return fail(HH_ERR_CUDA, std::string("restrict: ") + cudaGetErrorString(e));
+        if (xstart) {
+            x = xstart;
+            HH_TRY(smooth(l, b, p->o.nu_pre - 1, &x));
+        } else {
+            HH_TRY(smooth_from_zero(l, b, p->o.nu_pre, &x));
+        }
+        HH_TRY(resid_restrict(l, b, x, (V2*)H->b[l + 1]));
         V2* ec;
-        HH_TRY(vcycle(l + 1, (const V2*)H->b[l + 1], &ec));
-        e = hh::launch_prolong<T>(p->lv[l], ec, x, s);
-        if (e != cudaSuccess) return fail(HH_ERR_CUDA, std::string("prolong: ") + cudaGetErrorString(e));
-        HH_TRY(smooth(l, b, p->o.nu_post, &x));
+        HH_TRY(vcycle(l + 1, (const V2*)H->b[l + 1], nullptr, &ec));
+        if (p->o.nu_post == 0) {
+            HH_LAUNCH(hh::launch_prolong<T>(p->lv[l], ec, x, s));
+        } else {
+            V2* oth = other(l, x);
+            HH_TRY(prolong_jacobi(l, x, ec, b, oth));
+            x = oth;
+            HH_TRY(smooth(l, b, p->o.nu_post - 1, &x));
+        }
         *out = x;
         return HH_OK;
     }
 
-    // cycles_per_hss V-cycles for A_L x = b from x = 0; result buffer in *out.
-    hh_status mg_solve(const V2* b, V2** out) {
+    // cycles_per_hss V-cycles for A_L x = b; the first may start from xstart.
+    hh_status mg_solve(const V2* b, V2* xstart, V2** out) {
         V2* x;
-        HH_TRY(vcycle(0, b, &x));
+        HH_TRY(vcycle(0, b, xstart, &x));
         const long long N = p->lv[0].N;
         for (int c = 1; c < p->o.cycles_per_hss; ++c) {
             // keep x outside the level-0 ping-pong buffers the next cycle overwrites
             V2* keep = (V2*)((x == (V2*)H->ca) ? H->cb : H->ca);
             HH_CUDA(cudaMemcpyAsync(keep, x, (size_t)N * sizeof(V2), cudaMemcpyDeviceToDevice, s));
-            cudaError_t e = hh::launch_stencil<T>(hh::MODE_AXPBY, p->lv[0], al, keep, b, (V2*)H->cres,
-                                                  Cx<T>{-1, 0}, Cx<T>{1, 0}, T(0), s);
-            if (e != cudaSuccess) return fail(HH_ERR_CUDA, cudaGetErrorString(e));
+            HH_LAUNCH(hh::launch_stencil<T>(hh::MODE_AXPBY, p->lv[0], al, keep, b, (V2*)H->cres, Cx<T>{-1, 0},
+                                            Cx<T>{1, 0}, T(0), s));
             V2* corr;
-            HH_TRY(vcycle(0, (const V2*)H->cres, &corr));
-            e = hh::launch_add<T>(keep, corr, N, s);
-            if (e != cudaSuccess) return fail(HH_ERR_CUDA, cudaGetErrorString(e));
+            HH_TRY(vcycle(0, (const V2*)H->cres, nullptr, &corr));
+            HH_LAUNCH(hh::launch_add<T>(keep, corr, N, s));
             x = keep;
         }
         *out = x;
@@ -289,15 +444,21 @@ struct MG {
     // The HSS loop of Def. 4.1 on r_lo (already in this precision); result buffer in *out.
     hh_status hss_loop(V2** out) {
         const double k = p->k;
-        const double c1 = (k - 1.0) / (k + 1.0), c2 = 2.0 * k / (k + 1.0);
-        OpCoef<T> ar = to_coef<T>(p->AR);
+        const T c1 = T((k - 1.0) / (k + 1.0)), c2 = T(2.0 * k / (k + 1.0));
         const int nh = n_hss(k, p->o.theta);
+        const bool fuse = p->o.nu_pre >= 1 && p->o.levels >= 1 &&
+                          !(p->o.levels == 1 && p->o.nu_coarse == 0);
         V2* u = nullptr;
         for (int it = 0; it < nh; ++it) {
-            cudaError_t e = hh::launch_stencil<T>(hh::MODE_AXPBY, p->lv[0], ar, u, (const V2*)H->r_lo,
-                                                  (V2*)H->rhs, Cx<T>{T(c1), 0}, Cx<T>{T(c2), 0}, T(0), s);
-            if (e != cudaSuccess) return fail(HH_ERR_CUDA, cudaGetErrorString(e));
-            HH_TRY(mg_solve((const V2*)H->rhs, &u));
+            if (fuse) {
+                // the first pre-smoothing sweep of the fine level is fused with the right side
+                V2* x1 = (u == (V2*)H->xa[0]) ? (V2*)H->xb[0] : (V2*)H->xa[0];
+                HH_TRY(hss_first(u, (const V2*)H->r_lo, (V2*)H->rhs, x1, c1, c2));
+                HH_TRY(mg_solve((const V2*)H->rhs, x1, &u));
+            } else {
+                HH_TRY(hss_rhs(u, (const V2*)H->r_lo, (V2*)H->rhs, c1, c2));
+                HH_TRY(mg_solve((const V2*)H->rhs, nullptr, &u));
+            }
         }
         if (!u) {  // theta such that no iteration runs: u = 0
             u = (V2*)H->xa[0];
@@ -386,19 +547,36 @@ hh_status precondition_async(hh_problem* p, const double2* r, double2* z) {
 }
 
 // ------------------------------------------------------------------ FP64 helpers
-hh_status apply_B(hh_problem* p, const double2* x, double2* y) {
-    OpCoef<double> b = to_coef<double>(p->B);
-    HH_CUDA(hh::launch_stencil<double>(hh::MODE_APPLY, p->lv[0], b, x, nullptr, y, Cx<double>{0, 0},
-                                       Cx<double>{0, 0}, 0.0, p->s));
+// y = alpha (op x) + beta z  (z == nullptr: y = op x) on level l, stream st
+template <typename T>
+hh_status op_axpby(hh_problem* p, int l, const Triple& t, const hh::vec2<T>* x, const hh::vec2<T>* z,
+                   hh::vec2<T>* y, Cx<T> alpha, Cx<T> beta, cudaStream_t st) {
+    const OpCoef<T> op = to_coef<T>(t);
+    if (p->grid.dim == 2) {
+        hh::MArgs<T> a{};
+        a.g = p->lv[l];
+        a.op = op;
+        a.opd = op;
+        a.x = x;
+        a.z = z;
+        a.y = y;
+        a.alpha = alpha;
+        a.beta = beta;
+        HH_LAUNCH(hh::launch_march2<T>(z ? hh::M_AXPBY : hh::M_APPLY, a, st));
+    } else {
+        HH_LAUNCH(hh::launch_stencil<T>(z ? hh::MODE_AXPBY : hh::MODE_APPLY, p->lv[l], op, x, z, y, alpha, beta,
+                                        T(0), st));
+    }
     return HH_OK;
+}
+
+hh_status apply_B(hh_problem* p, const double2* x, double2* y) {
+    return op_axpby<double>(p, 0, p->B, x, nullptr, y, Cx<double>{1, 0}, Cx<double>{0, 0}, p->s);
 }
 
 // r = bvec - B x
 hh_status residual_B(hh_problem* p, const double2* x, double2* r) {
-    OpCoef<double> b = to_coef<double>(p->B);
-    HH_CUDA(hh::launch_stencil<double>(hh::MODE_AXPBY, p->lv[0], b, x, p->bvec, r, Cx<double>{-1, 0},
-                                       Cx<double>{1, 0}, 0.0, p->s));
-    return HH_OK;
+    return op_axpby<double>(p, 0, p->B, x, p->bvec, r, Cx<double>{-1, 0}, Cx<double>{1, 0}, p->s);
 }
 
 // ||v||^2 into hbuf[slot] (device), and optionally fetched to the host.
@@ -542,6 +720,8 @@ void hh_options_default(hh_options* o) {
     o->max_outer = 1000;
     o->precision = HH_C64;
     o->use_graphs = 1;
+    o->use_pdl = 1;
+    o->coarse_cluster_nodes = 20000;
 }
 
 static hh_status check_args(const hh_grid* grid, double k, double delta, double dh, const int* bc,
@@ -561,6 +741,7 @@ static hh_status check_args(const hh_grid* grid, double k, double delta, double 
     if (o->max_outer < 0) return fail(HH_ERR_INVALID, "max_outer < 0");
     if (!(o->theta >= 0) || !(o->omega > 0)) return fail(HH_ERR_INVALID, "theta >= 0 and omega > 0 required");
     if (o->precision != HH_C64 && o->precision != HH_C128) return fail(HH_ERR_INVALID, "bad precision");
+    if (o->coarse_cluster_nodes < 0) return fail(HH_ERR_INVALID, "coarse_cluster_nodes < 0");
     if (!bc) return fail(HH_ERR_INVALID, "null bc");
     for (int s = 0; s < 2 * grid->dim; ++s)
         if (bc[s] != HH_BC_SOMMERFELD && bc[s] != HH_BC_DIRICHLET) return fail(HH_ERR_INVALID, "bad boundary tag");
@@ -730,31 +911,30 @@ hh_status hh_apply(hh_problem* p, int level, int op, int precision, const void* 
     bool ok;
     Triple t = op_triple(p, op, &ok);
     if (!ok) return fail(HH_ERR_INVALID, "unknown operator");
+    HH_TRY(join_in(p));
     if (precision == HH_C64) {
-        HH_CUDA(hh::launch_stencil<float>(hh::MODE_APPLY, p->lv[level], to_coef<float>(t), (const float2*)x,
-                                          nullptr, (float2*)y, Cx<float>{0, 0}, Cx<float>{0, 0}, 0.f, p->user));
+        HH_TRY(op_axpby<float>(p, level, t, (const float2*)x, nullptr, (float2*)y, Cx<float>{1, 0}, Cx<float>{0, 0},
+                               p->s));
     } else {
-        HH_CUDA(hh::launch_stencil<double>(hh::MODE_APPLY, p->lv[level], to_coef<double>(t), (const double2*)x,
-                                           nullptr, (double2*)y, Cx<double>{0, 0}, Cx<double>{0, 0}, 0.0,
-                                           p->user));
+        HH_TRY(op_axpby<double>(p, level, t, (const double2*)x, nullptr, (double2*)y, Cx<double>{1, 0},
+                                Cx<double>{0, 0}, p->s));
     }
-    return HH_OK;
+    return join_out(p);
 }
 
 hh_status hh_jacobi(hh_problem* p, int level, int precision, const void* b, const void* x_in, void* x_out) {
     HH_TRY(validate_level(p, level, 0));
     HH_TRY(validate_prec(precision));
     if (!b || !x_out || x_out == x_in || x_out == b) return fail(HH_ERR_INVALID, "bad vectors");
+    HH_TRY(join_in(p));
     if (precision == HH_C64) {
-        HH_CUDA(hh::launch_stencil<float>(hh::MODE_JACOBI, p->lv[level], to_coef<float>(p->AL), (const float2*)x_in,
-                                          (const float2*)b, (float2*)x_out, Cx<float>{0, 0}, Cx<float>{0, 0},
-                                          float(p->o.omega), p->user));
+        MG<float> m = make_mg<float>(p, precision, p->s);
+        HH_TRY(m.jacobi(level, (const float2*)b, (const float2*)x_in, (float2*)x_out));
     } else {
-        HH_CUDA(hh::launch_stencil<double>(hh::MODE_JACOBI, p->lv[level], to_coef<double>(p->AL),
-                                           (const double2*)x_in, (const double2*)b, (double2*)x_out,
-                                           Cx<double>{0, 0}, Cx<double>{0, 0}, p->o.omega, p->user));
+        MG<double> m = make_mg<double>(p, precision, p->s);
+        HH_TRY(m.jacobi(level, (const double2*)b, (const double2*)x_in, (double2*)x_out));
     }
-    return HH_OK;
+    return join_out(p);
 }
 
 hh_status hh_residual_restrict(hh_problem* p, int level, int precision, const void* b, const void* x, void* rc) {
@@ -762,31 +942,28 @@ hh_status hh_residual_restrict(hh_problem* p, int level, int precision, const vo
     HH_TRY(validate_prec(precision));
     if (!b || !x || !rc) return fail(HH_ERR_INVALID, "null vector");
     HH_TRY(ensure_hier(p, precision));
-    Hier& H = p->hier[precision];
     HH_TRY(join_in(p));
     if (precision == HH_C64) {
-        HH_CUDA(hh::launch_residual_restrict<float>(p->lv[level], p->lv[level + 1], to_coef<float>(p->AL),
-                                                    (const float2*)b, (const float2*)x, (float2*)rc,
-                                                    (float2*)H.t[level], p->s));
+        MG<float> m = make_mg<float>(p, precision, p->s);
+        HH_TRY(m.resid_restrict(level, (const float2*)b, (const float2*)x, (float2*)rc));
     } else {
-        HH_CUDA(hh::launch_residual_restrict<double>(p->lv[level], p->lv[level + 1], to_coef<double>(p->AL),
-                                                     (const double2*)b, (const double2*)x, (double2*)rc,
-                                                     (double2*)H.t[level], p->s));
+        MG<double> m = make_mg<double>(p, precision, p->s);
+        HH_TRY(m.resid_restrict(level, (const double2*)b, (const double2*)x, (double2*)rc));
     }
-    HH_TRY(join_out(p));
-    return HH_OK;
+    return join_out(p);
 }
 
 hh_status hh_prolong_correct(hh_problem* p, int level, int precision, const void* ec, void* x) {
     HH_TRY(validate_level(p, level, 1));
     HH_TRY(validate_prec(precision));
     if (!ec || !x) return fail(HH_ERR_INVALID, "null vector");
+    HH_TRY(join_in(p));
     if (precision == HH_C64) {
-        HH_CUDA(hh::launch_prolong<float>(p->lv[level], (const float2*)ec, (float2*)x, p->user));
+        HH_CUDA(hh::launch_prolong<float>(p->lv[level], (const float2*)ec, (float2*)x, p->s));
     } else {
-        HH_CUDA(hh::launch_prolong<double>(p->lv[level], (const double2*)ec, (double2*)x, p->user));
+        HH_CUDA(hh::launch_prolong<double>(p->lv[level], (const double2*)ec, (double2*)x, p->s));
     }
-    return HH_OK;
+    return join_out(p);
 }
 
 hh_status hh_vcycle(hh_problem* p, int precision, const void* b, void* x) {
@@ -799,16 +976,15 @@ hh_status hh_vcycle(hh_problem* p, int precision, const void* b, void* x) {
     if (precision == HH_C64) {
         MG<float> m = make_mg<float>(p, precision, p->s);
         float2* out;
-        HH_TRY(m.vcycle(0, (const float2*)b, &out));
+        HH_TRY(m.vcycle(0, (const float2*)b, nullptr, &out));
         HH_CUDA(cudaMemcpyAsync(x, out, nb, cudaMemcpyDeviceToDevice, p->s));
     } else {
         MG<double> m = make_mg<double>(p, precision, p->s);
         double2* out;
-        HH_TRY(m.vcycle(0, (const double2*)b, &out));
+        HH_TRY(m.vcycle(0, (const double2*)b, nullptr, &out));
         HH_CUDA(cudaMemcpyAsync(x, out, nb, cudaMemcpyDeviceToDevice, p->s));
     }
-    HH_TRY(join_out(p));
-    return HH_OK;
+    return join_out(p);
 }
 
 hh_status hh_hss_rhs(hh_problem* p, int precision, const void* u, const void* r, void* rhs) {
@@ -816,16 +992,15 @@ hh_status hh_hss_rhs(hh_problem* p, int precision, const void* u, const void* r,
     HH_TRY(validate_prec(precision));
     if (!r || !rhs) return fail(HH_ERR_INVALID, "null vector");
     const double k = p->k, c1 = (k - 1.0) / (k + 1.0), c2 = 2.0 * k / (k + 1.0);
+    HH_TRY(join_in(p));
     if (precision == HH_C64) {
-        HH_CUDA(hh::launch_stencil<float>(hh::MODE_AXPBY, p->lv[0], to_coef<float>(p->AR), (const float2*)u,
-                                          (const float2*)r, (float2*)rhs, Cx<float>{float(c1), 0},
-                                          Cx<float>{float(c2), 0}, 0.f, p->user));
+        MG<float> m = make_mg<float>(p, precision, p->s);
+        HH_TRY(m.hss_rhs((const float2*)u, (const float2*)r, (float2*)rhs, float(c1), float(c2)));
     } else {
-        HH_CUDA(hh::launch_stencil<double>(hh::MODE_AXPBY, p->lv[0], to_coef<double>(p->AR), (const double2*)u,
-                                           (const double2*)r, (double2*)rhs, Cx<double>{c1, 0}, Cx<double>{c2, 0},
-                                           0.0, p->user));
+        MG<double> m = make_mg<double>(p, precision, p->s);
+        HH_TRY(m.hss_rhs((const double2*)u, (const double2*)r, (double2*)rhs, c1, c2));
     }
-    return HH_OK;
+    return join_out(p);
 }
 
 hh_status hh_precondition(hh_problem* p, const void* r, void* z) {
@@ -839,10 +1014,10 @@ hh_status hh_precondition(hh_problem* p, const void* r, void* z) {
 
 hh_status hh_load_vector(hh_problem* p, const void* f, void* b) {
     if (!p || !f || !b) return fail(HH_ERR_INVALID, "null argument");
-    Triple t{0.0, 1.0, 0.0};
-    HH_CUDA(hh::launch_stencil<double>(hh::MODE_APPLY, p->lv[0], to_coef<double>(t), (const double2*)f, nullptr,
-                                       (double2*)b, Cx<double>{0, 0}, Cx<double>{0, 0}, 0.0, p->user));
-    return HH_OK;
+    HH_TRY(join_in(p));
+    HH_TRY(op_axpby<double>(p, 0, Triple{0.0, 1.0, 0.0}, (const double2*)f, nullptr, (double2*)b, Cx<double>{1, 0},
+                            Cx<double>{0, 0}, p->s));
+    return join_out(p);
 }
 
 hh_status hh_dot(hh_problem* p, const void* x, const void* y, double* out) {

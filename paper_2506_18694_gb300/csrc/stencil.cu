@@ -9,115 +9,12 @@
 // dimensional mass of that side.  No matrix is stored: one output node reads the
 // 3^dim neighbourhood of x once.
 #include "internal.h"
+#include "node.cuh"
 
 namespace hh {
 
 thread_local long long g_kernel_launches = 0;
-
-template <typename T> struct NodeResult {
-    Cx<T> ax;  // (op x) at the node
-    Cx<T> d;   // diagonal entry of op at the node
-};
-
-// (op x) and diag(op) at node (i,j) of a 2D grid; rows rx, ry precomputed.
-template <typename T, bool NEED_AX>
-__device__ __forceinline__ NodeResult<T> node2(const vec2<T>* __restrict__ x, int nn, int i, int j,
-                                               const Row1<T>& rx, const Row1<T>& ry,
-                                               const OpCoef<T>& op) {
-    NodeResult<T> r;
-    const T fxw = rx.face ? ry.mc : T(0);
-    const T fyw = ry.face ? rx.mc : T(0);
-    const T dr = op.cK * (rx.kc * ry.mc + rx.mc * ry.kc);
-    const T dm = rx.mc * ry.mc;
-    const T dg = fxw + fyw;
-    r.d = cx<T>(dr + op.cM.re * dm + op.cG.re * dg, op.cM.im * dm + op.cG.im * dg);
-    if (!NEED_AX) {
-        r.ax = cx<T>(0, 0);
-        return r;
-    }
-    const int ia[3] = {rx.lo, i, rx.hi};
-    const int jb[3] = {ry.lo, j, ry.hi};
-    const T myw[3] = {ry.ml, ry.mc, ry.mr};
-    const T kyw[3] = {ry.kl, ry.kc, ry.kr};
-    Cx<T> Mx = cx<T>(0, 0), Kx = cx<T>(0, 0), Fx = cx<T>(0, 0), mxc = cx<T>(0, 0);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        const long long row = (long long)jb[b] * nn;
-        const Cx<T> v0 = ld<T>(x, row + ia[0]);
-        const Cx<T> v1 = ld<T>(x, row + ia[1]);
-        const Cx<T> v2 = ld<T>(x, row + ia[2]);
-        Cx<T> mx = fma_r(rx.mr, v2, fma_r(rx.mc, v1, rx.ml * v0));
-        Cx<T> kx = fma_r(rx.kr, v2, fma_r(rx.kc, v1, rx.kl * v0));
-        Mx = fma_r(myw[b], mx, Mx);
-        Kx = fma_r(myw[b], kx, fma_r(kyw[b], mx, Kx));
-        Fx = fma_r(myw[b], v1, Fx);
-        if (b == 1) mxc = mx;
-    }
-    Cx<T> F = rx.face ? Fx : cx<T>(0, 0);
-    if (ry.face) F = F + mxc;
-    Cx<T> ax = op.cK * Kx;
-    ax = fma_c(op.cM, Mx, ax);
-    ax = fma_c(op.cG, F, ax);
-    r.ax = ax;
-    return r;
-}
-
-// (op x) and diag(op) at node (i,j,l) of a 3D grid.
-template <typename T, bool NEED_AX>
-__device__ __forceinline__ NodeResult<T> node3(const vec2<T>* __restrict__ x, int nn, int i, int j,
-                                               int l, const Row1<T>& rx, const Row1<T>& ry,
-                                               const Row1<T>& rz, const OpCoef<T>& op) {
-    NodeResult<T> r;
-    const T dr = op.cK * (rx.kc * ry.mc * rz.mc + rx.mc * ry.kc * rz.mc + rx.mc * ry.mc * rz.kc);
-    const T dm = rx.mc * ry.mc * rz.mc;
-    const T dg = (rx.face ? ry.mc * rz.mc : T(0)) + (ry.face ? rx.mc * rz.mc : T(0)) +
-                 (rz.face ? rx.mc * ry.mc : T(0));
-    r.d = cx<T>(dr + op.cM.re * dm + op.cG.re * dg, op.cM.im * dm + op.cG.im * dg);
-    if (!NEED_AX) {
-        r.ax = cx<T>(0, 0);
-        return r;
-    }
-    const int ia[3] = {rx.lo, i, rx.hi};
-    const int jb[3] = {ry.lo, j, ry.hi};
-    const int lc[3] = {rz.lo, l, rz.hi};
-    const T myw[3] = {ry.ml, ry.mc, ry.mr};
-    const T kyw[3] = {ry.kl, ry.kc, ry.kr};
-    const T mzw[3] = {rz.ml, rz.mc, rz.mr};
-    const T kzw[3] = {rz.kl, rz.kc, rz.kr};
-    Cx<T> Mx = cx<T>(0, 0), Kx = cx<T>(0, 0);
-    Cx<T> Fxf = cx<T>(0, 0), Fyf = cx<T>(0, 0), Fzf = cx<T>(0, 0);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        Cx<T> PM = cx<T>(0, 0), PK = cx<T>(0, 0), Pf = cx<T>(0, 0), mxc = cx<T>(0, 0);
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const long long row = ((long long)lc[c] * nn + jb[b]) * nn;
-            const Cx<T> v0 = ld<T>(x, row + ia[0]);
-            const Cx<T> v1 = ld<T>(x, row + ia[1]);
-            const Cx<T> v2 = ld<T>(x, row + ia[2]);
-            Cx<T> mx = fma_r(rx.mr, v2, fma_r(rx.mc, v1, rx.ml * v0));
-            Cx<T> kx = fma_r(rx.kr, v2, fma_r(rx.kc, v1, rx.kl * v0));
-            PM = fma_r(myw[b], mx, PM);
-            PK = fma_r(myw[b], kx, fma_r(kyw[b], mx, PK));
-            Pf = fma_r(myw[b], v1, Pf);
-            if (b == 1) mxc = mx;
-        }
-        Mx = fma_r(mzw[c], PM, Mx);
-        Kx = fma_r(mzw[c], PK, fma_r(kzw[c], PM, Kx));
-        Fxf = fma_r(mzw[c], Pf, Fxf);   // x-side face: (M_y x M_z) on the centre column
-        Fyf = fma_r(mzw[c], mxc, Fyf);  // y-side face: (M_x x M_z) on the centre row
-        if (c == 1) Fzf = PM;           // z-side face: (M_x x M_y) on the centre plane
-    }
-    Cx<T> F = cx<T>(0, 0);
-    if (rx.face) F = F + Fxf;
-    if (ry.face) F = F + Fyf;
-    if (rz.face) F = F + Fzf;
-    Cx<T> ax = op.cK * Kx;
-    ax = fma_c(op.cM, Mx, ax);
-    ax = fma_c(op.cG, F, ax);
-    r.ax = ax;
-    return r;
-}
+thread_local int g_use_pdl = 1;
 
 template <typename T, int MODE, bool XZERO>
 __device__ __forceinline__ Cx<T> epilogue(const NodeResult<T>& nr, const vec2<T>* __restrict__ x,
@@ -144,6 +41,7 @@ __global__ void __launch_bounds__(256) k_stencil2(GridDesc g, OpCoef<T> op, T h,
                                                   const vec2<T>* __restrict__ z,
                                                   vec2<T>* __restrict__ y, Cx<T> alpha,
                                                   Cx<T> beta, T omega) {
+    pdl_entry();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i > g.n || j > g.n) return;
@@ -165,6 +63,7 @@ __global__ void __launch_bounds__(256) k_stencil3(GridDesc g, OpCoef<T> op, T h,
                                                   const vec2<T>* __restrict__ z,
                                                   vec2<T>* __restrict__ y, Cx<T> alpha,
                                                   Cx<T> beta, T omega) {
+    pdl_entry();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int l = blockIdx.z;
@@ -183,17 +82,18 @@ __global__ void __launch_bounds__(256) k_stencil3(GridDesc g, OpCoef<T> op, T h,
 }
 
 template <typename T, int MODE, bool XZERO>
-static void launch_mode(const GridDesc& g, const OpCoef<T>& op, const vec2<T>* x, const vec2<T>* z,
+static cudaError_t launch_mode(const GridDesc& g, const OpCoef<T>& op, const vec2<T>* x, const vec2<T>* z,
                         vec2<T>* y, Cx<T> alpha, Cx<T> beta, T omega, cudaStream_t s) {
     const T h = T(g.h), ih = T(1.0 / g.h);
-    ++g_kernel_launches;
     dim3 blk(32, 8, 1);
     if (g.dim == 2) {
         dim3 grd((g.nn + 31) / 32, (g.nn + 7) / 8, 1);
-        k_stencil2<T, MODE, XZERO><<<grd, blk, 0, s>>>(g, op, h, ih, x, z, y, alpha, beta, omega);
+        return klaunch(k_stencil2<T, MODE, XZERO>, dim3(grd), dim3(blk), 0, s, 1, g, op, h, ih, x, z, y, alpha, beta,
+                       omega);
     } else {
         dim3 grd((g.nn + 31) / 32, (g.nn + 7) / 8, g.nn);
-        k_stencil3<T, MODE, XZERO><<<grd, blk, 0, s>>>(g, op, h, ih, x, z, y, alpha, beta, omega);
+        return klaunch(k_stencil3<T, MODE, XZERO>, dim3(grd), dim3(blk), 0, s, 1, g, op, h, ih, x, z, y, alpha, beta,
+                       omega);
     }
 }
 
@@ -204,15 +104,15 @@ cudaError_t launch_stencil(int mode, const GridDesc& g, const OpCoef<T>& op, con
     const bool xz = (x == nullptr);
     if (mode == MODE_APPLY) {
         if (xz) return cudaErrorInvalidValue;
-        launch_mode<T, MODE_APPLY, false>(g, op, x, z, y, alpha, beta, omega, s);
+        HH_KRET((launch_mode<T, MODE_APPLY, false>(g, op, x, z, y, alpha, beta, omega, s)));
     } else if (mode == MODE_AXPBY) {
-        if (xz) launch_mode<T, MODE_AXPBY, true>(g, op, x, z, y, alpha, beta, omega, s);
-        else launch_mode<T, MODE_AXPBY, false>(g, op, x, z, y, alpha, beta, omega, s);
+        if (xz) HH_KRET((launch_mode<T, MODE_AXPBY, true>(g, op, x, z, y, alpha, beta, omega, s)));
+        else HH_KRET((launch_mode<T, MODE_AXPBY, false>(g, op, x, z, y, alpha, beta, omega, s)));
     } else {
-        if (xz) launch_mode<T, MODE_JACOBI, true>(g, op, x, z, y, alpha, beta, omega, s);
-        else launch_mode<T, MODE_JACOBI, false>(g, op, x, z, y, alpha, beta, omega, s);
+        if (xz) HH_KRET((launch_mode<T, MODE_JACOBI, true>(g, op, x, z, y, alpha, beta, omega, s)));
+        else HH_KRET((launch_mode<T, MODE_JACOBI, false>(g, op, x, z, y, alpha, beta, omega, s)));
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- restriction
@@ -221,6 +121,7 @@ cudaError_t launch_stencil(int mode, const GridDesc& g, const OpCoef<T>& op, con
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict(GridDesc gc, const vec2<T>* __restrict__ rf,
                                                   vec2<T>* __restrict__ rc) {
+    pdl_entry();
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     const int L = blockIdx.z;
@@ -263,9 +164,8 @@ template <typename T>
 cudaError_t launch_restrict(const GridDesc& gc, const vec2<T>* rf, vec2<T>* rc, cudaStream_t s) {
     dim3 blk(32, 8, 1);
     dim3 grd((gc.nn + 31) / 32, (gc.nn + 7) / 8, gc.dim == 3 ? gc.nn : 1);
-    ++g_kernel_launches;
-    k_restrict<T><<<grd, blk, 0, s>>>(gc, rf, rc);
-    return cudaGetLastError();
+    HH_KRET(klaunch(k_restrict<T>, dim3(grd), dim3(blk), 0, s, 1, gc, rf, rc));
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -284,6 +184,7 @@ cudaError_t launch_residual_restrict(const GridDesc& gf, const GridDesc& gc, con
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong(GridDesc gf, const vec2<T>* __restrict__ ec,
                                                  vec2<T>* __restrict__ x) {
+    pdl_entry();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int l = blockIdx.z;
@@ -323,14 +224,14 @@ template <typename T>
 cudaError_t launch_prolong(const GridDesc& gf, const vec2<T>* ec, vec2<T>* x, cudaStream_t s) {
     dim3 blk(32, 8, 1);
     dim3 grd((gf.nn + 31) / 32, (gf.nn + 7) / 8, gf.dim == 3 ? gf.nn : 1);
-    ++g_kernel_launches;
-    k_prolong<T><<<grd, blk, 0, s>>>(gf, ec, x);
-    return cudaGetLastError();
+    HH_KRET(klaunch(k_prolong<T>, dim3(grd), dim3(blk), 0, s, 1, gf, ec, x));
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- elementwise
 template <typename T>
 __global__ void k_add(vec2<T>* __restrict__ x, const vec2<T>* __restrict__ e, long long N) {
+    pdl_entry();
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x)
         st<T>(x, p, ld<T>(x, p) + ld<T>(e, p));
@@ -345,12 +246,12 @@ static inline unsigned ew_blocks(long long N) {
 
 template <typename T>
 cudaError_t launch_add(vec2<T>* x, const vec2<T>* e, long long N, cudaStream_t s) {
-    ++g_kernel_launches;
-    k_add<T><<<ew_blocks(N), 256, 0, s>>>(x, e, N);
-    return cudaGetLastError();
+    HH_KRET(klaunch(k_add<T>, dim3(ew_blocks(N)), dim3(256), 0, s, 1, x, e, N));
+    return cudaSuccess;
 }
 
 __global__ void k_cast_d2f(const double2* __restrict__ a, float2* __restrict__ b, long long N) {
+    pdl_entry();
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
         double2 v = a[p];
@@ -358,6 +259,7 @@ __global__ void k_cast_d2f(const double2* __restrict__ a, float2* __restrict__ b
     }
 }
 __global__ void k_cast_f2d(const float2* __restrict__ a, double2* __restrict__ b, long long N) {
+    pdl_entry();
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
         float2 v = a[p];
@@ -366,17 +268,16 @@ __global__ void k_cast_f2d(const float2* __restrict__ a, double2* __restrict__ b
 }
 
 cudaError_t launch_cast_d2f(const double2* a, float2* b, long long N, cudaStream_t s) {
-    ++g_kernel_launches;
-    k_cast_d2f<<<ew_blocks(N), 256, 0, s>>>(a, b, N);
-    return cudaGetLastError();
+    HH_KRET(klaunch(k_cast_d2f, dim3(ew_blocks(N)), dim3(256), 0, s, 1, a, b, N));
+    return cudaSuccess;
 }
 cudaError_t launch_cast_f2d(const float2* a, double2* b, long long N, cudaStream_t s) {
-    ++g_kernel_launches;
-    k_cast_f2d<<<ew_blocks(N), 256, 0, s>>>(a, b, N);
-    return cudaGetLastError();
+    HH_KRET(klaunch(k_cast_f2d, dim3(ew_blocks(N)), dim3(256), 0, s, 1, a, b, N));
+    return cudaSuccess;
 }
 
 __global__ void k_mask_copy(GridDesc g, const double2* __restrict__ src, double2* __restrict__ dst) {
+    pdl_entry();
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.N;
          p += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(p % g.nn);
@@ -390,9 +291,8 @@ __global__ void k_mask_copy(GridDesc g, const double2* __restrict__ src, double2
 }
 
 cudaError_t launch_mask_copy(const GridDesc& g, const double2* src, double2* dst, cudaStream_t s) {
-    ++g_kernel_launches;
-    k_mask_copy<<<ew_blocks(g.N), 256, 0, s>>>(g, src, dst);
-    return cudaGetLastError();
+    HH_KRET(klaunch(k_mask_copy, dim3(ew_blocks(g.N)), dim3(256), 0, s, 1, g, src, dst));
+    return cudaSuccess;
 }
 
 #define HH_INSTANTIATE(T)                                                                          \
@@ -407,6 +307,7 @@ cudaError_t launch_mask_copy(const GridDesc& g, const double2* src, double2* dst
     template cudaError_t launch_prolong<T>(const GridDesc&, const vec2<T>*, vec2<T>*,              \
                                            cudaStream_t);                                          \
     template cudaError_t launch_add<T>(vec2<T>*, const vec2<T>*, long long, cudaStream_t);
+
 
 HH_INSTANTIATE(float)
 HH_INSTANTIATE(double)

@@ -121,6 +121,53 @@ def test_vcycle(case, prec):
     assert rel(x, prob.vcycle(0, b)) <= (1e-12 if prec == hh.HH_C128 else 2e-5)
 
 
+NU = [(2, 2, 8), (1, 1, 3), (3, 2, 0), (0, 1, 2), (2, 0, 5), (4, 3, 1)]
+
+
+@pytest.mark.parametrize("prec", [hh.HH_C128, hh.HH_C64])
+@pytest.mark.parametrize("nu", NU, ids=lambda v: "nu%d%d%d" % v)
+@pytest.mark.parametrize("dim,n,L,bc", [(2, 40, 4, (S, D, S, S)), (3, 8, 3, (S, S, D, S, S, S))])
+def test_vcycle_sweep_counts(libhh, prec, nu, dim, n, L, bc):
+    """Every pre/post/coarse sweep count takes a different fused-kernel path."""
+    g = O.Grid(dim, n, bc)
+    o = dict(levels=L, nu_pre=nu[0], nu_post=nu[1], nu_coarse=nu[2], omega=0.7)
+    prob = O.Problem(g, 5.0, 0.0, 3.0, O.Options(**o))
+    with hh.Problem(dim, n, 5.0, 0.0, 3.0, bc, hh.default_options(**o)) as p:
+        b = rand(g, 71)
+        x = to_np(p.vcycle(to_dev(b, prec)))
+    assert rel(x, prob.vcycle(0, b)) <= (1e-12 if prec == hh.HH_C128 else 2e-5)
+
+
+@pytest.mark.parametrize("prec", [hh.HH_C128, hh.HH_C64])
+@pytest.mark.parametrize("pdl,cluster", [(0, 0), (1, 0), (0, 20000), (1, 100000)])
+@pytest.mark.parametrize("dim,n,L,bc", [(2, 64, 4, (D, S, S, S)), (3, 16, 4, (S, S, S, S, D, S))])
+def test_vcycle_launch_modes(libhh, prec, pdl, cluster, dim, n, L, bc):
+    """Same V-cycle with and without programmatic launch and the cluster-resident bottom."""
+    g = O.Grid(dim, n, bc)
+    prob = O.Problem(g, 8.0, 0.0, 8.0, O.Options(levels=L))
+    opts = hh.default_options(levels=L, use_pdl=pdl, coarse_cluster_nodes=cluster)
+    with hh.Problem(dim, n, 8.0, 0.0, 8.0, bc, opts) as p:
+        b = rand(g, 72)
+        x = to_np(p.vcycle(to_dev(b, prec)))
+        x2 = to_np(p.vcycle(to_dev(b, prec)))
+    assert rel(x, prob.vcycle(0, b)) <= (1e-12 if prec == hh.HH_C128 else 2e-5)
+    assert np.array_equal(x, x2)  # deterministic
+
+
+@pytest.mark.parametrize("prec", [hh.HH_C128, hh.HH_C64])
+@pytest.mark.parametrize("nu", [(2, 2, 8), (0, 1, 2), (1, 0, 4)], ids=lambda v: "nu%d%d%d" % v)
+@pytest.mark.parametrize("cycles", [1, 2])
+def test_precondition_paths(libhh, prec, nu, cycles):
+    """HSS loop with and without the fused first sweep, one or two V-cycles per HSS step."""
+    g = O.Grid(2, 32, (S, S, S, D))
+    o = dict(levels=3, nu_pre=nu[0], nu_post=nu[1], nu_coarse=nu[2], cycles_per_hss=cycles)
+    prob = O.Problem(g, 4.5, 0.0, 2.0, O.Options(**o))
+    with hh.Problem(2, 32, 4.5, 0.0, 2.0, g.bc, hh.default_options(precision=prec, **o)) as p:
+        r = rand(g, 101)
+        z = to_np(p.precondition(to_dev(r, hh.HH_C128)))
+    assert rel(z, prob.prec(r)) <= (1e-11 if prec == hh.HH_C128 else 5e-5)
+
+
 @pytest.mark.parametrize("prec", [hh.HH_C128, hh.HH_C64])
 def test_hss_rhs(case, prec):
     g, prob, p = case
