@@ -190,6 +190,27 @@ HH_API hh_status hh_load_vector(hh_problem* p, const void* f, void* b);
 /* out[0] + i out[1] = x^H y over level-0 complex128 vectors (deterministic order).  Blocking. */
 HH_API hh_status hh_dot(hh_problem* p, const void* x, const void* y, double* out);
 
+/*
+ * ---- reduction without allocation ----
+ * out[i] = V_i^H w for i < nvec (complex128; V_i = V + i*ld entries, each of length n),
+ * the same deterministic multi-vector inner product that the outer Krylov iteration
+ * runs, but with its block partial sums in a fixed array compiled into the library
+ * (nvec <= 64; 304 KiB of device memory that every GPU loading the library holds until
+ * the process exits) instead of memory owned by an hh_problem.  It allocates nothing:
+ * for callers that must not call cudaMalloc at the point of use (a serving loop whose
+ * device memory is all in its own pool, a caller under a budget reserved up front) or
+ * that have no hh_problem.  The paper has no counterpart; it is a service of this library.
+ *   V, w, out: device pointers (16-byte aligned); out receives nvec complex128 values.
+ *   cuda_stream: stream to launch on (NULL = legacy default stream); non-blocking.
+ * Returns HH_ERR_INVALID (with a message in hh_last_error) for nvec outside 1..64, n < 0,
+ * ld < n or a null pointer, HH_ERR_CUDA if a launch fails.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU (different streams, no ordering between them) race.
+ */
+HH_API hh_status hh_multidot_noalloc(const void* V, long long ld, int nvec, const void* w, long long n,
+                                     void* out, void* cuda_stream);
+
 HH_API const char* hh_status_string(hh_status s);
 HH_API const char* hh_last_error(void);
 

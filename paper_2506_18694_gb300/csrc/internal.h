@@ -7,6 +7,9 @@
 
 namespace hh {
 
+// Message returned by hh_last_error() for the calling thread.
+void set_last_error(const char* msg);
+
 // Kernels launched by this thread through the launchers below (graph captures included).
 extern thread_local long long g_kernel_launches;
 // 1: launch with programmatic stream serialization (overlaps a kernel's launch with the

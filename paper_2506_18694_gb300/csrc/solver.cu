@@ -87,6 +87,10 @@ struct Hier {
 
 }  // namespace
 
+namespace hh {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace hh
+
 struct hh_problem {
     int device = 0;
     hh_grid grid{};

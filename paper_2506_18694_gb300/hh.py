@@ -25,7 +25,7 @@ EXPORTED = (
     "hh_options_default", "hh_footprint_bytes", "hh_create_problem", "hh_destroy", "hh_solve",
     "hh_solve_host", "hh_level_nodes", "hh_apply", "hh_jacobi", "hh_residual_restrict",
     "hh_prolong_correct", "hh_vcycle", "hh_hss_rhs", "hh_precondition", "hh_load_vector", "hh_dot",
-    "hh_status_string", "hh_last_error",
+    "hh_multidot_noalloc", "hh_status_string", "hh_last_error",
 )
 
 
@@ -90,6 +90,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "hh_precondition": (I, [P, P, P]),
         "hh_load_vector": (I, [P, P, P]),
         "hh_dot": (I, [P, P, P, ctypes.POINTER(ctypes.c_double)]),
+        "hh_multidot_noalloc": (I, [P, ctypes.c_longlong, I, P, ctypes.c_longlong, P, P]),
         "hh_status_string": (ctypes.c_char_p, [I]),
         "hh_last_error": (ctypes.c_char_p, []),
     }
