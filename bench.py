@@ -362,15 +362,17 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed):
                            "rel_residual": i64.rel_residual, "value": prob.nodes() * i64.vcycles / t64,
                            "mixed_vs_fp64_rel_diff": diff}
 
-    # the paper's delta_hat = 2 on the same grid and source (mixed precision)
+    # the paper's delta_hat = 2 on the same grid and source (mixed precision).  One
+    # V(2,2)-Jacobi cycle per HSS step is too inexact over ceil(k) = 80 steps (FGMRES
+    # stagnates); two cycles per step converge.
     w2 = inputs.workload(WORKLOAD, 2.0)
-    with hh.Problem(w2.dim, w2.n, w2.k, w2.delta, w2.delta_hat, w2.bc, hh.default_options()) as p2:
+    with hh.Problem(w2.dim, w2.n, w2.k, w2.delta, w2.delta_hat, w2.bc, hh.default_options(cycles_per_hss=2)) as p2:
         p2.solve(b, w.tol)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, i2 = p2.solve(b, w.tol)
         t2 = time.perf_counter() - t0
-    out["delta_hat_2"] = {"solve_ms": 1e3 * t2, "outer_its": i2.outer_its, "vcycles": i2.vcycles,
+    out["delta_hat_2"] = {"cycles_per_hss": 2, "solve_ms": 1e3 * t2, "outer_its": i2.outer_its, "vcycles": i2.vcycles,
                           "rel_residual": i2.rel_residual, "value": prob.nodes() * i2.vcycles / t2}
 
     # FP64 CPU oracle on a bounded sample of the same workload

@@ -98,8 +98,9 @@ typedef struct {
     int precision;       /* hh_precision of the V-cycles                                      */
     int use_graphs;      /* 1: replay each preconditioner application from a CUDA graph       */
     int use_pdl;         /* 1: programmatic dependent launch between consecutive kernels      */
-    int coarse_cluster_nodes; /* levels (below the finest) with at most this many nodes run  */
-                              /* together inside one thread-block cluster; 0 = never         */
+    int coarse_cluster_nodes; /* the coarsest level, if it has at most this many nodes and   */
+                              /* fits, runs all its sweeps in one thread-block cluster with  */
+                              /* the level in distributed shared memory; 0 = never           */
 } hh_options;
 
 typedef struct {
@@ -115,8 +116,8 @@ typedef struct {
 typedef struct hh_problem hh_problem;
 
 /* Defaults: theta 1, 4 levels, V(2,2), 8 coarse sweeps, omega 0.6, restart 30,
- * max_outer 1000, complex FP32 V-cycles, graphs and programmatic launch on, cluster
- * levels of at most 20000 nodes. */
+ * max_outer 1000, complex FP32 V-cycles, graphs and programmatic launch on,
+ * coarse_cluster_nodes 100000. */
 HH_API void hh_options_default(hh_options* opts);
 
 /* Device bytes a problem with this grid and these options allocates (0 if invalid). */

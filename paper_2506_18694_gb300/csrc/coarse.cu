@@ -1,10 +1,14 @@
-// Bottom of the V-cycle in one launch: the coarsest levels (a few thousand to a few
-// tens of thousands of nodes) run inside a single thread-block cluster.  Every phase
-// (a Jacobi sweep, a residual, a restriction, a prolongation) is spread over all the
-// cluster's CTAs and closed by a cluster barrier, whose release/acquire semantics make
-// the phase's global (L2-resident) writes visible to every CTA of the cluster.  This
-// replaces one grid-wide launch per phase, which on grids this small costs more than
-// the phase itself.
+// Coarsest multigrid level in one launch: all nu_coarse Jacobi sweeps from x = 0 run
+// inside one thread-block cluster with the level held in distributed shared memory.
+//
+// The grid is cut into slabs along its slowest axis (rows in 2D, z-planes in 3D); CTA r
+// of the cluster owns a contiguous run of slabs and keeps them, plus one halo slab on
+// each side, in two shared-memory buffers (ping-pong) next to its slabs of b.  A sweep
+// reads only the CTA's own shared memory; the CTA writes its first and last new slab
+// straight into the halo slots of its two neighbours (remote shared-memory stores), and
+// one cluster barrier (release/acquire at cluster scope) then makes every write of the
+// sweep visible.  A launch per sweep would cost far more than a sweep of a few thousand
+// nodes.
 #include <cooperative_groups.h>
 
 #include "internal.h"
@@ -14,236 +18,242 @@ namespace cg = cooperative_groups;
 
 namespace hh {
 
-template <typename T>
-struct NodeCtx {
-    int i, j, l;
-    Row1<T> rx, ry, rz;
-    bool masked;
+struct SlabPlan {
+    int per;        // slabs owned by each CTA (the last CTAs may own fewer or none)
+    long long S;    // nodes per slab
+    size_t smem;    // dynamic shared memory per CTA
 };
 
 template <typename T>
-__device__ __forceinline__ NodeCtx<T> node_ctx(const GridDesc& g, long long pl) {
-    NodeCtx<T> c;
-    const T h = T(g.h), ih = T(1.0 / g.h);
-    // levels handled here hold far fewer than 2^31 nodes: 32-bit index arithmetic
-    const unsigned p = (unsigned)pl, nn = (unsigned)g.nn;
-    const unsigned q = p / nn;
-    c.i = (int)(p - q * nn);
-    c.j = (int)(q % nn);
-    c.l = g.dim == 3 ? (int)(q / nn) : 0;
-    c.rx = row1<T>(c.i, g.n, g.dir[0], g.dir[1], h, ih);
-    c.ry = row1<T>(c.j, g.n, g.dir[2], g.dir[3], h, ih);
-    c.masked = c.rx.masked || c.ry.masked;
-    if (g.dim == 3) {
-        c.rz = row1<T>(c.l, g.n, g.dir[4], g.dir[5], h, ih);
-        c.masked = c.masked || c.rz.masked;
-    } else {
-        c.rz = c.rx;
-    }
-    return c;
+static SlabPlan slab_plan(const GridDesc& g, int cs) {
+    SlabPlan sp;
+    sp.per = (g.nn + cs - 1) / cs;
+    sp.S = g.dim == 3 ? (long long)g.nn * g.nn : g.nn;
+    // two iterate buffers with a halo slab on each side
+    sp.smem = (size_t)(2 * (sp.per + 2)) * sp.S * sizeof(vec2<T>);
+    return sp;
 }
 
-template <typename T, bool NEED>
-__device__ __forceinline__ NodeResult<T> eval(const GridDesc& g, const NodeCtx<T>& c, const vec2<T>* x,
-                                              const OpCoef<T>& op) {
-    return g.dim == 3 ? node3<T, NEED>(x, g.nn, c.i, c.j, c.l, c.rx, c.ry, c.rz, op)
-                      : node2<T, NEED>(x, g.nn, c.i, c.j, c.rx, c.ry, op);
-}
-
-// xout = xin + omega D^{-1} (b - A xin)   (xin == nullptr: xin = 0)
-template <typename T>
-__device__ void ph_sweep(const GridDesc& g, const OpCoef<T>& op, T omega, const vec2<T>* b, const vec2<T>* xin,
-                         vec2<T>* xout, long long tid, long long nthr) {
-    for (long long p = tid; p < g.N; p += nthr) {
-        const NodeCtx<T> c = node_ctx<T>(g, p);
-        if (c.masked) {
-            st<T>(xout, p, cx<T>(0, 0));
-            continue;
-        }
-        if (xin) {
-            const NodeResult<T> r = eval<T, true>(g, c, xin, op);
-            st<T>(xout, p, fma_c(cinv(r.d), omega * (ld<T>(b, p) - r.ax), ld<T>(xin, p)));
-        } else {
-            const NodeResult<T> r = eval<T, false>(g, c, nullptr, op);
-            st<T>(xout, p, omega * cmul(cinv(r.d), ld<T>(b, p)));
-        }
-    }
-}
+// Interior weights of the coarsest operator (all neighbours are interior nodes): 2D
+// centre, edge, diagonal; 3D centre, face, edge, corner neighbours.  Filled on the host.
+template <typename T> struct CoarseW {
+    Cx<T> w[4];
+    Cx<T> dinv;  // omega / interior diagonal
+};
 
 template <typename T>
-__device__ void ph_residual(const GridDesc& g, const OpCoef<T>& op, const vec2<T>* b, const vec2<T>* x,
-                            vec2<T>* r, long long tid, long long nthr) {
-    for (long long p = tid; p < g.N; p += nthr) {
-        const NodeCtx<T> c = node_ctx<T>(g, p);
-        if (c.masked) {
-            st<T>(r, p, cx<T>(0, 0));
-            continue;
-        }
-        st<T>(r, p, ld<T>(b, p) - eval<T, true>(g, c, x, op).ax);
-    }
-}
-
-// bc = P^T r (full weighting) on the coarse grid gc
-template <typename T>
-__device__ void ph_restrict(const GridDesc& gc, const vec2<T>* r, vec2<T>* bc, long long tid, long long nthr) {
-    const int nf = 2 * gc.n, nnf = nf + 1;
-    const bool d3 = gc.dim == 3;
-    for (long long p = tid; p < gc.N; p += nthr) {
-        const NodeCtx<T> c = node_ctx<T>(gc, p);
-        if (c.masked) {
-            st<T>(bc, p, cx<T>(0, 0));
-            continue;
-        }
-        Cx<T> acc = cx<T>(0, 0);
-        for (int dz = d3 ? -1 : 0; dz <= (d3 ? 1 : 0); ++dz) {
-            const int fl = 2 * c.l + dz;
-            if (fl < 0 || fl > nf) continue;
-            const T wz = dz == 0 ? T(1) : T(0.5);
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int fj = 2 * c.j + dy;
-                if (fj < 0 || fj > nf) continue;
-                const T wy = dy == 0 ? wz : T(0.5) * wz;
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int fi = 2 * c.i + dx;
-                    if (fi < 0 || fi > nf) continue;
-                    const T w = dx == 0 ? wy : T(0.5) * wy;
-                    acc = fma_r(w, ld<T>(r, ((long long)(d3 ? fl : 0) * nnf + fj) * nnf + fi), acc);
-                }
-            }
-        }
-        st<T>(bc, p, acc);
-    }
-}
-
-// x += P e (e on the coarse grid of gf)
-template <typename T>
-__device__ void ph_prolong(const GridDesc& gf, const vec2<T>* e, vec2<T>* x, long long tid, long long nthr) {
-    const int nc = gf.n / 2, nnc = nc + 1;
-    const bool d3 = gf.dim == 3;
-    for (long long p = tid; p < gf.N; p += nthr) {
-        const NodeCtx<T> c = node_ctx<T>(gf, p);
-        if (c.masked) {
-            st<T>(x, p, cx<T>(0, 0));
-            continue;
-        }
-        const int I0 = c.i >> 1, J0 = c.j >> 1, L0 = c.l >> 1;
-        const int ni = (c.i & 1) ? 2 : 1, nj = (c.j & 1) ? 2 : 1, nl = (d3 && (c.l & 1)) ? 2 : 1;
-        const T w = ((c.i & 1) ? T(0.5) : T(1)) * ((c.j & 1) ? T(0.5) : T(1)) *
-                    ((d3 && (c.l & 1)) ? T(0.5) : T(1));
-        Cx<T> acc = cx<T>(0, 0);
-        for (int dz = 0; dz < nl; ++dz) {
-            const int L = L0 + dz;
-            if (d3 && ((L == 0 && gf.dir[4]) || (L == nc && gf.dir[5]))) continue;
-            for (int dy = 0; dy < nj; ++dy) {
-                const int J = J0 + dy;
-                if ((J == 0 && gf.dir[2]) || (J == nc && gf.dir[3])) continue;
-                for (int dx = 0; dx < ni; ++dx) {
-                    const int I = I0 + dx;
-                    if ((I == 0 && gf.dir[0]) || (I == nc && gf.dir[1])) continue;
-                    acc = fma_r(w, ld<T>(e, ((long long)(d3 ? L : 0) * nnc + J) * nnc + I), acc);
-                }
-            }
-        }
-        st<T>(x, p, ld<T>(x, p) + acc);
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kClusterThreads) k_coarse_cluster(CoarseArgs<T> a) {
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem(GridDesc g, OpCoef<T> op, CoarseW<T> cw,
+                                                                 const vec2<T>* __restrict__ b,
+                                                                 vec2<T>* __restrict__ xout, int nsweeps, T omega,
+                                                                 int per) {
     pdl_entry();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cl = cg::this_cluster();
-    const long long nthr = (long long)blockDim.x * gridDim.x;  // the grid is one cluster
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    vec2<T>* cur[kMaxClusterLevels];
-    // down: pre-smoothing, residual, restriction; the last level is smoothed from zero
-    for (int lv = 0; lv < a.nlev; ++lv) {
-        const GridDesc& g = a.g[lv];
-        const bool coarsest = lv == a.nlev - 1;
-        const int nsw = coarsest ? a.nu_coarse : a.nu_pre;
-        vec2<T>* x = a.xa[lv];
-        vec2<T>* o = a.xb[lv];
-        if (nsw == 0) {
-            for (long long p = tid; p < g.N; p += nthr) st<T>(x, p, cx<T>(0, 0));
-            cl.sync();
+    const int rank = (int)cl.block_rank();
+    const int nn = g.nn, n = g.n;
+    const bool d3 = g.dim == 3;
+    const long long S = d3 ? (long long)nn * nn : nn;
+    const int r0 = min(rank * per, nn);
+    const int r1 = min(r0 + per, nn);
+    const int own = (r1 - r0) * (int)S;               // owned nodes (at most kCoarseNodesPerThread per thread)
+    const long long buf = (long long)(per + 2) * S;   // one iterate buffer, halos included
+    vec2<T>* xs[2] = {reinterpret_cast<vec2<T>*>(smem_raw), reinterpret_cast<vec2<T>*>(smem_raw) + buf};
+    const T h = T(g.h), ih = T(1.0 / g.h);
+    const long long off = (long long)(r0 - 1) * S;    // global node number of local index 0
+
+    // per owned node, once: coordinates, class, b and omega D^{-1}
+    constexpr int K = kCoarseNodesPerThread;
+    int ii[K], jj[K], ll[K];
+    unsigned char cls[K];  // 0 masked, 1 interior (fast), 2 boundary (general)
+    Cx<T> bq[K], dw[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int q = threadIdx.x + k * blockDim.x;
+        cls[k] = 0;
+        ii[k] = jj[k] = ll[k] = 0;
+        bq[k] = dw[k] = cx<T>(0, 0);
+        if (q >= own) continue;
+        const unsigned pu = (unsigned)((long long)r0 * S + q), nnu = (unsigned)nn, qq = pu / nnu;
+        ii[k] = (int)(pu - qq * nnu);
+        jj[k] = (int)(qq % nnu);
+        ll[k] = d3 ? (int)(qq / nnu) : 0;
+        const Row1<T> rx = row1<T>(ii[k], n, g.dir[0], g.dir[1], h, ih);
+        const Row1<T> ry = row1<T>(jj[k], n, g.dir[2], g.dir[3], h, ih);
+        Row1<T> rz = rx;
+        bool masked = rx.masked || ry.masked;
+        if (d3) {
+            rz = row1<T>(ll[k], n, g.dir[4], g.dir[5], h, ih);
+            masked = masked || rz.masked;
         }
-        for (int s = 0; s < nsw; ++s) {
-            if (s == 0) {
-                ph_sweep<T>(g, a.op, a.omega, a.b[lv], nullptr, x, tid, nthr);
-            } else {
-                ph_sweep<T>(g, a.op, a.omega, a.b[lv], x, o, tid, nthr);
-                vec2<T>* t = x;
-                x = o;
-                o = t;
+        if (masked) continue;
+        const bool fast = ii[k] >= 2 && ii[k] <= n - 2 && jj[k] >= 2 && jj[k] <= n - 2 &&
+                          (!d3 || (ll[k] >= 2 && ll[k] <= n - 2));
+        cls[k] = fast ? 1 : 2;
+        bq[k] = ld<T>(b, (long long)r0 * S + q);
+        if (fast) {
+            dw[k] = cw.dinv;
+        } else {
+            const NodeResult<T> r = d3 ? node3<T, false>(xs[0], nn, ii[k], jj[k], ll[k], rx, ry, rz, op, off)
+                                       : node2<T, false>(xs[0], nn, ii[k], jj[k], rx, ry, op, off);
+            dw[k] = omega * cinv(r.d);
+        }
+    }
+    int cur = 0;
+    for (int s = 0; s < nsweeps; ++s) {
+        const vec2<T>* __restrict__ xc = xs[cur];
+        vec2<T>* xn = xs[cur ^ 1];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int q = threadIdx.x + k * blockDim.x;
+            if (q >= own) continue;
+            const long long lq = q + S;  // local index of the node
+            Cx<T> xv = cx<T>(0, 0);
+            if (cls[k] != 0) {
+                if (s == 0) {
+                    xv = cmul(dw[k], bq[k]);
+                } else {
+                    Cx<T> ax;
+                    if (cls[k] == 1) {
+                        if (!d3) {
+                            const Cx<T> e = (ld<T>(xc, lq - 1) + ld<T>(xc, lq + 1)) +
+                                            (ld<T>(xc, lq - nn) + ld<T>(xc, lq + nn));
+                            const Cx<T> dg = (ld<T>(xc, lq - nn - 1) + ld<T>(xc, lq - nn + 1)) +
+                                             (ld<T>(xc, lq + nn - 1) + ld<T>(xc, lq + nn + 1));
+                            ax = fma_c(cw.w[2], dg, fma_c(cw.w[1], e, cmul(cw.w[0], ld<T>(xc, lq))));
+                        } else {
+                            // neighbours grouped by how many coordinates differ: 6 faces, 12 edges, 8 corners
+                            Cx<T> fa = cx<T>(0, 0), ed = cx<T>(0, 0), co = cx<T>(0, 0);
+#pragma unroll
+                            for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+                                for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                                    for (int dx = -1; dx <= 1; ++dx) {
+                                        const int m = (dx != 0) + (dy != 0) + (dz != 0);
+                                        if (m == 0) continue;
+                                        const Cx<T> v = ld<T>(xc, lq + ((long long)dz * nn + dy) * nn + dx);
+                                        if (m == 1) fa = fa + v;
+                                        else if (m == 2) ed = ed + v;
+                                        else co = co + v;
+                                    }
+                            ax = fma_c(cw.w[3], co, fma_c(cw.w[2], ed, fma_c(cw.w[1], fa, cmul(cw.w[0], ld<T>(xc, lq)))));
+                        }
+                    } else {
+                        const Row1<T> rx = row1<T>(ii[k], n, g.dir[0], g.dir[1], h, ih);
+                        const Row1<T> ry = row1<T>(jj[k], n, g.dir[2], g.dir[3], h, ih);
+                        if (d3) {
+                            const Row1<T> rz = row1<T>(ll[k], n, g.dir[4], g.dir[5], h, ih);
+                            ax = node3<T, true>(xc, nn, ii[k], jj[k], ll[k], rx, ry, rz, op, off).ax;
+                        } else {
+                            ax = node2<T, true>(xc, nn, ii[k], jj[k], rx, ry, op, off).ax;
+                        }
+                    }
+                    xv = fma_c(dw[k], bq[k] - ax, ld<T>(xc, lq));
+                }
             }
-            cl.sync();
+            st<T>(xn, lq, xv);
+            // boundary slabs also go to the neighbours' halo slots of the same buffer
+            if (q < S && rank > 0) st<T>(cl.map_shared_rank(xn, rank - 1), (long long)(per + 1) * S + q, xv);
+            if (q >= own - S && r1 < nn) st<T>(cl.map_shared_rank(xn, rank + 1), q - (own - S), xv);
         }
-        cur[lv] = x;
-        if (!coarsest) {
-            ph_residual<T>(g, a.op, a.b[lv], x, a.t[lv], tid, nthr);
-            cl.sync();
-            ph_restrict<T>(a.g[lv + 1], a.t[lv], a.b[lv + 1], tid, nthr);
-            cl.sync();
-        }
-    }
-    // up: prolongation of the correction, post-smoothing
-    for (int lv = a.nlev - 2; lv >= 0; --lv) {
-        const GridDesc& g = a.g[lv];
-        vec2<T>* x = cur[lv];
-        vec2<T>* o = (x == a.xa[lv]) ? a.xb[lv] : a.xa[lv];
-        ph_prolong<T>(g, cur[lv + 1], x, tid, nthr);
         cl.sync();
-        for (int s = 0; s < a.nu_post; ++s) {
-            ph_sweep<T>(g, a.op, a.omega, a.b[lv], x, o, tid, nthr);
-            vec2<T>* t = x;
-            x = o;
-            o = t;
-            cl.sync();
-        }
-        cur[lv] = x;
+        cur ^= 1;
     }
-    // the result of the top level always ends in xa[0]
-    if (cur[0] != a.xa[0])
-        for (long long p = tid; p < a.g[0].N; p += nthr) a.xa[0][p] = cur[0][p];
+    for (int q = threadIdx.x; q < own; q += blockDim.x) xout[(long long)r0 * S + q] = xs[cur][q + S];
 }
 
-template <typename T>
-int cluster_size_for() {
-    static int cached = 0;
-    if (cached) return cached;
-    cudaFuncSetAttribute(k_coarse_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+static int g_cluster_size = 0;
+
+int coarse_cluster_size() {
+    if (g_cluster_size) return g_cluster_size;
+    cudaFuncSetAttribute(k_coarse_dsmem<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_coarse_dsmem<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaGetLastError();
-    for (int cs : {16, 8, 4, 2, 1}) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(cs, 1, 1);
-        cfg.blockDim = dim3(kClusterThreads, 1, 1);
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = cs;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_cluster<T>, &cfg) == cudaSuccess && nclusters > 0) {
-            cached = cs;
-            return cs;
-        }
-        cudaGetLastError();
+    for (int cs : {16, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(kCoarseThreads, 1, 1);
+    cfg.dynamicSmemBytes = kCoarseSmemMax;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_dsmem<float>, &cfg) == cudaSuccess && nclusters >= 1) {
+        g_cluster_size = cs;
+        return cs;
     }
-    cached = 1;
+    cudaGetLastError();
+    }
+    g_cluster_size = 1;
     return 1;
 }
 
 template <typename T>
-cudaError_t launch_coarse_cluster(const CoarseArgs<T>& a, cudaStream_t s) {
-    if (a.nlev < 1 || a.nlev > kMaxClusterLevels) return cudaErrorInvalidValue;
-    const int cs = cluster_size_for<T>();
-    return klaunch(k_coarse_cluster<T>, dim3(cs), dim3(kClusterThreads), 0, s, cs, a);
+bool coarse_fits(const GridDesc& g) {
+    const SlabPlan sp = slab_plan<T>(g, coarse_cluster_size());
+    return sp.smem <= kCoarseSmemMax && (long long)sp.per * sp.S <= (long long)kCoarseNodesPerThread * kCoarseThreads;
 }
 
-template int cluster_size_for<float>();
-template int cluster_size_for<double>();
-template cudaError_t launch_coarse_cluster<float>(const CoarseArgs<float>&, cudaStream_t);
-template cudaError_t launch_coarse_cluster<double>(const CoarseArgs<double>&, cudaStream_t);
+template <typename T>
+static CoarseW<T> coarse_weights(const GridDesc& g, const OpCoef<T>& op, T omega) {
+    // interior Q1 weights: stiffness and mass of the centre and of each neighbour class
+    double kw[4], mw[4];
+    const double h = g.h;
+    if (g.dim == 2) {
+        const double k2[4] = {8.0 / 3.0, -1.0 / 3.0, -1.0 / 3.0, 0.0};
+        const double m2[4] = {16.0 / 36.0, 4.0 / 36.0, 1.0 / 36.0, 0.0};
+        for (int c = 0; c < 4; ++c) {
+            kw[c] = k2[c];
+            mw[c] = m2[c] * h * h;
+        }
+    } else {
+        const double k3[4] = {8.0 / 3.0, 0.0, -1.0 / 6.0, -1.0 / 12.0};
+        const double m3[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
+        for (int c = 0; c < 4; ++c) {
+            kw[c] = k3[c] * h;
+            mw[c] = m3[c] * h * h * h;
+        }
+    }
+    CoarseW<T> cw;
+    for (int c = 0; c < 4; ++c)
+        cw.w[c] = cx<T>(T(double(op.cK) * kw[c] + double(op.cM.re) * mw[c]), T(double(op.cM.im) * mw[c]));
+    const double dr = double(op.cK) * kw[0] + double(op.cM.re) * mw[0], di = double(op.cM.im) * mw[0];
+    const double d2 = dr * dr + di * di;
+    cw.dinv = cx<T>(T(double(omega) * dr / d2), T(-double(omega) * di / d2));
+    return cw;
+}
+
+template <typename T>
+cudaError_t prepare_coarse() {
+    cudaError_t e = cudaFuncSetAttribute(k_coarse_dsmem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kCoarseSmemMax);
+    if (e != cudaSuccess) return e;
+    coarse_cluster_size();
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_coarse_solve(const GridDesc& g, const OpCoef<T>& op, const vec2<T>* b, vec2<T>* x, int nsweeps,
+                                T omega, cudaStream_t s) {
+    const int cs = coarse_cluster_size();
+    const SlabPlan sp = slab_plan<T>(g, cs);
+    if (sp.smem > kCoarseSmemMax || nsweeps < 1) return cudaErrorInvalidValue;
+    if ((long long)sp.per * sp.S > (long long)kCoarseNodesPerThread * kCoarseThreads) return cudaErrorInvalidValue;
+    return klaunch(k_coarse_dsmem<T>, dim3(cs), dim3(kCoarseThreads), sp.smem, s, cs, g, op,
+                   coarse_weights<T>(g, op, omega), b, x, nsweeps, omega, sp.per);
+}
+
+template bool coarse_fits<float>(const GridDesc&);
+template bool coarse_fits<double>(const GridDesc&);
+template cudaError_t prepare_coarse<float>();
+template cudaError_t prepare_coarse<double>();
+template cudaError_t launch_coarse_solve<float>(const GridDesc&, const OpCoef<float>&, const float2*, float2*, int,
+                                                float, cudaStream_t);
+template cudaError_t launch_coarse_solve<double>(const GridDesc&, const OpCoef<double>&, const double2*, double2*,
+                                                 int, double, cudaStream_t);
 
 }  // namespace hh

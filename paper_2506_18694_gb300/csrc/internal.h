@@ -80,27 +80,23 @@ cudaError_t launch_prolong(const GridDesc& gf, const vec2<T>* ec, vec2<T>* x, cu
 template <typename T>
 cudaError_t launch_add(vec2<T>* x, const vec2<T>* e, long long N, cudaStream_t s);
 
-// ---- bottom of the V-cycle inside one thread-block cluster (coarse.cu) ----
-constexpr int kMaxClusterLevels = 4;
-constexpr int kClusterThreads = 512;
+// ---- coarsest level inside one thread-block cluster, in distributed shared memory (coarse.cu) ----
+constexpr int kCoarseThreads = 512;
+constexpr int kCoarseNodesPerThread = 2;
+constexpr size_t kCoarseSmemMax = 200 * 1024;
 
-template <typename T> struct CoarseArgs {
-    int nlev;                           // levels handled; the last one is the coarsest
-    GridDesc g[kMaxClusterLevels];
-    vec2<T>* b[kMaxClusterLevels];      // right sides (b[0] given, the others restricted)
-    vec2<T>* xa[kMaxClusterLevels];     // iterates (ping-pong); the result ends in xa[0]
-    vec2<T>* xb[kMaxClusterLevels];
-    vec2<T>* t[kMaxClusterLevels];      // residual scratch
-    OpCoef<T> op;
-    T omega;
-    int nu_pre, nu_post, nu_coarse;
-};
-
+// CTAs per cluster (16 or 8 when the device can co-schedule them, else 1)
+int coarse_cluster_size();
+// whether a grid's slabs fit the shared memory of the cluster's CTAs
 template <typename T>
-cudaError_t launch_coarse_cluster(const CoarseArgs<T>& a, cudaStream_t s);
-// CTAs per cluster used by launch_coarse_cluster (queried once; call before stream capture)
+bool coarse_fits(const GridDesc& g);
+// one-time set-up (shared-memory limit, cluster query); call before any stream capture
 template <typename T>
-int cluster_size_for();
+cudaError_t prepare_coarse();
+// nsweeps scaled-Jacobi sweeps on A x = b from x = 0
+template <typename T>
+cudaError_t launch_coarse_solve(const GridDesc& g, const OpCoef<T>& op, const vec2<T>* b, vec2<T>* x, int nsweeps,
+                                T omega, cudaStream_t s);
 
 // ---- fused 2D marching kernels (march2.cu) ----
 enum MarchMode {
@@ -129,6 +125,8 @@ template <typename T> struct MArgs {
     // filled by the launcher
     T h, ih;
     int rows;
+    Cx<T> wc, we, wd;    // interior stencil weights of op: centre, edge, diagonal neighbours
+    Cx<T> wdinv;         // omega / (interior diagonal of opd)
 };
 
 template <typename T>

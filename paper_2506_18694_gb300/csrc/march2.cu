@@ -37,9 +37,10 @@ __device__ __forceinline__ Cx<T> field2(const MArgs<T>& a, int ic, int rc, const
     const long long p = (long long)rc * a.g.nn + ic;
     if (MODE == M_JACOBI2_ZERO) {
         // first sweep from x = 0: x1 = omega D^{-1} b (zero at Dirichlet nodes)
-        const Row1<T> ry = row1<T>(rc, a.g.n, a.g.dir[2], a.g.dir[3], h, ih);
         const Cx<T> b = ld<T>(a.z, p);
         *bval = b;
+        if (ic >= 1 && ic <= a.g.n - 1 && rc >= 1 && rc <= a.g.n - 1) return cmul(a.wdinv, b);
+        const Row1<T> ry = row1<T>(rc, a.g.n, a.g.dir[2], a.g.dir[3], h, ih);
         if (rx.masked || ry.masked) return cx<T>(0, 0);
         return a.omega * cmul(cinv(diag2(rx, ry, a.op)), b);
     } else if (MODE == M_PROLONG_JACOBI) {
@@ -75,7 +76,10 @@ __device__ __forceinline__ Cx<T> field2(const MArgs<T>& a, int ic, int rc, const
 // One warp: a strip of 30 output columns (lanes 1..30; lanes 0 and 31 are the halo) and
 // ROWS consecutive output rows (RESID_RESTRICT: ROWS coarse rows, 2 ROWS + 1 residual
 // rows, 28 fine columns per strip).  All stencil rows of the chunk are loaded before any
-// arithmetic so that every load of the warp is in flight at once.
+// arithmetic so that every load of the warp is in flight at once.  Nodes at least two
+// cells away from the boundary (none of their neighbours is a boundary node) use the
+// three interior weights of the operator (centre, edge, diagonal) and the interior
+// diagonal; the rest build their row from the 1D weight triples.
 template <typename T, int MODE, int ROWS>
 __global__ void __launch_bounds__(128) k_march2(MArgs<T> a) {
     pdl_entry();
@@ -94,6 +98,7 @@ __global__ void __launch_bounds__(128) k_march2(MArgs<T> a) {
     const int rfirst = RR ? 2 * base - 2 : base - 1;
     const int ic = clampi(i, 0, n);
     const bool col_in = (i >= 0 && i <= n);
+    const bool col_fast = (i >= 2 && i <= n - 2);
     const Row1<T> rx = row1<T>(ic, n, a.g.dir[0], a.g.dir[1], h, ih);
 
     Cx<T> fv[NR], bv[NR], zv[NZ];
@@ -106,12 +111,11 @@ __global__ void __launch_bounds__(128) k_march2(MArgs<T> a) {
     for (int t = 0; t < NZ; ++t)
         zv[t] = NEEDZ ? ld<T>(a.z, (long long)clampi(rfirst + 1 + t, 0, n) * a.g.nn + ic) : cx<T>(0, 0);
 
-    Cx<T> mx[NR], kx[NR];
+    Cx<T> lf[NR], rg[NR];
 #pragma unroll
     for (int t = 0; t < NR; ++t) {
-        const Cx<T> lft = shfl_up(fv[t]), rgt = shfl_dn(fv[t]);
-        mx[t] = fma_r(rx.mr, rgt, fma_r(rx.mc, fv[t], rx.ml * lft));
-        kx[t] = fma_r(rx.kr, rgt, fma_r(rx.kc, fv[t], rx.kl * lft));
+        lf[t] = shfl_up(fv[t]);
+        rg[t] = shfl_dn(fv[t]);
     }
 
     Cx<T> acc = cx<T>(0, 0);  // restriction accumulator of the coarse row in progress
@@ -119,19 +123,38 @@ __global__ void __launch_bounds__(128) k_march2(MArgs<T> a) {
     for (int t = 1; t < NR - 1; ++t) {
         const int j = rfirst + t;
         const bool row_in = (j >= 0 && j <= n);
+        const bool fast = col_fast && j >= 2 && j <= n - 2;
         const int jc = clampi(j, 0, n);
-        const Row1<T> ry = row1<T>(jc, n, a.g.dir[2], a.g.dir[3], h, ih);
-        Cx<T> Mx = fma_r(ry.mr, mx[t + 1], fma_r(ry.mc, mx[t], ry.ml * mx[t - 1]));
-        Cx<T> Kx = fma_r(ry.mr, kx[t + 1], fma_r(ry.mc, kx[t], ry.ml * kx[t - 1]));
-        Kx = fma_r(ry.kr, mx[t + 1], fma_r(ry.kc, mx[t], fma_r(ry.kl, mx[t - 1], Kx)));
-        Cx<T> F = cx<T>(0, 0);
-        if (rx.face) F = fma_r(ry.mr, fv[t + 1], fma_r(ry.mc, fv[t], ry.ml * fv[t - 1]));
-        if (ry.face) F = F + mx[t];
-        Cx<T> ax = a.op.cK * Kx;
-        ax = fma_c(a.op.cM, Mx, ax);
-        ax = fma_c(a.op.cG, F, ax);
-        const bool masked = rx.masked || ry.masked;
         const long long p = (long long)jc * a.g.nn + ic;
+        Cx<T> ax;
+        Cx<T> dinv_w;  // omega D^{-1} of opd at the node
+        bool masked = false;
+        if (fast) {
+            const Cx<T> edge = (lf[t] + rg[t]) + (fv[t - 1] + fv[t + 1]);
+            const Cx<T> diag = (lf[t - 1] + rg[t - 1]) + (lf[t + 1] + rg[t + 1]);
+            ax = fma_c(a.wd, diag, fma_c(a.we, edge, cmul(a.wc, fv[t])));
+            dinv_w = a.wdinv;
+        } else {
+            const Row1<T> ry = row1<T>(jc, n, a.g.dir[2], a.g.dir[3], h, ih);
+            Cx<T> mx[3], kx[3];
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                mx[u] = fma_r(rx.mr, rg[t - 1 + u], fma_r(rx.mc, fv[t - 1 + u], rx.ml * lf[t - 1 + u]));
+                kx[u] = fma_r(rx.kr, rg[t - 1 + u], fma_r(rx.kc, fv[t - 1 + u], rx.kl * lf[t - 1 + u]));
+            }
+            Cx<T> Mx = fma_r(ry.mr, mx[2], fma_r(ry.mc, mx[1], ry.ml * mx[0]));
+            Cx<T> Kx = fma_r(ry.mr, kx[2], fma_r(ry.mc, kx[1], ry.ml * kx[0]));
+            Kx = fma_r(ry.kr, mx[2], fma_r(ry.kc, mx[1], fma_r(ry.kl, mx[0], Kx)));
+            Cx<T> F = cx<T>(0, 0);
+            if (rx.face) F = fma_r(ry.mr, fv[t + 1], fma_r(ry.mc, fv[t], ry.ml * fv[t - 1]));
+            if (ry.face) F = F + mx[1];
+            ax = a.op.cK * Kx;
+            ax = fma_c(a.op.cM, Mx, ax);
+            ax = fma_c(a.op.cG, F, ax);
+            masked = rx.masked || ry.masked;
+            dinv_w = (MODE == M_APPLY || MODE == M_AXPBY || RR) ? cx<T>(0, 0)
+                                                                 : a.omega * cinv(diag2(rx, ry, a.opd));
+        }
         if (RR) {
             const Cx<T> res = (row_in && col_in && !masked) ? zv[t - 1] - ax : cx<T>(0, 0);
             // full weighting along x: r(i) + (r(i-1) + r(i+1)) / 2
@@ -166,21 +189,44 @@ __global__ void __launch_bounds__(128) k_march2(MArgs<T> a) {
         } else if (MODE == M_HSS_FIRST) {
             const Cx<T> rhs = fma_c(a.alpha, ax, cmul(a.beta, zv[t - 1]));
             st<T>(a.y, p, rhs);
-            st<T>(a.y2, p, a.omega * cmul(cinv(diag2(rx, ry, a.opd)), rhs));
+            st<T>(a.y2, p, cmul(dinv_w, rhs));
         } else {
             // Jacobi update of the field: field + omega D^{-1} (b - op field)
             const Cx<T> b = (MODE == M_JACOBI2_ZERO) ? bv[t] : zv[t - 1];
-            const Cx<T> d = diag2(rx, ry, a.op);
-            st<T>(a.y, p, fma_c(cinv(d), a.omega * (b - ax), fv[t]));
+            st<T>(a.y, p, fma_c(dinv_w, b - ax, fv[t]));
         }
     }
 }
 
 // Rows per warp: the largest that still leaves about 24 warps per SM (loads in flight).
+// Interior stencil weights of op (Q1 on a uniform square grid: stiffness 8/3, -1/3, -1/3
+// and mass h^2/36 x (16, 4, 1) for the centre, edge and diagonal neighbours) and
+// omega / (interior diagonal of opd), computed in double precision.
+template <typename T>
+static void interior_weights(MArgs<T>& a) {
+    const double h2 = a.g.h * a.g.h;
+    auto w = [&](const OpCoef<T>& o, double kw, double mw, double* re, double* im) {
+        *re = double(o.cK) * kw + double(o.cM.re) * mw * h2;
+        *im = double(o.cM.im) * mw * h2;
+    };
+    double r, im;
+    w(a.op, 8.0 / 3.0, 16.0 / 36.0, &r, &im);
+    a.wc = cx<T>(T(r), T(im));
+    w(a.op, -1.0 / 3.0, 4.0 / 36.0, &r, &im);
+    a.we = cx<T>(T(r), T(im));
+    w(a.op, -1.0 / 3.0, 1.0 / 36.0, &r, &im);
+    a.wd = cx<T>(T(r), T(im));
+    w(a.opd, 8.0 / 3.0, 16.0 / 36.0, &r, &im);
+    const double d2 = r * r + im * im;
+    const double om = double(a.omega);
+    a.wdinv = d2 > 0 ? cx<T>(T(om * r / d2), T(-om * im / d2)) : cx<T>(T(0), T(0));
+}
+
 template <typename T, int MODE>
 static cudaError_t go2(MArgs<T> a, cudaStream_t s) {
     a.h = T(a.g.h);
     a.ih = T(1.0 / a.g.h);
+    interior_weights(a);
     const long long want = 152LL * 24;
     if constexpr (MODE == M_RESID_RESTRICT) {
         const int nnc = a.g.n / 2 + 1;

@@ -12,10 +12,11 @@ template <typename T> struct NodeResult {
 };
 
 // (op x) and diag(op) at node (i,j) of a 2D grid; rows rx, ry precomputed.
+// x is indexed by global node number minus `off` (a slab window of the grid).
 template <typename T, bool NEED_AX>
 __device__ __forceinline__ NodeResult<T> node2(const vec2<T>* __restrict__ x, int nn, int i, int j,
                                                const Row1<T>& rx, const Row1<T>& ry,
-                                               const OpCoef<T>& op) {
+                                               const OpCoef<T>& op, long long off = 0) {
     NodeResult<T> r;
     const T fxw = rx.face ? ry.mc : T(0);
     const T fyw = ry.face ? rx.mc : T(0);
@@ -34,7 +35,7 @@ __device__ __forceinline__ NodeResult<T> node2(const vec2<T>* __restrict__ x, in
     Cx<T> Mx = cx<T>(0, 0), Kx = cx<T>(0, 0), Fx = cx<T>(0, 0), mxc = cx<T>(0, 0);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        const long long row = (long long)jb[b] * nn;
+        const long long row = (long long)jb[b] * nn - off;
         const Cx<T> v0 = ld<T>(x, row + ia[0]);
         const Cx<T> v1 = ld<T>(x, row + ia[1]);
         const Cx<T> v2 = ld<T>(x, row + ia[2]);
@@ -58,7 +59,7 @@ __device__ __forceinline__ NodeResult<T> node2(const vec2<T>* __restrict__ x, in
 template <typename T, bool NEED_AX>
 __device__ __forceinline__ NodeResult<T> node3(const vec2<T>* __restrict__ x, int nn, int i, int j,
                                                int l, const Row1<T>& rx, const Row1<T>& ry,
-                                               const Row1<T>& rz, const OpCoef<T>& op) {
+                                               const Row1<T>& rz, const OpCoef<T>& op, long long off = 0) {
     NodeResult<T> r;
     const T dr = op.cK * (rx.kc * ry.mc * rz.mc + rx.mc * ry.kc * rz.mc + rx.mc * ry.mc * rz.kc);
     const T dm = rx.mc * ry.mc * rz.mc;
@@ -83,7 +84,7 @@ __device__ __forceinline__ NodeResult<T> node3(const vec2<T>* __restrict__ x, in
         Cx<T> PM = cx<T>(0, 0), PK = cx<T>(0, 0), Pf = cx<T>(0, 0), mxc = cx<T>(0, 0);
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            const long long row = ((long long)lc[c] * nn + jb[b]) * nn;
+            const long long row = ((long long)lc[c] * nn + jb[b]) * nn - off;
             const Cx<T> v0 = ld<T>(x, row + ia[0]);
             const Cx<T> v1 = ld<T>(x, row + ia[1]);
             const Cx<T> v2 = ld<T>(x, row + ia[2]);

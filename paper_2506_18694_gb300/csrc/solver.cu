@@ -189,10 +189,9 @@ hh_status ensure_hier(hh_problem* p, int prec) {
     HH_TRY(dmalloc(p, &H.ca, n0));
     HH_TRY(dmalloc(p, &H.cb, n0));
     HH_TRY(dmalloc(p, &H.cres, n0));
-    // query the cluster shape now: nothing below may call into the runtime's
-    // configuration API while the stream is being captured
-    if (prec == HH_C64) hh::cluster_size_for<float>();
-    else hh::cluster_size_for<double>();
+    // one-time kernel configuration now: nothing may call into the runtime's
+    // configuration API later, while the stream is being captured
+    HH_CUDA(prec == HH_C64 ? hh::prepare_coarse<float>() : hh::prepare_coarse<double>());
     H.ready = true;
     return HH_OK;
 }
@@ -357,46 +356,17 @@ struct MG {
         return HH_OK;
     }
 
-    // First level handled by the cluster kernel (the bottom of the V-cycle), or L if none.
-    int cluster_level() const {
-        const int L = p->o.levels;
-        int lc = L;
-        while (lc - 1 >= 1 && p->lv[lc - 1].N <= p->o.coarse_cluster_nodes && L - (lc - 1) <= hh::kMaxClusterLevels)
-            --lc;
-        return lc;
-    }
-
-    hh_status cluster_cycle(int lc, const V2* b, V2** out) {
-        hh::CoarseArgs<T> a{};
-        a.nlev = p->o.levels - lc;
-        for (int i = 0; i < a.nlev; ++i) {
-            a.g[i] = p->lv[lc + i];
-            a.b[i] = (V2*)H->b[lc + i];
-            a.xa[i] = (V2*)H->xa[lc + i];
-            a.xb[i] = (V2*)H->xb[lc + i];
-            a.t[i] = (V2*)H->t[lc + i];
-        }
-        a.b[0] = const_cast<V2*>(b);
-        a.op = al;
-        a.omega = omega;
-        a.nu_pre = p->o.nu_pre;
-        a.nu_post = p->o.nu_post;
-        a.nu_coarse = p->o.nu_coarse;
-        HH_LAUNCH(hh::launch_coarse_cluster<T>(a, s));
-        *out = (V2*)H->xa[lc];
-        return HH_OK;
-    }
-
     // One V-cycle on level l for right side b from x = 0; result buffer in *out.
     // xstart: the first pre-smoothing sweep was already done and sits in xstart.
     hh_status vcycle(int l, const V2* b, V2* xstart, V2** out) {
         const int L = p->o.levels;
-        if (!xstart && l >= 1 && l == cluster_level()) return cluster_cycle(l, b, out);
         if (l == L - 1) {
             V2* x = (V2*)H->xa[l];
             if (xstart) {
                 x = xstart;
                 HH_TRY(smooth(l, b, p->o.nu_coarse - 1, &x));
+            } else if (p->o.nu_coarse >= 1 && p->lv[l].N <= p->o.coarse_cluster_nodes && hh::coarse_fits<T>(p->lv[l])) {
+                HH_LAUNCH(hh::launch_coarse_solve<T>(p->lv[l], al, b, x, p->o.nu_coarse, omega, s));
             } else {
                 HH_TRY(smooth_from_zero(l, b, p->o.nu_coarse, &x));
             }
@@ -725,7 +695,7 @@ void hh_options_default(hh_options* o) {
     o->precision = HH_C64;
     o->use_graphs = 1;
     o->use_pdl = 1;
-    o->coarse_cluster_nodes = 20000;
+    o->coarse_cluster_nodes = 100000;
 }
 
 static hh_status check_args(const hh_grid* grid, double k, double delta, double dh, const int* bc,

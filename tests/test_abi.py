@@ -30,7 +30,7 @@ def test_options_default(libhh):
     assert (o.theta, o.levels, o.nu_pre, o.nu_post, o.nu_coarse) == (1.0, 4, 2, 2, 8)
     assert o.cycles_per_hss == 1 and abs(o.omega - 0.6) < 1e-15
     assert o.restart == 30 and o.precision == hh.HH_C64 and o.use_graphs == 1
-    assert o.use_pdl == 1 and o.coarse_cluster_nodes == 20000
+    assert o.use_pdl == 1 and o.coarse_cluster_nodes == 100000
 
 
 def test_footprint_bytes(libhh):
