@@ -92,7 +92,7 @@ typedef struct {
     int nu_post;         /* Jacobi sweeps after prolongation                                  */
     int nu_coarse;       /* Jacobi sweeps on the coarsest level                               */
     int cycles_per_hss;  /* V-cycles per HSS iteration                                        */
-    double omega;        /* Jacobi damping                                                    */
+    double omega;        /* Jacobi damping in (0, 2); 0 = automatic: 0.6 in 2D, 0.5 in 3D      */
     int restart;         /* FGMRES restart length                                             */
     int max_outer;       /* FGMRES iteration cap                                              */
     int precision;       /* hh_precision of the V-cycles                                      */
@@ -115,7 +115,7 @@ typedef struct {
 
 typedef struct hh_problem hh_problem;
 
-/* Defaults: theta 1, 4 levels, V(2,2), 8 coarse sweeps, omega 0.6, restart 30,
+/* Defaults: theta 1, 4 levels, V(2,2), 8 coarse sweeps, omega automatic, restart 30,
  * max_outer 1000, complex FP32 V-cycles, graphs and programmatic launch on,
  * coarse_cluster_nodes 100000. */
 HH_API void hh_options_default(hh_options* opts);

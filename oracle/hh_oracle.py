@@ -326,7 +326,7 @@ class Options:
     nu_pre: int = 2
     nu_post: int = 2
     nu_coarse: int = 8
-    omega: float = 0.6
+    omega: float = 0.0          # Jacobi damping; 0 = 0.6 in 2D, 0.5 in 3D
     cycles_per_hss: int = 1
     restart: int = 30
     max_outer: int = 200
@@ -346,6 +346,10 @@ class Problem:
         L = self.opts.levels
         if self.grid.n % (2 ** (L - 1)):
             raise ValueError("n must be divisible by 2^(levels-1)")
+        if self.opts.omega == 0.0:
+            # damping by dimension: D^{-1}M reaches 9/4 in 2D and 27/8 in 3D, and the
+            # shifted mass term dominates A_L on coarse levels, so 3D needs omega < 0.59
+            self.opts = Options(**{**self.opts.__dict__, "omega": 0.5 if self.grid.dim == 3 else 0.6})
         self.grids = [self.grid]
         for _ in range(L - 1):
             self.grids.append(self.grids[-1].coarse())

@@ -200,30 +200,15 @@ bool coarse_fits(const GridDesc& g) {
 
 template <typename T>
 static CoarseW<T> coarse_weights(const GridDesc& g, const OpCoef<T>& op, T omega) {
-    // interior Q1 weights: stiffness and mass of the centre and of each neighbour class
-    double kw[4], mw[4];
-    const double h = g.h;
-    if (g.dim == 2) {
-        const double k2[4] = {8.0 / 3.0, -1.0 / 3.0, -1.0 / 3.0, 0.0};
-        const double m2[4] = {16.0 / 36.0, 4.0 / 36.0, 1.0 / 36.0, 0.0};
-        for (int c = 0; c < 4; ++c) {
-            kw[c] = k2[c];
-            mw[c] = m2[c] * h * h;
-        }
-    } else {
-        const double k3[4] = {8.0 / 3.0, 0.0, -1.0 / 6.0, -1.0 / 12.0};
-        const double m3[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
-        for (int c = 0; c < 4; ++c) {
-            kw[c] = k3[c] * h;
-            mw[c] = m3[c] * h * h * h;
-        }
-    }
+    MArgs<T> a{};
+    a.g = g;
+    a.op = op;
+    a.opd = op;
+    a.omega = omega;
+    interior_weights(a);
     CoarseW<T> cw;
-    for (int c = 0; c < 4; ++c)
-        cw.w[c] = cx<T>(T(double(op.cK) * kw[c] + double(op.cM.re) * mw[c]), T(double(op.cM.im) * mw[c]));
-    const double dr = double(op.cK) * kw[0] + double(op.cM.re) * mw[0], di = double(op.cM.im) * mw[0];
-    const double d2 = dr * dr + di * di;
-    cw.dinv = cx<T>(T(double(omega) * dr / d2), T(-double(omega) * di / d2));
+    for (int c = 0; c < 4; ++c) cw.w[c] = a.iw[c];
+    cw.dinv = a.wdinv;
     return cw;
 }
 

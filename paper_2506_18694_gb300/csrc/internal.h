@@ -51,26 +51,9 @@ inline cudaError_t klaunch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-enum StencilMode {
-    MODE_APPLY = 0,   // y = op x
-    MODE_AXPBY = 1,   // y = alpha (op x) + beta z          (x == nullptr: op x = 0)
-    MODE_JACOBI = 2   // y = x + omega D^{-1} (z - op x)    (x == nullptr: x = 0)
-};
-
-template <typename T>
-cudaError_t launch_stencil(int mode, const GridDesc& g, const OpCoef<T>& op, const vec2<T>* x,
-                           const vec2<T>* z, vec2<T>* y, Cx<T> alpha, Cx<T> beta, T omega,
-                           cudaStream_t s);
-
 // rc = P^T rf (rf on the fine grid of gc)
 template <typename T>
 cudaError_t launch_restrict(const GridDesc& gc, const vec2<T>* rf, vec2<T>* rc, cudaStream_t s);
-
-// rc = P^T (b - A x); scratch holds the fine residual (fine-grid length)
-template <typename T>
-cudaError_t launch_residual_restrict(const GridDesc& gf, const GridDesc& gc, const OpCoef<T>& op,
-                                     const vec2<T>* b, const vec2<T>* x, vec2<T>* rc,
-                                     vec2<T>* scratch, cudaStream_t s);
 
 // x += P ec (ec on the coarse grid of gf)
 template <typename T>
@@ -125,9 +108,18 @@ template <typename T> struct MArgs {
     // filled by the launcher
     T h, ih;
     int rows;
-    Cx<T> wc, we, wd;    // interior stencil weights of op: centre, edge, diagonal neighbours
+    // interior stencil weights of op by neighbour class (how many coordinates differ from
+    // the centre: 0 centre, 1 edge/face, 2 diagonal/edge, 3 corner in 3D)
+    Cx<T> iw[4];
     Cx<T> wdinv;         // omega / (interior diagonal of opd)
 };
+
+// ---- fused 3D tile kernels (march3.cu): modes as above except M_RESID_RESTRICT ----
+template <typename T>
+cudaError_t launch_march3(int mode, const MArgs<T>& a, cudaStream_t s);
+// interior weights (iw, wdinv) of a.op / a.opd on grid a.g (filled by the launchers)
+template <typename T>
+void interior_weights(MArgs<T>& a);
 
 template <typename T>
 cudaError_t launch_march2(int mode, const MArgs<T>& a, cudaStream_t s);

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(128) k_march2(MArgs<T> a) {
         if (fast) {
             const Cx<T> edge = (lf[t] + rg[t]) + (fv[t - 1] + fv[t + 1]);
             const Cx<T> diag = (lf[t - 1] + rg[t - 1]) + (lf[t + 1] + rg[t + 1]);
-            ax = fma_c(a.wd, diag, fma_c(a.we, edge, cmul(a.wc, fv[t])));
+            ax = fma_c(a.iw[2], diag, fma_c(a.iw[1], edge, cmul(a.iw[0], fv[t])));
             dinv_w = a.wdinv;
         } else {
             const Row1<T> ry = row1<T>(jc, n, a.g.dir[2], a.g.dir[3], h, ih);
@@ -199,28 +199,40 @@ __global__ void __launch_bounds__(128) k_march2(MArgs<T> a) {
 }
 
 // Rows per warp: the largest that still leaves about 24 warps per SM (loads in flight).
-// Interior stencil weights of op (Q1 on a uniform square grid: stiffness 8/3, -1/3, -1/3
-// and mass h^2/36 x (16, 4, 1) for the centre, edge and diagonal neighbours) and
-// omega / (interior diagonal of opd), computed in double precision.
+// Interior stencil weights of op by neighbour class and omega / (interior diagonal of opd),
+// in double precision.  Q1 on a uniform grid: 2D stiffness 8/3, -1/3, -1/3 and mass
+// h^2 (16, 4, 1)/36 for the centre, edge and diagonal neighbours; 3D stiffness
+// h (8/3, 0, -1/6, -1/12) and mass h^3 (8/27, 2/27, 1/54, 1/216) for the centre, face,
+// edge and corner neighbours.
 template <typename T>
-static void interior_weights(MArgs<T>& a) {
-    const double h2 = a.g.h * a.g.h;
-    auto w = [&](const OpCoef<T>& o, double kw, double mw, double* re, double* im) {
-        *re = double(o.cK) * kw + double(o.cM.re) * mw * h2;
-        *im = double(o.cM.im) * mw * h2;
-    };
-    double r, im;
-    w(a.op, 8.0 / 3.0, 16.0 / 36.0, &r, &im);
-    a.wc = cx<T>(T(r), T(im));
-    w(a.op, -1.0 / 3.0, 4.0 / 36.0, &r, &im);
-    a.we = cx<T>(T(r), T(im));
-    w(a.op, -1.0 / 3.0, 1.0 / 36.0, &r, &im);
-    a.wd = cx<T>(T(r), T(im));
-    w(a.opd, 8.0 / 3.0, 16.0 / 36.0, &r, &im);
-    const double d2 = r * r + im * im;
+void interior_weights(MArgs<T>& a) {
+    const double h = a.g.h;
+    double kw[4], mw[4];
+    if (a.g.dim == 2) {
+        const double k2[4] = {8.0 / 3.0, -1.0 / 3.0, -1.0 / 3.0, 0.0};
+        const double m2[4] = {16.0 / 36.0, 4.0 / 36.0, 1.0 / 36.0, 0.0};
+        for (int c = 0; c < 4; ++c) {
+            kw[c] = k2[c];
+            mw[c] = m2[c] * h * h;
+        }
+    } else {
+        const double k3[4] = {8.0 / 3.0, 0.0, -1.0 / 6.0, -1.0 / 12.0};
+        const double m3[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
+        for (int c = 0; c < 4; ++c) {
+            kw[c] = k3[c] * h;
+            mw[c] = m3[c] * h * h * h;
+        }
+    }
+    for (int c = 0; c < 4; ++c)
+        a.iw[c] = cx<T>(T(double(a.op.cK) * kw[c] + double(a.op.cM.re) * mw[c]), T(double(a.op.cM.im) * mw[c]));
+    const double dr = double(a.opd.cK) * kw[0] + double(a.opd.cM.re) * mw[0], di = double(a.opd.cM.im) * mw[0];
+    const double d2 = dr * dr + di * di;
     const double om = double(a.omega);
-    a.wdinv = d2 > 0 ? cx<T>(T(om * r / d2), T(-om * im / d2)) : cx<T>(T(0), T(0));
+    a.wdinv = d2 > 0 ? cx<T>(T(om * dr / d2), T(-om * di / d2)) : cx<T>(T(0), T(0));
 }
+
+template void interior_weights<float>(MArgs<float>&);
+template void interior_weights<double>(MArgs<double>&);
 
 template <typename T, int MODE>
 static cudaError_t go2(MArgs<T> a, cudaStream_t s) {

@@ -227,6 +227,10 @@ struct MG {
 
     bool d2() const { return p->grid.dim == 2; }
 
+    cudaError_t march(int mode, const hh::MArgs<T>& a) const {
+        return d2() ? hh::launch_march2<T>(mode, a, s) : hh::launch_march3<T>(mode, a, s);
+    }
+
     hh::MArgs<T> margs(int l, const OpCoef<T>& op) const {
         hh::MArgs<T> a{};
         a.g = p->lv[l];
@@ -239,31 +243,21 @@ struct MG {
     // ---- level kernels: fused 2D marching kernels, composed generic kernels in 3D ----
     // x_out = x_in + omega D^{-1} (b - A_L x_in); x_in == nullptr means 0
     hh_status jacobi(int l, const V2* b, const V2* xin, V2* xout) {
-        if (d2()) {
-            hh::MArgs<T> a = margs(l, al);
-            a.x = xin;
-            a.xzero = xin == nullptr;
-            a.z = b;
-            a.y = xout;
-            HH_LAUNCH(hh::launch_march2<T>(hh::M_JACOBI, a, s));
-        } else {
-            HH_LAUNCH(hh::launch_stencil<T>(hh::MODE_JACOBI, p->lv[l], al, xin, b, xout, Cx<T>{0, 0}, Cx<T>{0, 0},
-                                            omega, s));
-        }
+        hh::MArgs<T> a = margs(l, al);
+        a.x = xin;
+        a.xzero = xin == nullptr;
+        a.z = b;
+        a.y = xout;
+        HH_LAUNCH(march(hh::M_JACOBI, a));
         return HH_OK;
     }
     // two sweeps from x = 0
     hh_status jacobi2_zero(int l, const V2* b, V2* xout) {
-        if (d2()) {
-            hh::MArgs<T> a = margs(l, al);
-            a.z = b;
-            a.y = xout;
-            HH_LAUNCH(hh::launch_march2<T>(hh::M_JACOBI2_ZERO, a, s));
-            return HH_OK;
-        }
-        V2* tmp = (V2*)H->t[l];
-        HH_TRY(jacobi(l, b, nullptr, tmp));
-        return jacobi(l, b, tmp, xout);
+        hh::MArgs<T> a = margs(l, al);
+        a.z = b;
+        a.y = xout;
+        HH_LAUNCH(march(hh::M_JACOBI2_ZERO, a));
+        return HH_OK;
     }
     // rc = P^T (b - A_L x)
     hh_status resid_restrict(int l, const V2* b, const V2* x, V2* rc) {
@@ -274,56 +268,51 @@ struct MG {
             a.y = rc;
             HH_LAUNCH(hh::launch_march2<T>(hh::M_RESID_RESTRICT, a, s));
         } else {
-            HH_LAUNCH(hh::launch_residual_restrict<T>(p->lv[l], p->lv[l + 1], al, b, x, rc, (V2*)H->t[l], s));
+            hh::MArgs<T> a = margs(l, al);
+            a.x = x;
+            a.z = b;
+            a.y = (V2*)H->t[l];
+            a.alpha = Cx<T>{-1, 0};
+            a.beta = Cx<T>{1, 0};
+            HH_LAUNCH(hh::launch_march3<T>(hh::M_AXPBY, a, s));
+            HH_LAUNCH(hh::launch_restrict<T>(p->lv[l + 1], (const V2*)H->t[l], rc, s));
         }
         return HH_OK;
     }
-    // xout = x~ + omega D^{-1} (b - A_L x~), x~ = x + P ec   (x is clobbered in 3D)
+    // xout = x~ + omega D^{-1} (b - A_L x~), x~ = x + P ec
     hh_status prolong_jacobi(int l, V2* x, const V2* ec, const V2* b, V2* xout) {
-        if (d2()) {
-            hh::MArgs<T> a = margs(l, al);
-            a.x = x;
-            a.ec = ec;
-            a.z = b;
-            a.y = xout;
-            HH_LAUNCH(hh::launch_march2<T>(hh::M_PROLONG_JACOBI, a, s));
-            return HH_OK;
-        }
-        HH_LAUNCH(hh::launch_prolong<T>(p->lv[l], ec, x, s));
-        return jacobi(l, b, x, xout);
+        hh::MArgs<T> a = margs(l, al);
+        a.x = x;
+        a.ec = ec;
+        a.z = b;
+        a.y = xout;
+        HH_LAUNCH(march(hh::M_PROLONG_JACOBI, a));
+        return HH_OK;
     }
     // rhs = c1 A_R u + c2 r and the first Jacobi sweep x1 = omega D^{-1} rhs (u == nullptr: u = 0)
     hh_status hss_first(const V2* u, const V2* r, V2* rhs, V2* x1, T c1, T c2) {
         const OpCoef<T> ar = to_coef<T>(p->AR);
-        if (d2()) {
-            hh::MArgs<T> a = margs(0, ar);
-            a.x = u;
-            a.xzero = u == nullptr;
-            a.z = r;
-            a.y = rhs;
-            a.y2 = x1;
-            a.alpha = Cx<T>{c1, 0};
-            a.beta = Cx<T>{c2, 0};
-            HH_LAUNCH(hh::launch_march2<T>(hh::M_HSS_FIRST, a, s));
-            return HH_OK;
-        }
-        HH_LAUNCH(hh::launch_stencil<T>(hh::MODE_AXPBY, p->lv[0], ar, u, r, rhs, Cx<T>{c1, 0}, Cx<T>{c2, 0}, T(0), s));
-        return jacobi(0, rhs, nullptr, x1);
+        hh::MArgs<T> a = margs(0, ar);
+        a.x = u;
+        a.xzero = u == nullptr;
+        a.z = r;
+        a.y = rhs;
+        a.y2 = x1;
+        a.alpha = Cx<T>{c1, 0};
+        a.beta = Cx<T>{c2, 0};
+        HH_LAUNCH(march(hh::M_HSS_FIRST, a));
+        return HH_OK;
     }
     hh_status hss_rhs(const V2* u, const V2* r, V2* rhs, T c1, T c2) {
         const OpCoef<T> ar = to_coef<T>(p->AR);
-        if (d2()) {
-            hh::MArgs<T> a = margs(0, ar);
-            a.x = u;
-            a.xzero = u == nullptr;
-            a.z = r;
-            a.y = rhs;
-            a.alpha = Cx<T>{c1, 0};
-            a.beta = Cx<T>{c2, 0};
-            HH_LAUNCH(hh::launch_march2<T>(hh::M_AXPBY, a, s));
-            return HH_OK;
-        }
-        HH_LAUNCH(hh::launch_stencil<T>(hh::MODE_AXPBY, p->lv[0], ar, u, r, rhs, Cx<T>{c1, 0}, Cx<T>{c2, 0}, T(0), s));
+        hh::MArgs<T> a = margs(0, ar);
+        a.x = u;
+        a.xzero = u == nullptr;
+        a.z = r;
+        a.y = rhs;
+        a.alpha = Cx<T>{c1, 0};
+        a.beta = Cx<T>{c2, 0};
+        HH_LAUNCH(march(hh::M_AXPBY, a));
         return HH_OK;
     }
 
@@ -404,8 +393,13 @@ struct MG {
             // keep x outside the level-0 ping-pong buffers the next cycle overwrites
             V2* keep = (V2*)((x == (V2*)H->ca) ? H->cb : H->ca);
             HH_CUDA(cudaMemcpyAsync(keep, x, (size_t)N * sizeof(V2), cudaMemcpyDeviceToDevice, s));
-            HH_LAUNCH(hh::launch_stencil<T>(hh::MODE_AXPBY, p->lv[0], al, keep, b, (V2*)H->cres, Cx<T>{-1, 0},
-                                            Cx<T>{1, 0}, T(0), s));
+            hh::MArgs<T> a = margs(0, al);
+            a.x = keep;
+            a.z = b;
+            a.y = (V2*)H->cres;
+            a.alpha = Cx<T>{-1, 0};
+            a.beta = Cx<T>{1, 0};
+            HH_LAUNCH(march(hh::M_AXPBY, a));
             V2* corr;
             HH_TRY(vcycle(0, (const V2*)H->cres, nullptr, &corr));
             HH_LAUNCH(hh::launch_add<T>(keep, corr, N, s));
@@ -526,21 +520,17 @@ template <typename T>
 hh_status op_axpby(hh_problem* p, int l, const Triple& t, const hh::vec2<T>* x, const hh::vec2<T>* z,
                    hh::vec2<T>* y, Cx<T> alpha, Cx<T> beta, cudaStream_t st) {
     const OpCoef<T> op = to_coef<T>(t);
-    if (p->grid.dim == 2) {
-        hh::MArgs<T> a{};
-        a.g = p->lv[l];
-        a.op = op;
-        a.opd = op;
-        a.x = x;
-        a.z = z;
-        a.y = y;
-        a.alpha = alpha;
-        a.beta = beta;
-        HH_LAUNCH(hh::launch_march2<T>(z ? hh::M_AXPBY : hh::M_APPLY, a, st));
-    } else {
-        HH_LAUNCH(hh::launch_stencil<T>(z ? hh::MODE_AXPBY : hh::MODE_APPLY, p->lv[l], op, x, z, y, alpha, beta,
-                                        T(0), st));
-    }
+    hh::MArgs<T> a{};
+    a.g = p->lv[l];
+    a.op = op;
+    a.opd = op;
+    a.x = x;
+    a.z = z;
+    a.y = y;
+    a.alpha = alpha;
+    a.beta = beta;
+    const int mode = z ? hh::M_AXPBY : hh::M_APPLY;
+    HH_LAUNCH(p->grid.dim == 2 ? hh::launch_march2<T>(mode, a, st) : hh::launch_march3<T>(mode, a, st));
     return HH_OK;
 }
 
@@ -689,7 +679,7 @@ void hh_options_default(hh_options* o) {
     o->nu_post = 2;
     o->nu_coarse = 8;
     o->cycles_per_hss = 1;
-    o->omega = 0.6;
+    o->omega = 0.0;  // automatic: 0.6 in 2D, 0.5 in 3D
     o->restart = 30;
     o->max_outer = 1000;
     o->precision = HH_C64;
@@ -713,7 +703,7 @@ static hh_status check_args(const hh_grid* grid, double k, double delta, double 
         return fail(HH_ERR_INVALID, "negative sweep count or cycles_per_hss < 1");
     if (o->restart < 1 || o->restart > 63) return fail(HH_ERR_INVALID, "restart must be in 1..63");
     if (o->max_outer < 0) return fail(HH_ERR_INVALID, "max_outer < 0");
-    if (!(o->theta >= 0) || !(o->omega > 0)) return fail(HH_ERR_INVALID, "theta >= 0 and omega > 0 required");
+    if (!(o->theta >= 0) || !(o->omega >= 0) || !(o->omega < 2)) return fail(HH_ERR_INVALID, "theta >= 0 and 0 <= omega < 2 required");
     if (o->precision != HH_C64 && o->precision != HH_C128) return fail(HH_ERR_INVALID, "bad precision");
     if (o->coarse_cluster_nodes < 0) return fail(HH_ERR_INVALID, "coarse_cluster_nodes < 0");
     if (!bc) return fail(HH_ERR_INVALID, "null bc");
@@ -759,6 +749,10 @@ hh_status hh_create_problem(const hh_grid* grid, double k, double delta, double 
     p->dh = delta_hat;
     for (int s = 0; s < 6; ++s) p->bc[s] = s < 2 * grid->dim ? bc[s] : 0;
     p->o = *opts;
+    // automatic damping: on levels where the shifted mass term dominates, D^{-1} A_L has
+    // spectrum close to D^{-1} M, which reaches 9/4 in 2D and 27/8 in 3D; omega must stay
+    // below 2 / 27 * 8 = 0.59 in 3D for the sweeps not to amplify smooth modes
+    if (p->o.omega == 0.0) p->o.omega = grid->dim == 3 ? 0.5 : 0.6;
     p->AL = triple_AL(k, delta_hat);
     p->AR = triple_AR(k, delta_hat);
     p->B = triple_B(k, delta);

@@ -1,119 +1,11 @@
-// Matrix-free Q1 operator kernels: operator apply, scaled Jacobi, residual,
-// full-weighting restriction, bi/trilinear prolongation, precision casts.
-//
-// Every operator is c_K K + c_M M + c_G M_Gamma (primal weak form b_delta, Sec. 2;
-// A_L / A_R of Def. 4.1).  On a uniform grid the Q1 stiffness and mass matrices are
-// sums of tensor products of the 1D matrices (1/h)[-1 2 -1] and (h/6)[1 4 1], so the
-// row of a node is built from three 1D weight triples (one per axis) that encode the
-// domain ends and Dirichlet elimination; a Sommerfeld side adds the (dim-1)-
-// dimensional mass of that side.  No matrix is stored: one output node reads the
-// 3^dim neighbourhood of x once.
+// Grid-transfer and elementwise kernels: full-weighting restriction (3D and the
+// building-block API), bi/trilinear prolongation, precision casts, masked copies.
 #include "internal.h"
-#include "node.cuh"
 
 namespace hh {
 
 thread_local long long g_kernel_launches = 0;
 thread_local int g_use_pdl = 1;
-
-template <typename T, int MODE, bool XZERO>
-__device__ __forceinline__ Cx<T> epilogue(const NodeResult<T>& nr, const vec2<T>* __restrict__ x,
-                                          const vec2<T>* __restrict__ z, long long p, Cx<T> alpha,
-                                          Cx<T> beta, T omega) {
-    if (MODE == MODE_APPLY) return nr.ax;
-    if (MODE == MODE_AXPBY) {
-        Cx<T> out = cmul(beta, ld<T>(z, p));
-        if (!XZERO) out = fma_c(alpha, nr.ax, out);
-        return out;
-    }
-    // MODE_JACOBI: x + omega D^{-1} (z - op x)
-    const Cx<T> dinv = cinv(nr.d);
-    Cx<T> res = ld<T>(z, p);
-    if (!XZERO) res = res - nr.ax;
-    Cx<T> upd = omega * cmul(dinv, res);
-    if (!XZERO) upd = upd + ld<T>(x, p);
-    return upd;
-}
-
-template <typename T, int MODE, bool XZERO>
-__global__ void __launch_bounds__(256) k_stencil2(GridDesc g, OpCoef<T> op, T h, T ih,
-                                                  const vec2<T>* __restrict__ x,
-                                                  const vec2<T>* __restrict__ z,
-                                                  vec2<T>* __restrict__ y, Cx<T> alpha,
-                                                  Cx<T> beta, T omega) {
-    pdl_entry();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i > g.n || j > g.n) return;
-    const long long p = (long long)j * g.nn + i;
-    const Row1<T> rx = row1<T>(i, g.n, g.dir[0], g.dir[1], h, ih);
-    const Row1<T> ry = row1<T>(j, g.n, g.dir[2], g.dir[3], h, ih);
-    if (rx.masked || ry.masked) {
-        st<T>(y, p, cx<T>(0, 0));
-        return;
-    }
-    constexpr bool NEED = !XZERO;
-    const NodeResult<T> nr = node2<T, NEED>(x, g.nn, i, j, rx, ry, op);
-    st<T>(y, p, epilogue<T, MODE, XZERO>(nr, x, z, p, alpha, beta, omega));
-}
-
-template <typename T, int MODE, bool XZERO>
-__global__ void __launch_bounds__(256) k_stencil3(GridDesc g, OpCoef<T> op, T h, T ih,
-                                                  const vec2<T>* __restrict__ x,
-                                                  const vec2<T>* __restrict__ z,
-                                                  vec2<T>* __restrict__ y, Cx<T> alpha,
-                                                  Cx<T> beta, T omega) {
-    pdl_entry();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int l = blockIdx.z;
-    if (i > g.n || j > g.n) return;
-    const long long p = ((long long)l * g.nn + j) * g.nn + i;
-    const Row1<T> rx = row1<T>(i, g.n, g.dir[0], g.dir[1], h, ih);
-    const Row1<T> ry = row1<T>(j, g.n, g.dir[2], g.dir[3], h, ih);
-    const Row1<T> rz = row1<T>(l, g.n, g.dir[4], g.dir[5], h, ih);
-    if (rx.masked || ry.masked || rz.masked) {
-        st<T>(y, p, cx<T>(0, 0));
-        return;
-    }
-    constexpr bool NEED = !XZERO;
-    const NodeResult<T> nr = node3<T, NEED>(x, g.nn, i, j, l, rx, ry, rz, op);
-    st<T>(y, p, epilogue<T, MODE, XZERO>(nr, x, z, p, alpha, beta, omega));
-}
-
-template <typename T, int MODE, bool XZERO>
-static cudaError_t launch_mode(const GridDesc& g, const OpCoef<T>& op, const vec2<T>* x, const vec2<T>* z,
-                        vec2<T>* y, Cx<T> alpha, Cx<T> beta, T omega, cudaStream_t s) {
-    const T h = T(g.h), ih = T(1.0 / g.h);
-    dim3 blk(32, 8, 1);
-    if (g.dim == 2) {
-        dim3 grd((g.nn + 31) / 32, (g.nn + 7) / 8, 1);
-        return klaunch(k_stencil2<T, MODE, XZERO>, dim3(grd), dim3(blk), 0, s, 1, g, op, h, ih, x, z, y, alpha, beta,
-                       omega);
-    } else {
-        dim3 grd((g.nn + 31) / 32, (g.nn + 7) / 8, g.nn);
-        return klaunch(k_stencil3<T, MODE, XZERO>, dim3(grd), dim3(blk), 0, s, 1, g, op, h, ih, x, z, y, alpha, beta,
-                       omega);
-    }
-}
-
-template <typename T>
-cudaError_t launch_stencil(int mode, const GridDesc& g, const OpCoef<T>& op, const vec2<T>* x,
-                           const vec2<T>* z, vec2<T>* y, Cx<T> alpha, Cx<T> beta, T omega,
-                           cudaStream_t s) {
-    const bool xz = (x == nullptr);
-    if (mode == MODE_APPLY) {
-        if (xz) return cudaErrorInvalidValue;
-        HH_KRET((launch_mode<T, MODE_APPLY, false>(g, op, x, z, y, alpha, beta, omega, s)));
-    } else if (mode == MODE_AXPBY) {
-        if (xz) HH_KRET((launch_mode<T, MODE_AXPBY, true>(g, op, x, z, y, alpha, beta, omega, s)));
-        else HH_KRET((launch_mode<T, MODE_AXPBY, false>(g, op, x, z, y, alpha, beta, omega, s)));
-    } else {
-        if (xz) HH_KRET((launch_mode<T, MODE_JACOBI, true>(g, op, x, z, y, alpha, beta, omega, s)));
-        else HH_KRET((launch_mode<T, MODE_JACOBI, false>(g, op, x, z, y, alpha, beta, omega, s)));
-    }
-    return cudaSuccess;
-}
 
 // ---------------------------------------------------------------- restriction
 // Full weighting R = P^T: coarse node I gathers fine nodes 2I + a, a in {-1,0,1}^dim,
@@ -166,16 +58,6 @@ cudaError_t launch_restrict(const GridDesc& gc, const vec2<T>* rf, vec2<T>* rc, 
     dim3 grd((gc.nn + 31) / 32, (gc.nn + 7) / 8, gc.dim == 3 ? gc.nn : 1);
     HH_KRET(klaunch(k_restrict<T>, dim3(grd), dim3(blk), 0, s, 1, gc, rf, rc));
     return cudaSuccess;
-}
-
-template <typename T>
-cudaError_t launch_residual_restrict(const GridDesc& gf, const GridDesc& gc, const OpCoef<T>& op,
-                                     const vec2<T>* b, const vec2<T>* x, vec2<T>* rc,
-                                     vec2<T>* scratch, cudaStream_t s) {
-    cudaError_t e = launch_stencil<T>(MODE_AXPBY, gf, op, x, b, scratch, cx<T>(-1, 0), cx<T>(1, 0),
-                                      T(0), s);
-    if (e != cudaSuccess) return e;
-    return launch_restrict<T>(gc, scratch, rc, s);
 }
 
 // ---------------------------------------------------------------- prolongation
@@ -296,14 +178,8 @@ cudaError_t launch_mask_copy(const GridDesc& g, const double2* src, double2* dst
 }
 
 #define HH_INSTANTIATE(T)                                                                          \
-    template cudaError_t launch_stencil<T>(int, const GridDesc&, const OpCoef<T>&, const vec2<T>*, \
-                                           const vec2<T>*, vec2<T>*, Cx<T>, Cx<T>, T, cudaStream_t); \
     template cudaError_t launch_restrict<T>(const GridDesc&, const vec2<T>*, vec2<T>*,             \
                                             cudaStream_t);                                         \
-    template cudaError_t launch_residual_restrict<T>(const GridDesc&, const GridDesc&,             \
-                                                     const OpCoef<T>&, const vec2<T>*,             \
-                                                     const vec2<T>*, vec2<T>*, vec2<T>*,           \
-                                                     cudaStream_t);                                \
     template cudaError_t launch_prolong<T>(const GridDesc&, const vec2<T>*, vec2<T>*,              \
                                            cudaStream_t);                                          \
     template cudaError_t launch_add<T>(vec2<T>*, const vec2<T>*, long long, cudaStream_t);

@@ -28,7 +28,7 @@ def test_library_exports_every_declared_symbol(libhh):
 def test_options_default(libhh):
     o = hh.default_options()
     assert (o.theta, o.levels, o.nu_pre, o.nu_post, o.nu_coarse) == (1.0, 4, 2, 2, 8)
-    assert o.cycles_per_hss == 1 and abs(o.omega - 0.6) < 1e-15
+    assert o.cycles_per_hss == 1 and o.omega == 0.0
     assert o.restart == 30 and o.precision == hh.HH_C64 and o.use_graphs == 1
     assert o.use_pdl == 1 and o.coarse_cluster_nodes == 100000
 
