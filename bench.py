@@ -31,6 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "V-cycle DoF/s & HBM roofline %; solves/s, p99 latency; mixed vs FP64 at 1e-8"
 UNIT = "DoF*V-cycles/s"
 WORKLOAD = "2d_n512_k80"
+GRIDS = {"2d_n512_k80": "2D unit square, 512x512 Q1 cells (513^2 nodes), Sommerfeld on all sides",
+         "3d_n128_k40": "3D unit cube, 128^3 Q1 cells (129^3 nodes), u=0 on z=0, Sommerfeld elsewhere"}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -41,6 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--delta-hat", default="k")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["2d_n512_k80", "3d_n128_k40"],
+                    help="2D 512^2 k=80 (default) or 3D 128^3 k=40 (FGMRES restart 60)")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 / roofline / CPU legs")
     ap.add_argument("--max-outer", type=int, default=0,
                     help="cap FGMRES iterations (profiling runs only; 0 = solve to tolerance)")
@@ -147,7 +151,7 @@ def run_reference(args):
         return
     from paper_2506_18694_gb300 import inputs
 
-    w = inputs.workload(WORKLOAD, args.delta_hat)
+    w = inputs.workload(args.workload, args.delta_hat)
     from oracle import hh_oracle as O
 
     g = O.Grid(w.dim, w.n, w.bc)
@@ -175,10 +179,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "delta_hat": w.delta_hat, "nodes": g.N},
+        "data": "synthetic", "config": {"workload": w.name, "delta_hat": w.delta_hat, "nodes": g.N},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
                          "sample": f"{per_step_cycles} HSS iterations (V-cycles) per step of the "
-                                   f"513^2 k=80 workload, FP64 scipy CSR"},
+                                   f"{w.name} workload, FP64 scipy CSR"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -202,8 +206,8 @@ def main():
     else:
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
-    w = inputs.workload(WORKLOAD, args.delta_hat)
-    opts = hh.default_options(precision=hh.HH_C64)
+    w = inputs.workload(args.workload, args.delta_hat)
+    opts = hh.default_options(precision=hh.HH_C64, restart=60 if w.dim == 3 else 30)
     if args.max_outer > 0:
         opts.max_outer = args.max_outer
     prob = hh.Problem(w.dim, w.n, w.k, w.delta, w.delta_hat, w.bc, opts)
@@ -264,7 +268,7 @@ def main():
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        extras = measure_extras(hh, inputs, torch, w, prob, b, u, infos[-1])
+        extras = measure_extras(hh, inputs, torch, w, prob, b, u, infos[-1], opts)
     prob.close()
 
     if rank == 0:
@@ -273,9 +277,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 V-cycles / c128 FGMRES",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": "2D unit square, 512x512 Q1 cells (513^2 nodes)",
+            "config": {"workload": w.name, "grid": GRIDS[w.name],
                        "k": w.k, "delta": w.delta, "delta_hat": w.delta_hat, "tol": w.tol,
-                       "levels": opts.levels, "smoother": f"V({opts.nu_pre},{opts.nu_post}) Jacobi w={opts.omega}",
+                       "levels": opts.levels, "smoother": f"V({opts.nu_pre},{opts.nu_post}) Jacobi w={opts.omega or (0.5 if w.dim == 3 else 0.6)}",
                        "nu_coarse": opts.nu_coarse, "restart": opts.restart, "l2": "flushed between steps",
                        "per_rank": "one independent solve per step"},
             "solves_per_s": world * args.steps / total_s,
@@ -331,7 +335,7 @@ def time_kernel(torch, fn, reps, flush=None):
     return tot / reps / 1e3
 
 
-def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed):
+def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -350,8 +354,9 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed):
     b32 = b.to(torch.complex64)
     y = torch.empty_like(x)
     t_w = time_kernel(torch, lambda: prob.jacobi(0, b32, x, y), 50, flush)
-    big = hh.Problem(2, 4096, w.k, w.delta, w.delta_hat, w.bc, hh.default_options(precision=hh.HH_C64, levels=2,
-                                                                                   restart=1))
+    nbig = 4096 if w.dim == 2 else 256
+    big = hh.Problem(w.dim, nbig, w.k, w.delta, w.delta_hat, w.bc, hh.default_options(precision=hh.HH_C64, levels=2,
+                                                                                       restart=1))
     Nb = big.nodes()
     xb = torch.randn(Nb, dtype=torch.complex64, device="cuda")
     bb = torch.randn(Nb, dtype=torch.complex64, device="cuda")
@@ -359,16 +364,23 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed):
     t_b = time_kernel(torch, lambda: big.jacobi(0, bb, xb, yb), 20)
     big.close()
     ach = 24 * Nb / t_b / 1e9
-    out["roofline"] = {"bound": "hbm", "kernel": "k_march2<float, JACOBI, 8> (scaled-Jacobi sweep)",
+    if w.dim == 2:
+        kname, prof, src = ("k_march2<float, JACOBI, 8> (scaled-Jacobi sweep)", "jacobi_2d_4097sq_c64.md",
+                            "paper_2506_18694_gb300/csrc/march2.cu")
+        size = "4097^2 nodes (3 x 134 MB vectors > L2)"
+    else:
+        kname, prof, src = ("k_march3<float, JACOBI, 8> (scaled-Jacobi sweep)", "jacobi_3d_257cube_c64.md",
+                            "paper_2506_18694_gb300/csrc/march3.cu")
+        size = "257^3 nodes (3 x 136 MB vectors > L2)"
+    out["roofline"] = {"bound": "hbm", "kernel": kname,
                        "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                       "traffic": profiled_traffic("jacobi_2d_4097sq_c64.md", "paper_2506_18694_gb300/csrc/march2.cu"),
-                       "size": "4097^2 nodes (3 x 134 MB vectors > L2)",
+                       "traffic": profiled_traffic(prof, src), "size": size,
                        "bytes_per_node": 24, "peak_source": peak_src,
                        "at_workload": {"nodes": N, "us": t_w * 1e6, "effective_gbs": 24 * N / t_w / 1e9,
                                        "note": "513^2 vectors are L2-resident"}}
 
     # FP64 V-cycles on the same workload (single solve), error vs the mixed result
-    opts64 = hh.default_options(precision=hh.HH_C128)
+    opts64 = hh.default_options(precision=hh.HH_C128, restart=opts.restart)
     with hh.Problem(w.dim, w.n, w.k, w.delta, w.delta_hat, w.bc, opts64) as p64:
         p64.solve(b, w.tol)  # warm (graph capture)
         torch.cuda.synchronize()
@@ -383,7 +395,7 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed):
     # the paper's delta_hat = 2 on the same grid and source (mixed precision).  One
     # V(2,2)-Jacobi cycle per HSS step is too inexact over ceil(k) = 80 steps (FGMRES
     # stagnates); two cycles per step converge.
-    w2 = inputs.workload(WORKLOAD, 2.0)
+    w2 = inputs.workload(w.name, 2.0)
     with hh.Problem(w2.dim, w2.n, w2.k, w2.delta, w2.delta_hat, w2.bc, hh.default_options(cycles_per_hss=2)) as p2:
         p2.solve(b, w.tol)
         torch.cuda.synchronize()
@@ -397,7 +409,7 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed):
     try:
         v, cycles, dt = oracle_vcycle_rate(w)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                               "sample": f"{cycles} HSS iterations (one V-cycle each) of the 513^2 k=80 "
+                               "sample": f"{cycles} HSS iterations (one V-cycle each) of the {w.name} "
                                          f"workload in {dt:.1f} s, FP64 scipy CSR"}
     except Exception as e:  # the CPU leg must not hide the GPU numbers
         out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle", "sample": f"failed: {e}"}

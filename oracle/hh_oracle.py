@@ -229,6 +229,38 @@ def assemble(grid):
     return _mask(grid, K), _mask(grid, M), _mask(grid, MG.tocsr())
 
 
+def apply_elementwise(grid, coeff, x):
+    """(c_K K + c_M M + c_G M_Gamma) x without assembling: sum over cells of the element
+    matrices times the cell's nodal values, plus the Sommerfeld face terms; rows and
+    columns of Dirichlet nodes masked.  Same operator as ``combine(assemble(grid), coeff)``,
+    for grids too large to assemble (millions of nodes)."""
+    dim, N = grid.dim, grid.N
+    cK, cM, cG = coeff
+    Ke, Me = element_matrices(dim, grid.h)
+    Ae = cK * Ke + cM * Me
+    free = grid.free()
+    xm = np.where(free, np.asarray(x, dtype=complex), 0.0)
+    cells, g = _cell_vertex_globals(grid)
+    y = np.zeros(N, dtype=complex)
+    xe = xm[g]                       # (ncells, 2^dim)
+    ye = xe @ Ae.T                   # element contributions
+    for A in range(g.shape[1]):
+        y += np.bincount(g[:, A], weights=ye[:, A].real, minlength=N) + \
+            1j * np.bincount(g[:, A], weights=ye[:, A].imag, minlength=N)
+    for axis in range(dim):
+        for side in (0, 1):
+            if grid.bc[2 * axis + side] != SOMMERFELD:
+                continue
+            on = cells[:, axis] == (0 if side == 0 else grid.n - 1)
+            Fe = cG * face_mass_matrix(dim, grid.h, axis, side)
+            gf = g[on]
+            yf = xm[gf] @ Fe.T
+            for A in range(gf.shape[1]):
+                y += np.bincount(gf[:, A], weights=yf[:, A].real, minlength=N) + \
+                    1j * np.bincount(gf[:, A], weights=yf[:, A].imag, minlength=N)
+    return np.where(free, y, 0.0)
+
+
 # ---------------------------------------------------------------------------
 # Operator coefficient triples (c_K, c_M, c_Gamma): op = c_K K + c_M M + c_Gamma M_Gamma
 # ---------------------------------------------------------------------------

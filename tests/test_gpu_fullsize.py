@@ -1,0 +1,99 @@
+"""Parity at the full sizes of the benchmark workloads, in the benchmark's launch configuration
+(default options: 4 levels, V(2,2), complex64 V-cycles, CUDA graphs, programmatic launch,
+cluster coarse solve).
+
+2D 512^2, k = 80 (263,169 nodes): everything against the oracle's assembled CSR matrices and
+sparse LU.  3D 128^3, k = 40 (2,146,689 nodes): too large to assemble in the oracle; operator
+applies and the FP64 residual of the solve are recomputed with the oracle's element-by-element
+apply, and the discrete energy identity Im(u^H b) = -k u^H M_Gamma u (delta = 0) is checked
+up to the residual.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hh_oracle as O
+from paper_2506_18694_gb300 import hh, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def c2():
+    w = inputs.workload("2d_n512_k80")
+    g = O.Grid(w.dim, w.n, w.bc)
+    prob = O.Problem(g, w.k, w.delta, w.delta_hat, O.Options())
+    f = inputs.gaussian_source(w.dim, w.n, w.centre, w.sigma)
+    b = O.load_vector_nodal(g, f)
+    return w, g, prob, f, b
+
+
+def test_c2_kernels_full_vectors(libhh, c2):
+    w, g, prob, f, b = c2
+    with hh.Problem(w.dim, w.n, w.k, w.delta, w.delta_hat, w.bc) as p:
+        x = inputs.random_complex(g.N, 300) * g.free()
+        for prec, dt, tol in ((hh.HH_C128, torch.complex128, 1e-12), (hh.HH_C64, torch.complex64, 2e-6)):
+            xd = torch.from_numpy(x).to(dt).cuda()
+            assert rel(p.apply(0, "AL", xd).cpu().numpy(), prob.AL[0] @ x) <= tol
+            assert rel(p.jacobi(0, xd, xd.clone()).cpu().numpy(), prob.jacobi(0, x, x)) <= tol
+        v = p.vcycle(torch.from_numpy(x).to(torch.complex64).cuda()).cpu().numpy()
+        assert rel(v, prob.vcycle(0, x)) <= 2e-5
+
+
+@pytest.mark.parametrize("dh,cycles", [("k", 1), (2.0, 2)])
+def test_c2_solve_against_lu(libhh, c2, dh, cycles):
+    w0, g, _, f, b = c2
+    w = inputs.workload("2d_n512_k80", dh)
+    prob = O.Problem(g, w.k, w.delta, w.delta_hat, O.Options(levels=1))
+    with hh.Problem(w.dim, w.n, w.k, w.delta, w.delta_hat, w.bc, hh.default_options(cycles_per_hss=cycles)) as p:
+        bd = p.load_vector(torch.from_numpy(f).cuda())
+        assert rel(bd.cpu().numpy(), b) <= 1e-13
+        u, info = p.solve(bd, 1e-8)
+        u = u.cpu().numpy()
+    res = np.linalg.norm(b - prob.B @ u) / np.linalg.norm(b)
+    assert info.rel_residual <= 1e-8 and res <= 1.01e-8
+    assert rel(u, prob.lu("B")(b)) <= 1e-6
+
+
+@pytest.fixture(scope="module")
+def c3():
+    w = inputs.workload("3d_n128_k40")
+    g = O.Grid(w.dim, w.n, w.bc)
+    f = inputs.gaussian_source(w.dim, w.n, w.centre, w.sigma)
+    b = O.apply_elementwise(g, (0.0, 1.0, 0.0), f)
+    return w, g, f, b
+
+
+def test_c3_apply_full_vectors(libhh, c3):
+    w, g, f, b = c3
+    x = inputs.random_complex(g.N, 301)
+    with hh.Problem(w.dim, w.n, w.k, w.delta, w.delta_hat, w.bc) as p:
+        for op, coeff in (("AL", O.coeff_AL(w.k, w.delta_hat)), ("B", O.coeff_B(w.k, w.delta))):
+            ref = O.apply_elementwise(g, coeff, x)
+            for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 2e-6)):
+                y = p.apply(0, op, torch.from_numpy(x).to(dt).cuda()).cpu().numpy()
+                assert rel(y, ref) <= tol, (op, dt)
+
+
+@pytest.mark.parametrize("dh,cycles,restart", [("k", 1, 60), (2.0, 2, 30)])
+def test_c3_solve_residual_and_energy(libhh, c3, dh, cycles, restart):
+    w0, g, f, b = c3
+    w = inputs.workload("3d_n128_k40", dh)
+    opts = hh.default_options(cycles_per_hss=cycles, restart=restart)
+    with hh.Problem(w.dim, w.n, w.k, w.delta, w.delta_hat, w.bc, opts) as p:
+        bd = p.load_vector(torch.from_numpy(f).cuda())
+        assert rel(bd.cpu().numpy(), b) <= 1e-13
+        u, info = p.solve(bd, 1e-8)
+        u = u.cpu().numpy()
+    r = b - O.apply_elementwise(g, O.coeff_B(w.k, w.delta), u)
+    res = np.linalg.norm(r) / np.linalg.norm(b)
+    assert info.rel_residual <= 1e-8 and res <= 1.01e-8
+    assert np.all(u[~g.free()] == 0)
+    # Im(u^H b) = -k u^H M_Gamma u + Im(u^H r)  (K, M, M_Gamma real symmetric, delta = 0)
+    mg = np.real(np.vdot(u, O.apply_elementwise(g, (0.0, 0.0, 1.0), u)))
+    gap = abs(np.imag(np.vdot(u, b)) + w.k * mg)
+    assert gap <= 1.01 * np.linalg.norm(u) * np.linalg.norm(r) + 1e-12 * abs(w.k * mg)

@@ -476,3 +476,14 @@ def test_jacobi_sweeps_converge_to_lu():
         x = prob.jacobi(0, b, x)
     ex = prob.lu("AL")(b)
     assert np.linalg.norm(x - ex) <= 1e-9 * np.linalg.norm(ex)
+
+
+@pytest.mark.parametrize("dim,n,bc", [(2, 6, (S, D, S, S)), (3, 4, (S, S, S, S, D, S))])
+def test_apply_elementwise_equals_assembled(dim, n, bc):
+    """The matrix-free element loop applies the same operator as the assembled CSR matrix."""
+    g = O.Grid(dim, n, bc)
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(g.N) + 1j * rng.standard_normal(g.N)
+    for coeff in (O.coeff_AL(7.0, 2.0), O.coeff_B(7.0, 0.0), (1.0, 0.0, 0.0), (0.0, 0.0, 1.0)):
+        ref = O.combine(O.assemble(g), coeff) @ (x * g.free())
+        assert np.abs(O.apply_elementwise(g, coeff, x) - ref).max() <= 1e-12 * np.abs(ref).max()
