@@ -101,6 +101,8 @@ typedef struct {
     int coarse_cluster_nodes; /* the coarsest level, if it has at most this many nodes and   */
                               /* fits, runs all its sweeps in one thread-block cluster with  */
                               /* the level in distributed shared memory; 0 = never           */
+    int tile_rows;       /* rows (2D) / z-planes (3D) per warp tile of the stencil kernels:   */
+                         /* 2, 4 or 8; 0 = chosen from the grid size                          */
 } hh_options;
 
 typedef struct {

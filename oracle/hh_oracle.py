@@ -261,6 +261,28 @@ def apply_elementwise(grid, coeff, x):
     return np.where(free, y, 0.0)
 
 
+def diag_elementwise(grid, coeff):
+    """diag(c_K K + c_M M + c_G M_Gamma) from the element and face matrices' diagonals (no
+    assembly); zero at Dirichlet nodes."""
+    dim, N = grid.dim, grid.N
+    cK, cM, cG = coeff
+    Ke, Me = element_matrices(dim, grid.h)
+    de = np.diag(cK * Ke + cM * Me)
+    cells, g = _cell_vertex_globals(grid)
+    d = np.zeros(N, dtype=complex)
+    for A in range(g.shape[1]):
+        d += np.bincount(g[:, A], minlength=N) * de[A]
+    for axis in range(dim):
+        for side in (0, 1):
+            if grid.bc[2 * axis + side] != SOMMERFELD:
+                continue
+            on = cells[:, axis] == (0 if side == 0 else grid.n - 1)
+            df = cG * np.diag(face_mass_matrix(dim, grid.h, axis, side))
+            for A in range(g.shape[1]):
+                d += np.bincount(g[on][:, A], minlength=N) * df[A]
+    return np.where(grid.free(), d, 0.0)
+
+
 # ---------------------------------------------------------------------------
 # Operator coefficient triples (c_K, c_M, c_Gamma): op = c_K K + c_M M + c_Gamma M_Gamma
 # ---------------------------------------------------------------------------

@@ -105,6 +105,7 @@ template <typename T> struct MArgs {
     Cx<T> alpha, beta;
     T omega;
     int xzero;           // 1: x is identically zero
+    int tile_rows;       // 0: automatic; else 2, 4 or 8 rows (2D) / planes (3D) per tile
     // filled by the launcher
     T h, ih;
     int rows;

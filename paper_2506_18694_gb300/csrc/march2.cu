@@ -73,44 +73,82 @@ __device__ __forceinline__ Cx<T> field2(const MArgs<T>& a, int ic, int rc, const
     }
 }
 
-// One warp: a strip of 30 output columns (lanes 1..30; lanes 0 and 31 are the halo) and
-// ROWS consecutive output rows (RESID_RESTRICT: ROWS coarse rows, 2 ROWS + 1 residual
-// rows, 28 fine columns per strip).  All stencil rows of the chunk are loaded before any
-// arithmetic so that every load of the warp is in flight at once.  Nodes at least two
+// One warp tile: a strip of 30 output columns (lanes 1..30; lanes 0 and 31 are the halo)
+// and ROWS consecutive output rows (RESID_RESTRICT: ROWS coarse rows, 2 ROWS + 1 residual
+// rows, 28 fine columns per strip).  tile_load issues every load of the tile (all in
+// flight at once); tile_compute does the arithmetic and the stores.  Nodes at least two
 // cells away from the boundary (none of their neighbours is a boundary node) use the
-// three interior weights of the operator (centre, edge, diagonal) and the interior
-// diagonal; the rest build their row from the 1D weight triples.
+// interior weights of the operator (centre, edge, diagonal) and the interior diagonal; the
+// rest build their row from the 1D weight triples.
+template <typename T, int MODE, int ROWS> struct Tile2 {
+    static constexpr bool RR = MODE == M_RESID_RESTRICT;
+    static constexpr int NR = RR ? 2 * ROWS + 3 : ROWS + 2;  // stencil rows
+    static constexpr int NZ = NR - 2;                         // rows whose right side is read
+    static constexpr bool NEEDZ = MODE != M_APPLY && MODE != M_JACOBI2_ZERO;
+    Cx<T> fv[NR];  // stencil field (M_JACOBI2_ZERO: filled from bv in tile_compute)
+    Cx<T> bv[NR];  // right side on every stencil row (M_JACOBI2_ZERO only)
+    Cx<T> zv[NZ];  // right side / second vector on the output rows
+};
+
 template <typename T, int MODE, int ROWS>
-__global__ void __launch_bounds__(128) k_march2(MArgs<T> a) {
-    pdl_entry();
-    constexpr bool RR = MODE == M_RESID_RESTRICT;
-    constexpr int NR = RR ? 2 * ROWS + 3 : ROWS + 2;  // stencil rows
-    constexpr int NZ = NR - 2;                         // rows whose right side is read
-    constexpr bool NEEDZ = MODE != M_APPLY && MODE != M_JACOBI2_ZERO;
+__device__ __forceinline__ void tile_load(const MArgs<T>& a, int strip, int cy, Tile2<T, MODE, ROWS>& tl) {
+    using TL = Tile2<T, MODE, ROWS>;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
+    const int n = a.g.n;
+    const int i = strip * (TL::RR ? 28 : 30) + lane - (TL::RR ? 2 : 1);
+    const int base = cy * ROWS;
+    const int rfirst = TL::RR ? 2 * base - 2 : base - 1;
+    const int ic = clampi(i, 0, n);
+#pragma unroll
+    for (int t = 0; t < TL::NR; ++t) {
+        const int rc = clampi(rfirst + t, 0, n);
+        if (MODE == M_JACOBI2_ZERO) {
+            tl.bv[t] = ld<T>(a.z, (long long)rc * a.g.nn + ic);
+        } else if (MODE == M_PROLONG_JACOBI) {
+            const Row1<T> rx = row1<T>(ic, n, a.g.dir[0], a.g.dir[1], a.h, a.ih);
+            Cx<T> dummy;
+            tl.fv[t] = field2<T, MODE>(a, ic, rc, rx, a.h, a.ih, &dummy);
+        } else {
+            tl.fv[t] = a.xzero ? cx<T>(0, 0) : ld<T>(a.x, (long long)rc * a.g.nn + ic);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < TL::NZ; ++t)
+        tl.zv[t] = TL::NEEDZ ? ld<T>(a.z, (long long)clampi(rfirst + 1 + t, 0, n) * a.g.nn + ic) : cx<T>(0, 0);
+}
+
+template <typename T, int MODE, int ROWS>
+__device__ __forceinline__ void tile_compute(const MArgs<T>& a, int strip, int cy, Tile2<T, MODE, ROWS>& tl) {
+    using TL = Tile2<T, MODE, ROWS>;
+    constexpr bool RR = TL::RR;
+    constexpr int NR = TL::NR;
+    const int lane = threadIdx.x & 31;
     const int n = a.g.n;
     const int nc = n >> 1;
     const T h = a.h, ih = a.ih;
-    const int i = blockIdx.x * (RR ? 28 : 30) + lane - (RR ? 2 : 1);
-    const int base = (blockIdx.y * 4 + warp) * ROWS;  // first output row (coarse row if RR)
-    if (base > (RR ? nc : n)) return;
+    const int i = strip * (RR ? 28 : 30) + lane - (RR ? 2 : 1);
+    const int base = cy * ROWS;
     const int rfirst = RR ? 2 * base - 2 : base - 1;
     const int ic = clampi(i, 0, n);
     const bool col_in = (i >= 0 && i <= n);
     const bool col_fast = (i >= 2 && i <= n - 2);
     const Row1<T> rx = row1<T>(ic, n, a.g.dir[0], a.g.dir[1], h, ih);
 
-    Cx<T> fv[NR], bv[NR], zv[NZ];
+    if (MODE == M_JACOBI2_ZERO) {
+        // first sweep from x = 0: x1 = omega D^{-1} b, zero at Dirichlet nodes
 #pragma unroll
-    for (int t = 0; t < NR; ++t) {
-        bv[t] = cx<T>(0, 0);
-        fv[t] = field2<T, MODE>(a, ic, clampi(rfirst + t, 0, n), rx, h, ih, &bv[t]);
+        for (int t = 0; t < NR; ++t) {
+            const int rc = clampi(rfirst + t, 0, n);
+            if (ic >= 1 && ic <= n - 1 && rc >= 1 && rc <= n - 1) {
+                tl.fv[t] = cmul(a.wdinv, tl.bv[t]);
+            } else {
+                const Row1<T> ry = row1<T>(rc, n, a.g.dir[2], a.g.dir[3], h, ih);
+                tl.fv[t] = (rx.masked || ry.masked) ? cx<T>(0, 0)
+                                                   : a.omega * cmul(cinv(diag2(rx, ry, a.op)), tl.bv[t]);
+            }
+        }
     }
-#pragma unroll
-    for (int t = 0; t < NZ; ++t)
-        zv[t] = NEEDZ ? ld<T>(a.z, (long long)clampi(rfirst + 1 + t, 0, n) * a.g.nn + ic) : cx<T>(0, 0);
-
+    const Cx<T>* fv = tl.fv;
     Cx<T> lf[NR], rg[NR];
 #pragma unroll
     for (int t = 0; t < NR; ++t) {
@@ -156,7 +194,7 @@ __global__ void __launch_bounds__(128) k_march2(MArgs<T> a) {
                                                                  : a.omega * cinv(diag2(rx, ry, a.opd));
         }
         if (RR) {
-            const Cx<T> res = (row_in && col_in && !masked) ? zv[t - 1] - ax : cx<T>(0, 0);
+            const Cx<T> res = (row_in && col_in && !masked) ? tl.zv[t - 1] - ax : cx<T>(0, 0);
             // full weighting along x: r(i) + (r(i-1) + r(i+1)) / 2
             const Cx<T> rr = fma_r(T(0.5), shfl_up(res) + shfl_dn(res), res);
             if ((t & 1) == 0) {  // j = 2 base - 1 + t - 1 is even: centre row of coarse row j/2
@@ -165,7 +203,7 @@ __global__ void __launch_bounds__(128) k_march2(MArgs<T> a) {
                 if (t >= 3) {  // odd row closes coarse row (j - 1)/2
                     acc = fma_r(T(0.5), rr, acc);
                     const int J = (j - 1) >> 1;
-                    const int I = blockIdx.x * 14 + ((lane - 2) >> 1);
+                    const int I = strip * 14 + ((lane - 2) >> 1);
                     if (lane >= 2 && lane <= 28 && !(lane & 1) && I <= nc && J <= nc) {
                         const bool cm = (I == 0 && a.g.dir[0]) || (I == nc && a.g.dir[1]) ||
                                         (J == 0 && a.g.dir[2]) || (J == nc && a.g.dir[3]);
@@ -185,20 +223,50 @@ __global__ void __launch_bounds__(128) k_march2(MArgs<T> a) {
         if (MODE == M_APPLY) {
             st<T>(a.y, p, ax);
         } else if (MODE == M_AXPBY) {
-            st<T>(a.y, p, fma_c(a.alpha, ax, cmul(a.beta, zv[t - 1])));
+            st<T>(a.y, p, fma_c(a.alpha, ax, cmul(a.beta, tl.zv[t - 1])));
         } else if (MODE == M_HSS_FIRST) {
-            const Cx<T> rhs = fma_c(a.alpha, ax, cmul(a.beta, zv[t - 1]));
+            const Cx<T> rhs = fma_c(a.alpha, ax, cmul(a.beta, tl.zv[t - 1]));
             st<T>(a.y, p, rhs);
             st<T>(a.y2, p, cmul(dinv_w, rhs));
         } else {
             // Jacobi update of the field: field + omega D^{-1} (b - op field)
-            const Cx<T> b = (MODE == M_JACOBI2_ZERO) ? bv[t] : zv[t - 1];
+            const Cx<T> b = (MODE == M_JACOBI2_ZERO) ? tl.bv[t] : tl.zv[t - 1];
             st<T>(a.y, p, fma_c(dinv_w, b - ax, fv[t]));
         }
     }
 }
 
-// Rows per warp: the largest that still leaves about 24 warps per SM (loads in flight).
+// One tile per warp; grid (strips, ceil(chunks / 4)).
+template <typename T, int MODE, int ROWS>
+__global__ void __launch_bounds__(128) k_march2(MArgs<T> a, int chunks) {
+    pdl_entry();
+    const int cy = blockIdx.y * 4 + (threadIdx.x >> 5);
+    if (cy >= chunks) return;
+    Tile2<T, MODE, ROWS> tl;
+    tile_load<T, MODE, ROWS>(a, blockIdx.x, cy, tl);
+    tile_compute<T, MODE, ROWS>(a, blockIdx.x, cy, tl);
+}
+
+// Persistent form for grids with many more tiles than resident warps: each warp walks the
+// tiles c, c + W, c + 2W, ... (strip fastest) and issues the loads of its next tile before
+// computing the current one, so that its loads stay in flight while it computes.
+template <typename T, int MODE, int ROWS>
+__global__ void __launch_bounds__(128) k_march2p(MArgs<T> a, int strips, int tiles) {
+    pdl_entry();
+    const int W = gridDim.x * 4;
+    int c = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (c >= tiles) return;
+    Tile2<T, MODE, ROWS> cur;
+    tile_load<T, MODE, ROWS>(a, c % strips, c / strips, cur);
+    for (; c < tiles; c += W) {
+        Tile2<T, MODE, ROWS> nxt;
+        const int cn = c + W;
+        if (cn < tiles) tile_load<T, MODE, ROWS>(a, cn % strips, cn / strips, nxt);
+        tile_compute<T, MODE, ROWS>(a, c % strips, c / strips, cur);
+        cur = nxt;
+    }
+}
+
 // Interior stencil weights of op by neighbour class and omega / (interior diagonal of opd),
 // in double precision.  Q1 on a uniform grid: 2D stiffness 8/3, -1/3, -1/3 and mass
 // h^2 (16, 4, 1)/36 for the centre, edge and diagonal neighbours; 3D stiffness
@@ -234,6 +302,20 @@ void interior_weights(MArgs<T>& a) {
 template void interior_weights<float>(MArgs<float>&);
 template void interior_weights<double>(MArgs<double>&);
 
+template <typename T, int MODE, int ROWS>
+static cudaError_t run2(const MArgs<T>& a, int strips, int chunks, cudaStream_t s) {
+    const long long tiles = (long long)strips * chunks;
+    // resident tiles: 152 SMs x 4 blocks x 4 warps; persistent once there are several per warp
+    const long long resident = 152LL * 4 * 4;
+    if (MODE != M_PROLONG_JACOBI && tiles >= 4 * resident && tiles < (1LL << 31)) {
+        const unsigned blocks = (unsigned)(resident / 4);
+        return klaunch(k_march2p<T, MODE, ROWS>, dim3(blocks), dim3(128), 0, s, 1, a, strips, (int)tiles);
+    }
+    dim3 grd((unsigned)strips, (unsigned)((chunks + 3) / 4), 1);
+    return klaunch(k_march2<T, MODE, ROWS>, grd, dim3(128), 0, s, 1, a, chunks);
+}
+
+// Rows per warp tile: the largest that still leaves about 24 warps per SM (loads in flight).
 template <typename T, int MODE>
 static cudaError_t go2(MArgs<T> a, cudaStream_t s) {
     a.h = T(a.g.h);
@@ -242,26 +324,21 @@ static cudaError_t go2(MArgs<T> a, cudaStream_t s) {
     const long long want = 152LL * 24;
     if constexpr (MODE == M_RESID_RESTRICT) {
         const int nnc = a.g.n / 2 + 1;
-        const long long strips = (nnc + 13) / 14;
-        const int rows = (strips * ((nnc + 3) / 4) >= want) ? 4 : 2;
-        const int chunks = (nnc + rows - 1) / rows;
-        dim3 grd((unsigned)strips, (unsigned)((chunks + 3) / 4), 1);
-        if (rows == 4) return klaunch(k_march2<T, MODE, 4>, dim3(grd), dim3(128), 0, s, 1, a);
-        return klaunch(k_march2<T, MODE, 2>, dim3(grd), dim3(128), 0, s, 1, a);
+        const int strips = (nnc + 13) / 14;
+        int rows = ((long long)strips * ((nnc + 3) / 4) >= want) ? 4 : 2;
+        if (a.tile_rows == 2 || a.tile_rows == 4) rows = a.tile_rows;
+        if (rows == 4) return run2<T, MODE, 4>(a, strips, (nnc + 3) / 4, s);
+        return run2<T, MODE, 2>(a, strips, (nnc + 1) / 2, s);
     } else {
-        const long long strips = (a.g.nn + 29) / 30;
+        const int strips = (a.g.nn + 29) / 30;
         int rows = 2;
-        if (sizeof(T) == 4 && strips * ((a.g.nn + 7) / 8) >= want) rows = 8;
-        else if (strips * ((a.g.nn + 3) / 4) >= want) rows = 4;
-        const int chunks = (a.g.nn + rows - 1) / rows;
-        dim3 grd((unsigned)strips, (unsigned)((chunks + 3) / 4), 1);
+        if ((long long)strips * ((a.g.nn + 3) / 4) >= want) rows = 4;
+        if (a.tile_rows == 2 || a.tile_rows == 4 || (a.tile_rows == 8 && sizeof(T) == 4)) rows = a.tile_rows;
         if constexpr (sizeof(T) == 4) {
-            if (rows == 8) {
-                return klaunch(k_march2<T, MODE, 8>, dim3(grd), dim3(128), 0, s, 1, a);
-            }
+            if (rows == 8) return run2<T, MODE, 8>(a, strips, (a.g.nn + 7) / 8, s);
         }
-        if (rows == 4) return klaunch(k_march2<T, MODE, 4>, dim3(grd), dim3(128), 0, s, 1, a);
-        return klaunch(k_march2<T, MODE, 2>, dim3(grd), dim3(128), 0, s, 1, a);
+        if (rows == 4) return run2<T, MODE, 4>(a, strips, (a.g.nn + 3) / 4, s);
+        return run2<T, MODE, 2>(a, strips, (a.g.nn + 1) / 2, s);
     }
 }
 

@@ -127,25 +127,24 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(MArgs<T> a) {
     if (!out_row || !(lane >= 1 && lane <= 30) || i > n || j > n) return;
     const bool colrow_fast = i >= 2 && i <= n - 2 && j >= 2 && j <= n - 2;
     const int wm = w - 1, wp = w + 1;
+    // rows j-1 + j+1 summed (value and x-sum) per plane, in a rolling window of 3 planes
+    auto ysum = [&](const vec2<T>* arr, int tpl) {
+        return ld<T>(arr, (wm * NP + tpl) * 32 + lane) + ld<T>(arr, (wp * NP + tpl) * 32 + lane);
+    };
+    Cx<T> vy0 = ysum(sv, 0), vy1 = ysum(sv, 1), sy0 = ysum(ss, 0), sy1 = ysum(ss, 1);
 #pragma unroll
     for (int t = 0; t < R; ++t) {
         const int l = l0 + t;
         if (l > n) break;
         const int tp = t + 1;  // local plane of the output
+        const Cx<T> vy2 = ysum(sv, tp + 1), sy2 = ysum(ss, tp + 1);
         const long long p = ((long long)l * nn + j) * nn + i;
         Cx<T> ax, dinv_w;
         bool masked = false;
         if (colrow_fast && l >= 2 && l <= n - 2) {
-            // rows j-1 and j+1 (value and x-sum) on planes l-1, l, l+1
-            Cx<T> vy[3], sy[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                vy[c] = ld<T>(sv, (wm * NP + tp - 1 + c) * 32 + lane) + ld<T>(sv, (wp * NP + tp - 1 + c) * 32 + lane);
-                sy[c] = ld<T>(ss, (wm * NP + tp - 1 + c) * 32 + lane) + ld<T>(ss, (wp * NP + tp - 1 + c) * 32 + lane);
-            }
-            const Cx<T> face = xs[tp] + vy[1] + (fv[tp - 1] + fv[tp + 1]);
-            const Cx<T> edge = sy[1] + (xs[tp - 1] + xs[tp + 1]) + (vy[0] + vy[2]);
-            const Cx<T> corner = sy[0] + sy[2];
+            const Cx<T> face = xs[tp] + vy1 + (fv[tp - 1] + fv[tp + 1]);
+            const Cx<T> edge = sy1 + (xs[tp - 1] + xs[tp + 1]) + (vy0 + vy2);
+            const Cx<T> corner = sy0 + sy2;
             ax = fma_c(a.iw[3], corner, fma_c(a.iw[2], edge, fma_c(a.iw[1], face, cmul(a.iw[0], fv[tp]))));
             dinv_w = a.wdinv;
         } else {
@@ -188,9 +187,7 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(MArgs<T> a) {
         if (masked) {
             st<T>(a.y, p, cx<T>(0, 0));
             if (MODE == M_HSS_FIRST) st<T>(a.y2, p, cx<T>(0, 0));
-            continue;
-        }
-        if (MODE == M_APPLY) {
+        } else if (MODE == M_APPLY) {
             st<T>(a.y, p, ax);
         } else if (MODE == M_AXPBY) {
             st<T>(a.y, p, fma_c(a.alpha, ax, cmul(a.beta, zv[t])));
@@ -201,6 +198,10 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(MArgs<T> a) {
         } else {
             st<T>(a.y, p, fma_c(dinv_w, zv[t] - ax, fv[tp]));
         }
+        vy0 = vy1;
+        vy1 = vy2;
+        sy0 = sy1;
+        sy1 = sy2;
     }
 }
 
@@ -222,7 +223,9 @@ static cudaError_t pick3(MArgs<T> a, cudaStream_t s) {
     // more planes per tile on large grids (fewer halo planes), fewer on small ones (more CTAs)
     const long long ctas4 = (long long)((a.g.nn + 29) / 30) * ((a.g.nn + 5) / 6) * ((a.g.nn + 3) / 4);
     if constexpr (sizeof(T) == 4) {
-        if (ctas4 >= 152LL * 16) return go3<T, MODE, 8>(a, s);
+        if (a.tile_rows == 2) return go3<T, MODE, 2>(a, s);
+        if (a.tile_rows == 4) return go3<T, MODE, 4>(a, s);
+        if (a.tile_rows == 8 || ctas4 >= 152LL * 16) return go3<T, MODE, 8>(a, s);
         return go3<T, MODE, 4>(a, s);
     } else {
         return go3<T, MODE, 2>(a, s);

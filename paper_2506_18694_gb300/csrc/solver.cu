@@ -237,6 +237,7 @@ struct MG {
         a.op = op;
         a.opd = al;
         a.omega = omega;
+        a.tile_rows = p->o.tile_rows;
         return a;
     }
 
@@ -529,6 +530,7 @@ hh_status op_axpby(hh_problem* p, int l, const Triple& t, const hh::vec2<T>* x, 
     a.y = y;
     a.alpha = alpha;
     a.beta = beta;
+    a.tile_rows = p->o.tile_rows;
     const int mode = z ? hh::M_AXPBY : hh::M_APPLY;
     HH_LAUNCH(p->grid.dim == 2 ? hh::launch_march2<T>(mode, a, st) : hh::launch_march3<T>(mode, a, st));
     return HH_OK;
@@ -686,6 +688,7 @@ void hh_options_default(hh_options* o) {
     o->use_graphs = 1;
     o->use_pdl = 1;
     o->coarse_cluster_nodes = 100000;
+    o->tile_rows = 0;
 }
 
 static hh_status check_args(const hh_grid* grid, double k, double delta, double dh, const int* bc,
@@ -706,6 +709,8 @@ static hh_status check_args(const hh_grid* grid, double k, double delta, double 
     if (!(o->theta >= 0) || !(o->omega >= 0) || !(o->omega < 2)) return fail(HH_ERR_INVALID, "theta >= 0 and 0 <= omega < 2 required");
     if (o->precision != HH_C64 && o->precision != HH_C128) return fail(HH_ERR_INVALID, "bad precision");
     if (o->coarse_cluster_nodes < 0) return fail(HH_ERR_INVALID, "coarse_cluster_nodes < 0");
+    if (o->tile_rows != 0 && o->tile_rows != 2 && o->tile_rows != 4 && o->tile_rows != 8)
+        return fail(HH_ERR_INVALID, "tile_rows must be 0, 2, 4 or 8");
     if (!bc) return fail(HH_ERR_INVALID, "null bc");
     for (int s = 0; s < 2 * grid->dim; ++s)
         if (bc[s] != HH_BC_SOMMERFELD && bc[s] != HH_BC_DIRICHLET) return fail(HH_ERR_INVALID, "bad boundary tag");

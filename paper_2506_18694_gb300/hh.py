@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
         ("nu_post", ctypes.c_int), ("nu_coarse", ctypes.c_int), ("cycles_per_hss", ctypes.c_int),
         ("omega", ctypes.c_double), ("restart", ctypes.c_int), ("max_outer", ctypes.c_int),
         ("precision", ctypes.c_int), ("use_graphs", ctypes.c_int), ("use_pdl", ctypes.c_int),
-        ("coarse_cluster_nodes", ctypes.c_int),
+        ("coarse_cluster_nodes", ctypes.c_int), ("tile_rows", ctypes.c_int),
     ]
 
 

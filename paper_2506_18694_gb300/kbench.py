@@ -32,6 +32,7 @@ def main(argv=None):
     ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--rows", type=int, default=0, help="tile rows/planes (0 = automatic)")
     args = ap.parse_args(argv)
     prec = hh.HH_C64 if args.prec == "c64" else hh.HH_C128
     dt = torch.complex64 if prec == hh.HH_C64 else torch.complex128
@@ -39,7 +40,8 @@ def main(argv=None):
     k = 80.0
     bc = [hh.SOMMERFELD] * (2 * args.dim)
     levels = 4 if args.kernel == "vcycle" else 2
-    p = hh.Problem(args.dim, args.n, k, 0.0, k, bc, hh.default_options(precision=prec, levels=levels, restart=1))
+    p = hh.Problem(args.dim, args.n, k, 0.0, k, bc,
+                   hh.default_options(precision=prec, levels=levels, restart=1, tile_rows=args.rows))
     N = p.nodes()
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.randn(N, dtype=dt, device="cuda", generator=g)
@@ -63,7 +65,8 @@ def main(argv=None):
     end.record(s)
     end.synchronize()
     t = start.elapsed_time(end) / args.reps / 1e3
-    out = {"kernel": args.kernel, "dim": args.dim, "n": args.n, "nodes": N, "prec": args.prec, "us": t * 1e6}
+    out = {"kernel": args.kernel, "dim": args.dim, "n": args.n, "nodes": N, "prec": args.prec, "rows": args.rows,
+           "us": t * 1e6}
     if BYTES[args.kernel] is not None:
         byt = BYTES[args.kernel](e, args.dim) * N
         out.update({"bytes": byt, "gbs": byt / t / 1e9})

@@ -97,3 +97,25 @@ def test_c3_solve_residual_and_energy(libhh, c3, dh, cycles, restart):
     mg = np.real(np.vdot(u, O.apply_elementwise(g, (0.0, 0.0, 1.0), u)))
     gap = abs(np.imag(np.vdot(u, b)) + w.k * mg)
     assert gap <= 1.01 * np.linalg.norm(u) * np.linalg.norm(r) + 1e-12 * abs(w.k * mg)
+
+
+def test_large_2d_grid_persistent_kernels(libhh):
+    """2049^2 nodes: enough tiles for the persistent, load-ahead form of the 2D kernels."""
+    n, k, dh, bc = 2048, 160.0, 160.0, (0, 1, 0, 0)
+    g = O.Grid(2, n, bc)
+    coeff = O.coeff_AL(k, dh)
+    x = inputs.random_complex(g.N, 400) * g.free()
+    b = inputs.random_complex(g.N, 401) * g.free()
+    ax = O.apply_elementwise(g, coeff, x)
+    d = O.diag_elementwise(g, coeff)
+    d[~g.free()] = 1.0
+    omega = 0.6
+    jac = np.where(g.free(), x + omega * (b - ax) / d, 0.0)
+    P = O.prolongation(g)
+    rc_ref = P.T @ (b - ax)
+    with hh.Problem(2, n, k, 0.0, dh, bc, hh.default_options(levels=2)) as p:
+        for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 2e-6)):
+            xd, bd = torch.from_numpy(x).to(dt).cuda(), torch.from_numpy(b).to(dt).cuda()
+            assert rel(p.apply(0, "AL", xd).cpu().numpy(), ax) <= tol
+            assert rel(p.jacobi(0, bd, xd).cpu().numpy(), jac) <= tol
+            assert rel(p.residual_restrict(0, bd, xd).cpu().numpy(), rc_ref) <= 10 * tol

@@ -155,6 +155,21 @@ def test_vcycle_launch_modes(libhh, prec, pdl, cluster, dim, n, L, bc):
 
 
 @pytest.mark.parametrize("prec", [hh.HH_C128, hh.HH_C64])
+@pytest.mark.parametrize("rows", [2, 4, 8])
+@pytest.mark.parametrize("dim,n,bc", [(2, 72, (S, D, S, S)), (3, 24, (S, S, D, S, S, S))])
+def test_tile_rows(libhh, prec, rows, dim, n, bc):
+    """Every tile height gives the same apply, sweep and residual-restriction."""
+    g = O.Grid(dim, n, bc)
+    prob = O.Problem(g, 6.0, 0.0, 3.0, O.Options(levels=2))
+    with hh.Problem(dim, n, 6.0, 0.0, 3.0, bc, hh.default_options(levels=2, tile_rows=rows)) as p:
+        x, b = rand(g, 110), rand(g, 111)
+        assert rel(to_np(p.apply(0, "AL", to_dev(x, prec))), prob.AL[0] @ x) <= TOL[prec]
+        assert rel(to_np(p.jacobi(0, to_dev(b, prec), to_dev(x, prec))), prob.jacobi(0, b, x)) <= TOL[prec]
+        rc = to_np(p.residual_restrict(0, to_dev(b, prec), to_dev(x, prec)))
+        assert rel(rc, prob.P[0].T @ (b - prob.AL[0] @ x)) <= TOL[prec] * 10
+
+
+@pytest.mark.parametrize("prec", [hh.HH_C128, hh.HH_C64])
 @pytest.mark.parametrize("nu", [(2, 2, 8), (0, 1, 2), (1, 0, 4)], ids=lambda v: "nu%d%d%d" % v)
 @pytest.mark.parametrize("cycles", [1, 2])
 def test_precondition_paths(libhh, prec, nu, cycles):

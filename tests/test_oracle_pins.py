@@ -487,3 +487,11 @@ def test_apply_elementwise_equals_assembled(dim, n, bc):
     for coeff in (O.coeff_AL(7.0, 2.0), O.coeff_B(7.0, 0.0), (1.0, 0.0, 0.0), (0.0, 0.0, 1.0)):
         ref = O.combine(O.assemble(g), coeff) @ (x * g.free())
         assert np.abs(O.apply_elementwise(g, coeff, x) - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dim,n,bc", [(2, 5, (S, D, S, S)), (3, 3, (S, S, D, S, S, S))])
+def test_diag_elementwise_equals_assembled(dim, n, bc):
+    g = O.Grid(dim, n, bc)
+    for coeff in (O.coeff_AL(7.0, 2.0), (1.0, 0.0, 0.0), (0.0, 1.0, 0.5)):
+        ref = O.combine(O.assemble(g), coeff).diagonal()
+        assert np.abs(O.diag_elementwise(g, coeff) - ref).max() <= 1e-13 * np.abs(ref).max()
