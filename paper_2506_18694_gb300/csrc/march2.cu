@@ -305,17 +305,28 @@ template void interior_weights<double>(MArgs<double>&);
 template <typename T, int MODE, int ROWS>
 static cudaError_t run2(const MArgs<T>& a, int strips, int chunks, cudaStream_t s) {
     const long long tiles = (long long)strips * chunks;
-    // resident tiles: 152 SMs x 4 blocks x 4 warps; persistent once there are several per warp
-    const long long resident = 152LL * 4 * 4;
-    if (MODE != M_PROLONG_JACOBI && tiles >= 4 * resident && tiles < (1LL << 31)) {
-        const unsigned blocks = (unsigned)(resident / 4);
-        return klaunch(k_march2p<T, MODE, ROWS>, dim3(blocks), dim3(128), 0, s, 1, a, strips, (int)tiles);
+    // persistent once there are several tiles per resident warp: exactly the resident blocks
+    static int per_sm = 0;
+    if (!per_sm) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march2p<T, MODE, ROWS>, 128, 0) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+    }
+    const long long resident_blocks = 152LL * per_sm;
+    // (residual-restriction and prolongation tiles carry more rows; they run one tile per warp)
+    if (MODE != M_PROLONG_JACOBI && MODE != M_RESID_RESTRICT && tiles >= 16 * resident_blocks &&
+        tiles < (1LL << 31)) {
+        return klaunch(k_march2p<T, MODE, ROWS>, dim3((unsigned)resident_blocks), dim3(128), 0, s, 1, a, strips,
+                       (int)tiles);
     }
     dim3 grd((unsigned)strips, (unsigned)((chunks + 3) / 4), 1);
     return klaunch(k_march2<T, MODE, ROWS>, grd, dim3(128), 0, s, 1, a, chunks);
 }
 
-// Rows per warp tile: the largest that still leaves about 24 warps per SM (loads in flight).
+// Rows per warp tile: the largest that still leaves about 24 warps per SM (loads in flight),
+// 8-row persistent tiles on large grids.
 template <typename T, int MODE>
 static cudaError_t go2(MArgs<T> a, cudaStream_t s) {
     a.h = T(a.g.h);
@@ -333,6 +344,9 @@ static cudaError_t go2(MArgs<T> a, cudaStream_t s) {
         const int strips = (a.g.nn + 29) / 30;
         int rows = 2;
         if ((long long)strips * ((a.g.nn + 3) / 4) >= want) rows = 4;
+        // large grids run persistent 8-row tiles (measured best on 4097^2)
+        if (sizeof(T) == 4 && MODE != M_PROLONG_JACOBI && (long long)strips * ((a.g.nn + 7) / 8) >= 16 * want)
+            rows = 8;
         if (a.tile_rows == 2 || a.tile_rows == 4 || (a.tile_rows == 8 && sizeof(T) == 4)) rows = a.tile_rows;
         if constexpr (sizeof(T) == 4) {
             if (rows == 8) return run2<T, MODE, 8>(a, strips, (a.g.nn + 7) / 8, s);
