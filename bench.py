@@ -317,15 +317,26 @@ def profiled_traffic(profile, source):
 
 
 def time_kernel(torch, fn, reps, flush=None):
-    """Average device time of fn() launches on the current stream (CUDA events)."""
+    """Average device time of one fn() launch on the current stream (CUDA events).
+
+    With flush: each launch timed alone after an L2 flush.  Without: reps launches back to
+    back between one pair of events (inputs larger than L2 make every launch read HBM).
+    """
     s = torch.cuda.current_stream()
     for _ in range(3):
         fn()
     torch.cuda.synchronize()
+    if flush is None:
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for _ in range(reps):
+            fn()
+        z.record(s)
+        z.synchronize()
+        return a.elapsed_time(z) / reps / 1e3
     tot = 0.0
     for _ in range(reps):
-        if flush is not None:
-            flush.zero_()
+        flush.zero_()
         a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(s)
         fn()
