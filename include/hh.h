@@ -21,17 +21,24 @@
  * full-weighting restriction R = P^T, bi/trilinear prolongation P) in complex FP32
  * or complex FP64.
  *
- * Data layout (every vector argument): (n_l + 1)^dim complex nodal values of level l
- * (level 0 is the finest, n_l = n / 2^l), lexicographic with x fastest, real and
- * imaginary parts interleaved: double2 for HH_C128, float2 for HH_C64.  Device
- * pointers must be 16-byte (c128) or 8-byte (c64) aligned.  Entries at Dirichlet
- * nodes of inputs are ignored; outputs hold exact zeros there.
+ * Batches: one hh_problem holds nb >= 1 independent problems on the same grid, each
+ * with its own k, delta and delta_hat (hh_create_batch; hh_create_problem is nb = 1).
+ * Every call works on all nb problems at once, in the same kernel launches; a problem
+ * whose HSS loop or outer iteration has ended is skipped on the device, so each
+ * problem's result is the one a batch of one would give, bit for bit.
+ *
+ * Data layout (every vector argument): nb consecutive blocks, block b holding problem
+ * b's (n_l + 1)^dim complex nodal values of level l (level 0 is the finest,
+ * n_l = n / 2^l), lexicographic with x fastest, real and imaginary parts interleaved:
+ * double2 for HH_C128, float2 for HH_C64.  Device pointers must be 16-byte (c128) or
+ * 8-byte (c64) aligned.  Entries at Dirichlet nodes of inputs are ignored; outputs hold
+ * exact zeros there.
  *
  * Ownership: the caller owns every vector it passes; the library owns everything it
  * allocates for a problem (grid hierarchy, Krylov basis, CUDA graphs, streams) and
  * frees it in hh_destroy.  A problem is not thread-safe; distinct problems are
  * independent.  All calls are made on the device that was current at
- * hh_create_problem.
+ * hh_create_problem / hh_create_batch.
  *
  * Errors: every call returns an hh_status; no exception crosses the ABI and no
  * device code traps.  hh_last_error() returns a message for the last failing call
@@ -122,8 +129,12 @@ typedef struct hh_problem hh_problem;
  * coarse_cluster_nodes 100000. */
 HH_API void hh_options_default(hh_options* opts);
 
-/* Device bytes a problem with this grid and these options allocates (0 if invalid). */
+/* Device bytes a problem with this grid and these options allocates for its solves
+ * (0 if invalid); building blocks called in the other precision add a second hierarchy. */
 HH_API size_t hh_footprint_bytes(const hh_grid* grid, const hh_options* opts);
+
+/* As hh_footprint_bytes for a batch of nb problems (0 if invalid or nb < 1). */
+HH_API size_t hh_footprint_batch_bytes(const hh_grid* grid, const hh_options* opts, int nb);
 
 /*
  * Build a problem: validate, compute the operator coefficients of every level and
@@ -140,14 +151,30 @@ HH_API hh_status hh_create_problem(const hh_grid* grid, double k, double delta, 
                             const int* bc, const hh_options* opts, void* cuda_stream,
                             hh_problem** out);
 
+/*
+ * Build a batch of nb problems on one grid with the same boundary tags and options:
+ * k[b], delta[b], delta_hat[b] (host arrays of nb values, each as in hh_create_problem)
+ * define problem b; its HSS length is ceil(k[b]^theta).  1 <= nb <= 65535, and in 3D
+ * (n + 1) nb <= 65535 (problems share the launch grid's z extent with the planes).
+ */
+HH_API hh_status hh_create_batch(const hh_grid* grid, int nb, const double* k, const double* delta,
+                                 const double* delta_hat, const int* bc, const hh_options* opts,
+                                 void* cuda_stream, hh_problem** out);
+
+/* Problems in the batch (0 for NULL). */
+HH_API int hh_batch_size(const hh_problem* p);
+
 HH_API void hh_destroy(hh_problem* p);
 
 /*
  * Solve B_delta u = rhs to ||rhs - B_delta u||_2 <= tol ||rhs||_2 (true residual,
- * recomputed in FP64 at the end of every restart cycle).  rhs (load vector), u and the
- * optional initial guess x0 are device complex128 vectors of level 0.  Blocking: returns
- * when u is written.  On HH_NOT_CONVERGED u holds the last iterate and info is filled;
- * on errors u is unspecified and info->rel_residual is NaN.  info may be NULL.
+ * recomputed in FP64 at the end of every restart cycle) for every problem of the batch.
+ * rhs (load vectors), u and the optional initial guess x0 are device complex128 vectors
+ * of level 0 (nb blocks).  Blocking: returns when u is written.  info, if not NULL,
+ * points to nb records (kernel_launches is counted for the whole call in info[0]).
+ * Returns HH_OK when every problem converged, HH_NOT_CONVERGED when one reached
+ * max_outer (u holds the last iterates and info is filled); on errors u is unspecified
+ * and every rel_residual is NaN.
  */
 HH_API hh_status hh_solve(hh_problem* p, const void* rhs, double tol, void* u, const void* x0,
                    hh_info* info);
@@ -190,7 +217,8 @@ HH_API hh_status hh_precondition(hh_problem* p, const void* r, void* z);
 /* b = M f (load vector of a nodal f, Sec. 2), complex128 on level 0. */
 HH_API hh_status hh_load_vector(hh_problem* p, const void* f, void* b);
 
-/* out[0] + i out[1] = x^H y over level-0 complex128 vectors (deterministic order).  Blocking. */
+/* out[2b] + i out[2b+1] = x_b^H y_b over the level-0 complex128 vectors of problem b, for
+ * every problem of the batch (deterministic order; out holds 2 nb doubles).  Blocking. */
 HH_API hh_status hh_dot(hh_problem* p, const void* x, const void* y, double* out);
 
 /*

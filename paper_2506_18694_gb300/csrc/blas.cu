@@ -31,58 +31,66 @@ __device__ __forceinline__ double2 block_sum(double2 v) {
     return v;  // valid in thread 0
 }
 
-// partials[i * gridDim.x + blockIdx.x] = sum over this block's slice of conj(V_i) w.
-// grid = (kRedBlocks, nvec); block slices are fixed so the sum order never changes.
-__global__ void __launch_bounds__(kRedThreads) k_multidot_partial(const double2* __restrict__ V,
-                                                                  long long ld,
-                                                                  const double2* __restrict__ w,
-                                                                  long long N,
-                                                                  double2* __restrict__ partials) {
+// partials[(b * nvec + i) * gridDim.x + blockIdx.x] = sum over this block's slice of conj(V_i) w
+// for problem b = blockIdx.z.  grid = (kRedBlocks, nvec, problems); block slices are fixed so
+// the sum order never changes.
+__global__ void __launch_bounds__(kRedThreads) k_multidot_partial(const double2* __restrict__ V, long long ld,
+                                                                  const double2* __restrict__ w, long long N,
+                                                                  double2* __restrict__ partials, KBatch kb) {
     pdl_entry();
-    const int vi = blockIdx.y;
-    const double2* __restrict__ v = V + (long long)vi * ld;
+    const int vi = blockIdx.y, b = blockIdx.z;
+    if (kb.active && !kb.active[b]) return;
+    const double2* __restrict__ v = V + (long long)b * kb.bs_v + (long long)vi * ld;
+    w += (long long)b * kb.bs_w;
     double2 acc = make_double2(0.0, 0.0);
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += stride) {
-        const double2 a = v[p], b = w[p];
-        acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-        acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+        const double2 a = v[p], c = w[p];
+        acc.x = fma(a.x, c.x, fma(a.y, c.y, acc.x));
+        acc.y = fma(a.x, c.y, fma(-a.y, c.x, acc.y));
     }
     acc = block_sum(acc);
-    if (threadIdx.x == 0) partials[(long long)vi * gridDim.x + blockIdx.x] = acc;
+    if (threadIdx.x == 0) partials[((long long)b * gridDim.y + vi) * gridDim.x + blockIdx.x] = acc;
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_multidot_final(const double2* __restrict__ partials,
-                                                                int nblk, double2* __restrict__ out) {
+// out[b * bs_out + i] = sum of the partials of (b, i); grid = (nvec, problems)
+__global__ void __launch_bounds__(kRedThreads) k_multidot_final(const double2* __restrict__ partials, int nblk,
+                                                                double2* __restrict__ out, KBatch kb) {
     pdl_entry();
-    const int vi = blockIdx.x;
+    const int vi = blockIdx.x, b = blockIdx.y;
+    if (kb.active && !kb.active[b]) return;
+    const double2* pp = partials + ((long long)b * gridDim.x + vi) * nblk;
     double2 acc = make_double2(0.0, 0.0);
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc = cadd(acc, partials[(long long)vi * nblk + b]);
+    for (int t = threadIdx.x; t < nblk; t += blockDim.x) acc = cadd(acc, pp[t]);
     acc = block_sum(acc);
-    if (threadIdx.x == 0) out[vi] = acc;
+    if (threadIdx.x == 0) out[(long long)b * kb.bs_out + vi] = acc;
 }
 
-cudaError_t launch_multidot(const double2* V, long long ld, int nvec, const double2* w, long long N,
-                            double2* partials, double2* out, cudaStream_t s) {
+cudaError_t launch_multidot(const double2* V, long long ld, int nvec, const double2* w, long long N, double2* partials,
+                            double2* out, const KBatch& kb, cudaStream_t s) {
     if (nvec <= 0) return cudaSuccess;
-    dim3 g1(kRedBlocks, nvec);
-    HH_KRET(klaunch(k_multidot_partial, dim3(g1), dim3(kRedThreads), 0, s, 1, V, ld, w, N, partials));
-    HH_KRET(klaunch(k_multidot_final, dim3(nvec), dim3(kRedThreads), 0, s, 1, partials, kRedBlocks, out));
+    HH_KRET(klaunch(k_multidot_partial, dim3(kRedBlocks, nvec, kb.nb), dim3(kRedThreads), 0, s, 1, V, ld, w, N,
+                    partials, kb));
+    HH_KRET(klaunch(k_multidot_final, dim3(nvec, kb.nb), dim3(kRedThreads), 0, s, 1, (const double2*)partials,
+                    kRedBlocks, out, kb));
     return cudaSuccess;
 }
 
-// w += sign * sum_i coef[i] V_i   (coefficients read from device memory)
+// w_b += sign * sum_i coef[b * bs_out + i] V_{b,i}   (coefficients read from device memory)
 __global__ void __launch_bounds__(256) k_multi_axpy(double2* __restrict__ w, const double2* __restrict__ V,
-                                                    long long ld, int nvec,
-                                                    const double2* __restrict__ coef, double sign,
-                                                    long long N) {
+                                                    long long ld, int nvec, const double2* __restrict__ coef,
+                                                    double sign, long long N, KBatch kb) {
     pdl_entry();
+    const int b = blockIdx.y;
+    if (kb.active && !kb.active[b]) return;
     __shared__ double2 c[64];
     for (int t = threadIdx.x; t < nvec && t < 64; t += blockDim.x) {
-        double2 v = coef[t];
+        double2 v = coef[(long long)b * kb.bs_out + t];
         c[t] = make_double2(sign * v.x, sign * v.y);
     }
     __syncthreads();
+    w += (long long)b * kb.bs_w;
+    V += (long long)b * kb.bs_v;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += stride) {
         double2 acc = w[p];
@@ -103,33 +111,22 @@ static inline unsigned ew_blocks(long long N) {
     return (unsigned)b;
 }
 
-cudaError_t launch_multi_axpy(double2* w, const double2* V, long long ld, int nvec,
-                              const double2* coef, double sign, long long N, cudaStream_t s) {
+cudaError_t launch_multi_axpy(double2* w, const double2* V, long long ld, int nvec, const double2* coef, double sign,
+                              long long N, const KBatch& kb, cudaStream_t s) {
     if (nvec <= 0) return cudaSuccess;
     if (nvec > 64) return cudaErrorInvalidValue;
-    HH_KRET(klaunch(k_multi_axpy, dim3(ew_blocks(N)), dim3(256), 0, s, 1, w, V, ld, nvec, coef, sign, N));
-    return cudaSuccess;
+    return klaunch(k_multi_axpy, dim3(ew_blocks(N), kb.nb), dim3(256), 0, s, 1, w, V, ld, nvec, coef, sign, N, kb);
 }
 
-__global__ void k_scale_by_rnorm(double2* __restrict__ x, const double2* __restrict__ nrm2, long long N) {
+// x_b *= 1 / sqrt(nrm2[b * bs_out].x) (skipped when zero); x_b at offset b * bs_w
+__global__ void k_scale_by_rnorm(double2* __restrict__ x, const double2* __restrict__ nrm2, long long N, KBatch kb) {
     pdl_entry();
-    const double n2 = nrm2->x;
+    const int b = blockIdx.y;
+    if (kb.active && !kb.active[b]) return;
+    const double n2 = nrm2[(long long)b * kb.bs_out].x;
     if (!(n2 > 0.0)) return;
-    const double s = 1.0 / sqrt(n2);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += stride) {
-        double2 v = x[p];
-        x[p] = make_double2(v.x * s, v.y * s);
-    }
-}
-
-cudaError_t launch_scale_by_rnorm(double2* x, const double2* nrm2, long long N, cudaStream_t s) {
-    HH_KRET(klaunch(k_scale_by_rnorm, dim3(ew_blocks(N)), dim3(256), 0, s, 1, x, nrm2, N));
-    return cudaSuccess;
-}
-
-__global__ void k_scale(double2* __restrict__ x, double sc, long long N) {
-    pdl_entry();
+    const double sc = 1.0 / sqrt(n2);
+    x += (long long)b * kb.bs_w;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += stride) {
         double2 v = x[p];
@@ -137,9 +134,8 @@ __global__ void k_scale(double2* __restrict__ x, double sc, long long N) {
     }
 }
 
-cudaError_t launch_scale(double2* x, double sc, long long N, cudaStream_t st) {
-    HH_KRET(klaunch(k_scale, dim3(ew_blocks(N)), dim3(256), 0, st, 1, x, sc, N));
-    return cudaSuccess;
+cudaError_t launch_scale_by_rnorm(double2* x, const double2* nrm2, long long N, const KBatch& kb, cudaStream_t s) {
+    return klaunch(k_scale_by_rnorm, dim3(ew_blocks(N), kb.nb), dim3(256), 0, s, 1, x, nrm2, N, kb);
 }
 
 }  // namespace hh

@@ -34,22 +34,22 @@ static SlabPlan slab_plan(const GridDesc& g, int cs) {
     return sp;
 }
 
-// Interior weights of the coarsest operator (all neighbours are interior nodes): 2D
-// centre, edge, diagonal; 3D centre, face, edge, corner neighbours.  Filled on the host.
-template <typename T> struct CoarseW {
-    Cx<T> w[4];
-    Cx<T> dinv;  // omega / interior diagonal
-};
-
+// One cluster per problem of the batch: problem = blockIdx.x / cluster size.  Coefficients
+// from the table entry of A_L on this level (interior weights and omega D^{-1} included).
 template <typename T>
-__global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem(GridDesc g, OpCoef<T> op, CoarseW<T> cw,
-                                                                 const vec2<T>* __restrict__ b,
-                                                                 vec2<T>* __restrict__ xout, int nsweeps, T omega,
-                                                                 int per) {
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem(MArgs<T> a, int nsweeps, int per) {
     pdl_entry();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
+    const int prob = blockIdx.x / (int)cl.num_blocks();
+    if (problem_skipped(a, prob)) return;  // uniform over the cluster: no barrier is left waiting
+    const GridDesc& g = a.g;
+    const PCoef<T> pcf = coef_of(a, prob);
+    const OpCoef<T> op = pcf.op;
+    const vec2<T>* __restrict__ b = a.z + (long long)prob * a.bs;
+    vec2<T>* __restrict__ xout = a.y + (long long)prob * a.bs;
+    const T omega = a.omega;
     const int nn = g.nn, n = g.n;
     const bool d3 = g.dim == 3;
     const long long S = d3 ? (long long)nn * nn : nn;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem(GridDesc g, OpC
         cls[k] = fast ? 1 : 2;
         bq[k] = ld<T>(b, (long long)r0 * S + q);
         if (fast) {
-            dw[k] = cw.dinv;
+            dw[k] = pcf.wdinv;
         } else {
             const NodeResult<T> r = d3 ? node3<T, false>(xs[0], nn, ii[k], jj[k], ll[k], rx, ry, rz, op, off)
                                        : node2<T, false>(xs[0], nn, ii[k], jj[k], rx, ry, op, off);
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem(GridDesc g, OpC
                                             (ld<T>(xc, lq - nn) + ld<T>(xc, lq + nn));
                             const Cx<T> dg = (ld<T>(xc, lq - nn - 1) + ld<T>(xc, lq - nn + 1)) +
                                              (ld<T>(xc, lq + nn - 1) + ld<T>(xc, lq + nn + 1));
-                            ax = fma_c(cw.w[2], dg, fma_c(cw.w[1], e, cmul(cw.w[0], ld<T>(xc, lq))));
+                            ax = fma_c(pcf.iw[2], dg, fma_c(pcf.iw[1], e, cmul(pcf.iw[0], ld<T>(xc, lq))));
                         } else {
                             // neighbours grouped by how many coordinates differ: 6 faces, 12 edges, 8 corners
                             Cx<T> fa = cx<T>(0, 0), ed = cx<T>(0, 0), co = cx<T>(0, 0);
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem(GridDesc g, OpC
                                         else if (m == 2) ed = ed + v;
                                         else co = co + v;
                                     }
-                            ax = fma_c(cw.w[3], co, fma_c(cw.w[2], ed, fma_c(cw.w[1], fa, cmul(cw.w[0], ld<T>(xc, lq)))));
+                            ax = fma_c(pcf.iw[3], co, fma_c(pcf.iw[2], ed, fma_c(pcf.iw[1], fa, cmul(pcf.iw[0], ld<T>(xc, lq)))));
                         }
                     } else {
                         const Row1<T> rx = row1<T>(ii[k], n, g.dir[0], g.dir[1], h, ih);
@@ -199,20 +199,6 @@ bool coarse_fits(const GridDesc& g) {
 }
 
 template <typename T>
-static CoarseW<T> coarse_weights(const GridDesc& g, const OpCoef<T>& op, T omega) {
-    MArgs<T> a{};
-    a.g = g;
-    a.op = op;
-    a.opd = op;
-    a.omega = omega;
-    interior_weights(a);
-    CoarseW<T> cw;
-    for (int c = 0; c < 4; ++c) cw.w[c] = a.iw[c];
-    cw.dinv = a.wdinv;
-    return cw;
-}
-
-template <typename T>
 cudaError_t prepare_coarse() {
     cudaError_t e = cudaFuncSetAttribute(k_coarse_dsmem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kCoarseSmemMax);
@@ -222,23 +208,19 @@ cudaError_t prepare_coarse() {
 }
 
 template <typename T>
-cudaError_t launch_coarse_solve(const GridDesc& g, const OpCoef<T>& op, const vec2<T>* b, vec2<T>* x, int nsweeps,
-                                T omega, cudaStream_t s) {
+cudaError_t launch_coarse_solve(const MArgs<T>& a, int nsweeps, cudaStream_t s) {
     const int cs = coarse_cluster_size();
-    const SlabPlan sp = slab_plan<T>(g, cs);
+    const SlabPlan sp = slab_plan<T>(a.g, cs);
     if (sp.smem > kCoarseSmemMax || nsweeps < 1) return cudaErrorInvalidValue;
     if ((long long)sp.per * sp.S > (long long)kCoarseNodesPerThread * kCoarseThreads) return cudaErrorInvalidValue;
-    return klaunch(k_coarse_dsmem<T>, dim3(cs), dim3(kCoarseThreads), sp.smem, s, cs, g, op,
-                   coarse_weights<T>(g, op, omega), b, x, nsweeps, omega, sp.per);
+    return klaunch(k_coarse_dsmem<T>, dim3(cs * a.nb), dim3(kCoarseThreads), sp.smem, s, cs, a, nsweeps, sp.per);
 }
 
 template bool coarse_fits<float>(const GridDesc&);
 template bool coarse_fits<double>(const GridDesc&);
 template cudaError_t prepare_coarse<float>();
 template cudaError_t prepare_coarse<double>();
-template cudaError_t launch_coarse_solve<float>(const GridDesc&, const OpCoef<float>&, const float2*, float2*, int,
-                                                float, cudaStream_t);
-template cudaError_t launch_coarse_solve<double>(const GridDesc&, const OpCoef<double>&, const double2*, double2*,
-                                                 int, double, cudaStream_t);
+template cudaError_t launch_coarse_solve<float>(const MArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_coarse_solve<double>(const MArgs<double>&, int, cudaStream_t);
 
 }  // namespace hh

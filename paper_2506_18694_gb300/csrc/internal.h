@@ -51,35 +51,39 @@ inline cudaError_t klaunch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-// rc = P^T rf (rf on the fine grid of gc)
+// Batch selection for the transfer and elementwise kernels: nb problems, problem b at offset
+// b * bs in its level vector and b * bsc in its coarse vector; skipped like MArgs.
+struct Batch {
+    int nb;
+    long long bs, bsc;
+    int hss_it;
+    const int* nhss;
+    const int* active;
+};
+
+// rc = P^T rf (rf on the fine grid of gc), every problem of the batch
 template <typename T>
-cudaError_t launch_restrict(const GridDesc& gc, const vec2<T>* rf, vec2<T>* rc, cudaStream_t s);
+cudaError_t launch_restrict(const GridDesc& gc, const vec2<T>* rf, vec2<T>* rc, const Batch& bt, cudaStream_t s);
 
 // x += P ec (ec on the coarse grid of gf)
 template <typename T>
-cudaError_t launch_prolong(const GridDesc& gf, const vec2<T>* ec, vec2<T>* x, cudaStream_t s);
+cudaError_t launch_prolong(const GridDesc& gf, const vec2<T>* ec, vec2<T>* x, const Batch& bt, cudaStream_t s);
 
-// x += e elementwise
+// x += e, x = e (first N entries of each problem's vector)
 template <typename T>
-cudaError_t launch_add(vec2<T>* x, const vec2<T>* e, long long N, cudaStream_t s);
+cudaError_t launch_add(vec2<T>* x, const vec2<T>* e, long long N, const Batch& bt, cudaStream_t s);
+template <typename T>
+cudaError_t launch_copy(vec2<T>* x, const vec2<T>* e, long long N, const Batch& bt, cudaStream_t s);
+template <typename T>
+cudaError_t launch_zero(vec2<T>* x, long long N, const Batch& bt, cudaStream_t s);
 
-// ---- coarsest level inside one thread-block cluster, in distributed shared memory (coarse.cu) ----
-constexpr int kCoarseThreads = 512;
-constexpr int kCoarseNodesPerThread = 2;
-constexpr size_t kCoarseSmemMax = 200 * 1024;
-
-// CTAs per cluster (16 or 8 when the device can co-schedule them, else 1)
-int coarse_cluster_size();
-// whether a grid's slabs fit the shared memory of the cluster's CTAs
+cudaError_t launch_cast_d2f(const double2* a, float2* b, long long N, cudaStream_t s);
+// dst (nb consecutive complex128 vectors of N) = *src[b] (device array of nb pointers)
 template <typename T>
-bool coarse_fits(const GridDesc& g);
-// one-time set-up (shared-memory limit, cluster query); call before any stream capture
-template <typename T>
-cudaError_t prepare_coarse();
-// nsweeps scaled-Jacobi sweeps on A x = b from x = 0
-template <typename T>
-cudaError_t launch_coarse_solve(const GridDesc& g, const OpCoef<T>& op, const vec2<T>* b, vec2<T>* x, int nsweeps,
-                                T omega, cudaStream_t s);
+cudaError_t launch_gather_c128(const vec2<T>* const* src, double2* dst, long long N, int nb, const int* active,
+                               cudaStream_t s);
+// dst = src with exact zeros at the Dirichlet nodes of g (nb consecutive vectors)
+cudaError_t launch_mask_copy(const GridDesc& g, const double2* src, double2* dst, int nb, cudaStream_t s);
 
 // ---- fused 2D marching kernels (march2.cu) ----
 enum MarchMode {
@@ -93,57 +97,132 @@ enum MarchMode {
     M_RESID_RESTRICT = 6  // y (coarse) = P^T (z - op x)
 };
 
+// Coefficients of one operator on one level for one problem of a batch (a device table
+// indexed by problem): the stencil operator, the operator whose diagonal scales the Jacobi
+// update (A_L), the interior weights of op by neighbour class (how many coordinates differ
+// from the centre: 0 centre, 1 edge/face, 2 diagonal/edge, 3 corner in 3D), omega / interior
+// diag(opd), and two per-problem scalars (the HSS weights (k-1)/(k+1), 2k/(k+1)).
+template <typename T> struct PCoef {
+    OpCoef<T> op;
+    OpCoef<T> opd;
+    Cx<T> iw[4];
+    Cx<T> wdinv;
+    Cx<T> alpha, beta;
+};
+
+// Host: fill the interior weights and wdinv of c for grid g and damping omega.
+template <typename T>
+void interior_weights(PCoef<T>& c, const GridDesc& g, double omega);
+
+// Arguments of the stencil kernels.  Problem b of a batch of nb reads x, z, y, y2 at
+// offset b * bs, ec (and writes the coarse output of RESID_RESTRICT) at offset b * bsc,
+// and its coefficients at pc[b].
 template <typename T> struct MArgs {
     GridDesc g;          // grid of the level the stencil runs on
-    OpCoef<T> op;        // stencil operator
-    OpCoef<T> opd;       // operator whose diagonal scales the HSS-first Jacobi step (A_L)
+    const PCoef<T>* pc;  // device coefficient table of this operator and level (nullptr: c0)
+    PCoef<T> c0;         // the coefficients of a batch of one, passed by value
     const vec2<T>* x;    // stencil input (ignored for M_JACOBI2_ZERO; nullptr = 0 when xzero)
     const vec2<T>* z;    // right side / second vector
     const vec2<T>* ec;   // coarse correction (M_PROLONG_JACOBI)
     vec2<T>* y;          // output
     vec2<T>* y2;         // second output (M_HSS_FIRST)
-    Cx<T> alpha, beta;
+    long long bs, bsc;
+    int nb;
+    Cx<T> alpha, beta;   // AXPBY / HSS_FIRST scalars when use_pc_ab == 0
+    int use_pc_ab;       // 1: alpha, beta of problem b from pc[b]
     T omega;
     int xzero;           // 1: x is identically zero
     int tile_rows;       // 0: automatic; else 2, 4 or 8 rows (2D) / planes (3D) per tile
+    int hss_it;          // >= 0: problem b is skipped when hss_it >= nhss[b]
+    const int* nhss;     // device: HSS iterations of each problem
+    const int* active;   // device: 0 = problem skipped (nullptr: all active)
     // filled by the launcher
     T h, ih;
     int rows;
-    // interior stencil weights of op by neighbour class (how many coordinates differ from
-    // the centre: 0 centre, 1 edge/face, 2 diagonal/edge, 3 corner in 3D)
-    Cx<T> iw[4];
-    Cx<T> wdinv;         // omega / (interior diagonal of opd)
 };
 
-// ---- fused 3D tile kernels (march3.cu): modes as above except M_RESID_RESTRICT ----
+// Vector pointers of problem b.
+template <typename T> struct VPtrs {
+    const vec2<T>* x;
+    const vec2<T>* z;
+    const vec2<T>* ec;
+    vec2<T>* y;
+    vec2<T>* y2;
+};
+
 template <typename T>
-cudaError_t launch_march3(int mode, const MArgs<T>& a, cudaStream_t s);
-// interior weights (iw, wdinv) of a.op / a.opd on grid a.g (filled by the launchers)
+__device__ __forceinline__ VPtrs<T> problem_ptrs(const MArgs<T>& a, int b, bool coarse_out) {
+    const long long o = (long long)b * a.bs, oc = (long long)b * a.bsc;
+    VPtrs<T> v;
+    v.x = a.x ? a.x + o : nullptr;
+    v.z = a.z ? a.z + o : nullptr;
+    v.ec = a.ec ? a.ec + oc : nullptr;
+    v.y = a.y ? a.y + (coarse_out ? oc : o) : nullptr;
+    v.y2 = a.y2 ? a.y2 + o : nullptr;
+    return v;
+}
+
+// Coefficients of problem b.
 template <typename T>
-void interior_weights(MArgs<T>& a);
+__device__ __forceinline__ PCoef<T> coef_of(const MArgs<T>& a, int b) {
+    return a.pc ? a.pc[b] : a.c0;
+}
+
+// Whether problem b takes part in a launch.
+template <typename T>
+__device__ __forceinline__ bool problem_skipped(const MArgs<T>& a, int b) {
+    if (a.active && !a.active[b]) return true;
+    return a.hss_it >= 0 && a.hss_it >= a.nhss[b];
+}
 
 template <typename T>
 cudaError_t launch_march2(int mode, const MArgs<T>& a, cudaStream_t s);
 
-cudaError_t launch_cast_d2f(const double2* a, float2* b, long long N, cudaStream_t s);
-cudaError_t launch_cast_f2d(const float2* a, double2* b, long long N, cudaStream_t s);
-// dst = src with exact zeros at the Dirichlet nodes of g
-cudaError_t launch_mask_copy(const GridDesc& g, const double2* src, double2* dst, cudaStream_t s);
+// ---- fused 3D tile kernels (march3.cu): modes as above except M_RESID_RESTRICT ----
+template <typename T>
+cudaError_t launch_march3(int mode, const MArgs<T>& a, cudaStream_t s);
+
+// ---- coarsest level inside one thread-block cluster per problem, in distributed shared
+//      memory (coarse.cu) ----
+constexpr int kCoarseThreads = 512;
+constexpr int kCoarseNodesPerThread = 2;
+constexpr size_t kCoarseSmemMax = 200 * 1024;
+
+// CTAs per cluster (16 or 8 when the device can co-schedule them, else 1)
+int coarse_cluster_size();
+// whether a grid's slabs fit the shared memory of the cluster's CTAs
+template <typename T>
+bool coarse_fits(const GridDesc& g);
+// one-time set-up (shared-memory limit, cluster query); call before any stream capture
+template <typename T>
+cudaError_t prepare_coarse();
+// a.nb problems: nsweeps scaled-Jacobi sweeps on op x = z from x = 0 into y (coefficients
+// from a.pc), one cluster per problem
+template <typename T>
+cudaError_t launch_coarse_solve(const MArgs<T>& a, int nsweeps, cudaStream_t s);
+
 
 // ---- FP64 Krylov kernels (blas.cu) ----
 // Fixed reduction grid: results do not depend on timing or launch history.
 constexpr int kRedBlocks = 304;
 constexpr int kRedThreads = 256;
 
-// out[i] = sum_p conj(V_i[p]) w[p] for i < nvec (V_i = V + i*ld); partials holds nvec*kRedBlocks
-cudaError_t launch_multidot(const double2* V, long long ld, int nvec, const double2* w,
-                            long long N, double2* partials, double2* out, cudaStream_t s);
-// w[p] -= sum_i coef[i] V_i[p]    (sign = -1)   or   w[p] += sum_i coef[i] V_i[p] (sign = +1)
-cudaError_t launch_multi_axpy(double2* w, const double2* V, long long ld, int nvec,
-                              const double2* coef, double sign, long long N, cudaStream_t s);
-// x *= 1 / sqrt(nrm2->x) (nrm2 on the device, skipped when zero)
-cudaError_t launch_scale_by_rnorm(double2* x, const double2* nrm2, long long N, cudaStream_t s);
-// x *= s
-cudaError_t launch_scale(double2* x, double s, long long N, cudaStream_t st);
+// Batch of nb problems for the Krylov kernels: problem b's V (or x) at offset b * bs_v, its w
+// at b * bs_w, its results / coefficients / norms at b * bs_out; active[b] == 0 skips it.
+struct KBatch {
+    int nb;
+    long long bs_v, bs_w, bs_out;
+    const int* active;
+};
+
+// out[b*bs_out + i] = sum_p conj(V_{b,i}[p]) w_b[p], i < nvec (V_{b,i} = V + b*bs_v + i*ld);
+// partials holds nb * nvec * kRedBlocks
+cudaError_t launch_multidot(const double2* V, long long ld, int nvec, const double2* w, long long N, double2* partials,
+                            double2* out, const KBatch& kb, cudaStream_t s);
+// w_b += sign * sum_i coef[b*bs_out + i] V_{b,i}
+cudaError_t launch_multi_axpy(double2* w, const double2* V, long long ld, int nvec, const double2* coef, double sign,
+                              long long N, const KBatch& kb, cudaStream_t s);
+// x_b *= 1 / sqrt(nrm2[b*bs_out].x) (x_b = x + b*bs_w; skipped when zero)
+cudaError_t launch_scale_by_rnorm(double2* x, const double2* nrm2, long long N, const KBatch& kb, cudaStream_t s);
 
 }  // namespace hh

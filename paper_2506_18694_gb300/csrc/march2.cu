@@ -32,17 +32,17 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 
 // Value of the stencil field at node (i, r) (both clamped into the grid).
 template <typename T, int MODE>
-__device__ __forceinline__ Cx<T> field2(const MArgs<T>& a, int ic, int rc, const Row1<T>& rx, T h, T ih,
-                                        Cx<T>* bval) {
+__device__ __forceinline__ Cx<T> field2(const MArgs<T>& a, const PCoef<T>& c, const VPtrs<T>& v, int ic, int rc,
+                                        const Row1<T>& rx, T h, T ih, Cx<T>* bval) {
     const long long p = (long long)rc * a.g.nn + ic;
     if (MODE == M_JACOBI2_ZERO) {
         // first sweep from x = 0: x1 = omega D^{-1} b (zero at Dirichlet nodes)
-        const Cx<T> b = ld<T>(a.z, p);
+        const Cx<T> b = ld<T>(v.z, p);
         *bval = b;
-        if (ic >= 1 && ic <= a.g.n - 1 && rc >= 1 && rc <= a.g.n - 1) return cmul(a.wdinv, b);
+        if (ic >= 1 && ic <= a.g.n - 1 && rc >= 1 && rc <= a.g.n - 1) return cmul(c.wdinv, b);
         const Row1<T> ry = row1<T>(rc, a.g.n, a.g.dir[2], a.g.dir[3], h, ih);
         if (rx.masked || ry.masked) return cx<T>(0, 0);
-        return a.omega * cmul(cinv(diag2(rx, ry, a.op)), b);
+        return a.omega * cmul(cinv(diag2(rx, ry, c.op)), b);
     } else if (MODE == M_PROLONG_JACOBI) {
         // x + P e_c: bilinear interpolation of the coarse correction (coarse Dirichlet
         // nodes carry no basis function and are skipped)
@@ -64,12 +64,12 @@ __device__ __forceinline__ Cx<T> field2(const MArgs<T>& a, int ic, int rc, const
                 const int I = I0 + ai;
                 if ((I == 0 && a.g.dir[0]) || (I == nc && a.g.dir[1])) continue;
                 const T w = oi ? T(0.5) * wj : wj;
-                e = fma_r(w, ld<T>(a.ec, (long long)J * nnc + I), e);
+                e = fma_r(w, ld<T>(v.ec, (long long)J * nnc + I), e);
             }
         }
-        return ld<T>(a.x, p) + e;
+        return ld<T>(v.x, p) + e;
     } else {
-        return a.xzero ? cx<T>(0, 0) : ld<T>(a.x, p);
+        return a.xzero ? cx<T>(0, 0) : ld<T>(v.x, p);
     }
 }
 
@@ -91,7 +91,8 @@ template <typename T, int MODE, int ROWS> struct Tile2 {
 };
 
 template <typename T, int MODE, int ROWS>
-__device__ __forceinline__ void tile_load(const MArgs<T>& a, int strip, int cy, Tile2<T, MODE, ROWS>& tl) {
+__device__ __forceinline__ void tile_load(const MArgs<T>& a, const PCoef<T>& c, const VPtrs<T>& v, int strip, int cy,
+                                          Tile2<T, MODE, ROWS>& tl) {
     using TL = Tile2<T, MODE, ROWS>;
     const int lane = threadIdx.x & 31;
     const int n = a.g.n;
@@ -103,22 +104,23 @@ __device__ __forceinline__ void tile_load(const MArgs<T>& a, int strip, int cy, 
     for (int t = 0; t < TL::NR; ++t) {
         const int rc = clampi(rfirst + t, 0, n);
         if (MODE == M_JACOBI2_ZERO) {
-            tl.bv[t] = ld<T>(a.z, (long long)rc * a.g.nn + ic);
+            tl.bv[t] = ld<T>(v.z, (long long)rc * a.g.nn + ic);
         } else if (MODE == M_PROLONG_JACOBI) {
             const Row1<T> rx = row1<T>(ic, n, a.g.dir[0], a.g.dir[1], a.h, a.ih);
             Cx<T> dummy;
-            tl.fv[t] = field2<T, MODE>(a, ic, rc, rx, a.h, a.ih, &dummy);
+            tl.fv[t] = field2<T, MODE>(a, c, v, ic, rc, rx, a.h, a.ih, &dummy);
         } else {
-            tl.fv[t] = a.xzero ? cx<T>(0, 0) : ld<T>(a.x, (long long)rc * a.g.nn + ic);
+            tl.fv[t] = a.xzero ? cx<T>(0, 0) : ld<T>(v.x, (long long)rc * a.g.nn + ic);
         }
     }
 #pragma unroll
     for (int t = 0; t < TL::NZ; ++t)
-        tl.zv[t] = TL::NEEDZ ? ld<T>(a.z, (long long)clampi(rfirst + 1 + t, 0, n) * a.g.nn + ic) : cx<T>(0, 0);
+        tl.zv[t] = TL::NEEDZ ? ld<T>(v.z, (long long)clampi(rfirst + 1 + t, 0, n) * a.g.nn + ic) : cx<T>(0, 0);
 }
 
 template <typename T, int MODE, int ROWS>
-__device__ __forceinline__ void tile_compute(const MArgs<T>& a, int strip, int cy, Tile2<T, MODE, ROWS>& tl) {
+__device__ __forceinline__ void tile_compute(const MArgs<T>& a, const PCoef<T>& c, const VPtrs<T>& v, int strip,
+                                             int cy, Tile2<T, MODE, ROWS>& tl) {
     using TL = Tile2<T, MODE, ROWS>;
     constexpr bool RR = TL::RR;
     constexpr int NR = TL::NR;
@@ -140,11 +142,11 @@ __device__ __forceinline__ void tile_compute(const MArgs<T>& a, int strip, int c
         for (int t = 0; t < NR; ++t) {
             const int rc = clampi(rfirst + t, 0, n);
             if (ic >= 1 && ic <= n - 1 && rc >= 1 && rc <= n - 1) {
-                tl.fv[t] = cmul(a.wdinv, tl.bv[t]);
+                tl.fv[t] = cmul(c.wdinv, tl.bv[t]);
             } else {
                 const Row1<T> ry = row1<T>(rc, n, a.g.dir[2], a.g.dir[3], h, ih);
                 tl.fv[t] = (rx.masked || ry.masked) ? cx<T>(0, 0)
-                                                   : a.omega * cmul(cinv(diag2(rx, ry, a.op)), tl.bv[t]);
+                                                   : a.omega * cmul(cinv(diag2(rx, ry, c.op)), tl.bv[t]);
             }
         }
     }
@@ -170,8 +172,8 @@ __device__ __forceinline__ void tile_compute(const MArgs<T>& a, int strip, int c
         if (fast) {
             const Cx<T> edge = (lf[t] + rg[t]) + (fv[t - 1] + fv[t + 1]);
             const Cx<T> diag = (lf[t - 1] + rg[t - 1]) + (lf[t + 1] + rg[t + 1]);
-            ax = fma_c(a.iw[2], diag, fma_c(a.iw[1], edge, cmul(a.iw[0], fv[t])));
-            dinv_w = a.wdinv;
+            ax = fma_c(c.iw[2], diag, fma_c(c.iw[1], edge, cmul(c.iw[0], fv[t])));
+            dinv_w = c.wdinv;
         } else {
             const Row1<T> ry = row1<T>(jc, n, a.g.dir[2], a.g.dir[3], h, ih);
             Cx<T> mx[3], kx[3];
@@ -186,12 +188,12 @@ __device__ __forceinline__ void tile_compute(const MArgs<T>& a, int strip, int c
             Cx<T> F = cx<T>(0, 0);
             if (rx.face) F = fma_r(ry.mr, fv[t + 1], fma_r(ry.mc, fv[t], ry.ml * fv[t - 1]));
             if (ry.face) F = F + mx[1];
-            ax = a.op.cK * Kx;
-            ax = fma_c(a.op.cM, Mx, ax);
-            ax = fma_c(a.op.cG, F, ax);
+            ax = c.op.cK * Kx;
+            ax = fma_c(c.op.cM, Mx, ax);
+            ax = fma_c(c.op.cG, F, ax);
             masked = rx.masked || ry.masked;
             dinv_w = (MODE == M_APPLY || MODE == M_AXPBY || RR) ? cx<T>(0, 0)
-                                                                 : a.omega * cinv(diag2(rx, ry, a.opd));
+                                                                 : a.omega * cinv(diag2(rx, ry, c.opd));
         }
         if (RR) {
             const Cx<T> res = (row_in && col_in && !masked) ? tl.zv[t - 1] - ax : cx<T>(0, 0);
@@ -207,7 +209,7 @@ __device__ __forceinline__ void tile_compute(const MArgs<T>& a, int strip, int c
                     if (lane >= 2 && lane <= 28 && !(lane & 1) && I <= nc && J <= nc) {
                         const bool cm = (I == 0 && a.g.dir[0]) || (I == nc && a.g.dir[1]) ||
                                         (J == 0 && a.g.dir[2]) || (J == nc && a.g.dir[3]);
-                        st<T>(a.y, (long long)J * (nc + 1) + I, cm ? cx<T>(0, 0) : acc);
+                        st<T>(v.y, (long long)J * (nc + 1) + I, cm ? cx<T>(0, 0) : acc);
                     }
                 }
                 acc = T(0.5) * rr;
@@ -216,54 +218,94 @@ __device__ __forceinline__ void tile_compute(const MArgs<T>& a, int strip, int c
         }
         if (!(lane >= 1 && lane <= 30 && col_in && row_in)) continue;
         if (masked) {
-            st<T>(a.y, p, cx<T>(0, 0));
-            if (MODE == M_HSS_FIRST) st<T>(a.y2, p, cx<T>(0, 0));
+            st<T>(v.y, p, cx<T>(0, 0));
+            if (MODE == M_HSS_FIRST) st<T>(v.y2, p, cx<T>(0, 0));
             continue;
         }
+        const Cx<T> alpha = a.use_pc_ab ? c.alpha : a.alpha, beta = a.use_pc_ab ? c.beta : a.beta;
         if (MODE == M_APPLY) {
-            st<T>(a.y, p, ax);
+            st<T>(v.y, p, ax);
         } else if (MODE == M_AXPBY) {
-            st<T>(a.y, p, fma_c(a.alpha, ax, cmul(a.beta, tl.zv[t - 1])));
+            st<T>(v.y, p, fma_c(alpha, ax, cmul(beta, tl.zv[t - 1])));
         } else if (MODE == M_HSS_FIRST) {
-            const Cx<T> rhs = fma_c(a.alpha, ax, cmul(a.beta, tl.zv[t - 1]));
-            st<T>(a.y, p, rhs);
-            st<T>(a.y2, p, cmul(dinv_w, rhs));
+            const Cx<T> rhs = fma_c(alpha, ax, cmul(beta, tl.zv[t - 1]));
+            st<T>(v.y, p, rhs);
+            st<T>(v.y2, p, cmul(dinv_w, rhs));
         } else {
             // Jacobi update of the field: field + omega D^{-1} (b - op field)
             const Cx<T> b = (MODE == M_JACOBI2_ZERO) ? tl.bv[t] : tl.zv[t - 1];
-            st<T>(a.y, p, fma_c(dinv_w, b - ax, fv[t]));
+            st<T>(v.y, p, fma_c(dinv_w, b - ax, fv[t]));
         }
     }
 }
 
-// One tile per warp; grid (strips, ceil(chunks / 4)).
-template <typename T, int MODE, int ROWS>
+// One tile per warp; grid (strips, ceil(chunks / 4), problems).  BATCH = false: a batch of
+// one, coefficients from the kernel parameters and no activity flags.
+template <typename T, int MODE, int ROWS, bool BATCH>
 __global__ void __launch_bounds__(128) k_march2(MArgs<T> a, int chunks) {
     pdl_entry();
+    const int b = BATCH ? (int)blockIdx.z : 0;
     const int cy = blockIdx.y * 4 + (threadIdx.x >> 5);
     if (cy >= chunks) return;
+    if (BATCH && problem_skipped(a, b)) return;
+    const PCoef<T> c = BATCH ? a.pc[b] : a.c0;
+    const VPtrs<T> v = problem_ptrs(a, b, MODE == M_RESID_RESTRICT);
     Tile2<T, MODE, ROWS> tl;
-    tile_load<T, MODE, ROWS>(a, blockIdx.x, cy, tl);
-    tile_compute<T, MODE, ROWS>(a, blockIdx.x, cy, tl);
+    tile_load<T, MODE, ROWS>(a, c, v, blockIdx.x, cy, tl);
+    tile_compute<T, MODE, ROWS>(a, c, v, blockIdx.x, cy, tl);
 }
 
 // Persistent form for grids with many more tiles than resident warps: each warp walks the
-// tiles c, c + W, c + 2W, ... (strip fastest) and issues the loads of its next tile before
-// computing the current one, so that its loads stay in flight while it computes.
-template <typename T, int MODE, int ROWS>
-__global__ void __launch_bounds__(128) k_march2p(MArgs<T> a, int strips, int tiles) {
+// tiles t, t + W, t + 2W, ... (strip fastest; in a batch, the problems' tiles one after
+// another) and issues the loads of its next tile before computing the current one, so that
+// its loads stay in flight while it computes.
+template <typename T, int MODE, int ROWS, bool BATCH>
+__global__ void __launch_bounds__(128) k_march2p(MArgs<T> a, int strips, int per_problem, int tiles) {
     pdl_entry();
     const int W = gridDim.x * 4;
-    int c = blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (c >= tiles) return;
-    Tile2<T, MODE, ROWS> cur;
-    tile_load<T, MODE, ROWS>(a, c % strips, c / strips, cur);
-    for (; c < tiles; c += W) {
-        Tile2<T, MODE, ROWS> nxt;
-        const int cn = c + W;
-        if (cn < tiles) tile_load<T, MODE, ROWS>(a, cn % strips, cn / strips, nxt);
-        tile_compute<T, MODE, ROWS>(a, c % strips, c / strips, cur);
-        cur = nxt;
+    int t = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (t >= tiles) return;
+    if constexpr (!BATCH) {
+        const PCoef<T> c = a.c0;
+        const VPtrs<T> v = problem_ptrs(a, 0, false);
+        Tile2<T, MODE, ROWS> cur;
+        tile_load<T, MODE, ROWS>(a, c, v, t % strips, t / strips, cur);
+        for (; t < tiles; t += W) {
+            Tile2<T, MODE, ROWS> nxt;
+            const int tn = t + W;
+            if (tn < tiles) tile_load<T, MODE, ROWS>(a, c, v, tn % strips, tn / strips, nxt);
+            tile_compute<T, MODE, ROWS>(a, c, v, t % strips, t / strips, cur);
+            cur = nxt;
+        }
+    } else {
+        auto split = [&](int tt, int* b, int* strip, int* cy) {
+            *b = tt / per_problem;
+            const int r = tt - *b * per_problem;
+            *strip = r % strips;
+            *cy = r / strips;
+        };
+        int b, strip, cy;
+        split(t, &b, &strip, &cy);
+        Tile2<T, MODE, ROWS> cur;
+        bool have = !problem_skipped(a, b);
+        if (have) tile_load<T, MODE, ROWS>(a, a.pc[b], problem_ptrs(a, b, false), strip, cy, cur);
+        for (; t < tiles; t += W) {
+            Tile2<T, MODE, ROWS> nxt;
+            const int tn = t + W;
+            int bn = 0, sn = 0, cn = 0;
+            bool next = false;
+            if (tn < tiles) {
+                split(tn, &bn, &sn, &cn);
+                next = !problem_skipped(a, bn);
+                if (next) tile_load<T, MODE, ROWS>(a, a.pc[bn], problem_ptrs(a, bn, false), sn, cn, nxt);
+            }
+            if (have) tile_compute<T, MODE, ROWS>(a, a.pc[b], problem_ptrs(a, b, false), strip, cy, cur);
+            cur = nxt;
+            have = next;
+            b = bn;
+            strip = sn;
+            cy = cn;
+        }
     }
 }
 
@@ -273,56 +315,63 @@ __global__ void __launch_bounds__(128) k_march2p(MArgs<T> a, int strips, int til
 // h (8/3, 0, -1/6, -1/12) and mass h^3 (8/27, 2/27, 1/54, 1/216) for the centre, face,
 // edge and corner neighbours.
 template <typename T>
-void interior_weights(MArgs<T>& a) {
-    const double h = a.g.h;
+void interior_weights(PCoef<T>& c, const GridDesc& g, double omega) {
+    const double h = g.h;
     double kw[4], mw[4];
-    if (a.g.dim == 2) {
+    if (g.dim == 2) {
         const double k2[4] = {8.0 / 3.0, -1.0 / 3.0, -1.0 / 3.0, 0.0};
         const double m2[4] = {16.0 / 36.0, 4.0 / 36.0, 1.0 / 36.0, 0.0};
-        for (int c = 0; c < 4; ++c) {
-            kw[c] = k2[c];
-            mw[c] = m2[c] * h * h;
+        for (int q = 0; q < 4; ++q) {
+            kw[q] = k2[q];
+            mw[q] = m2[q] * h * h;
         }
     } else {
         const double k3[4] = {8.0 / 3.0, 0.0, -1.0 / 6.0, -1.0 / 12.0};
         const double m3[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
-        for (int c = 0; c < 4; ++c) {
-            kw[c] = k3[c] * h;
-            mw[c] = m3[c] * h * h * h;
+        for (int q = 0; q < 4; ++q) {
+            kw[q] = k3[q] * h;
+            mw[q] = m3[q] * h * h * h;
         }
     }
-    for (int c = 0; c < 4; ++c)
-        a.iw[c] = cx<T>(T(double(a.op.cK) * kw[c] + double(a.op.cM.re) * mw[c]), T(double(a.op.cM.im) * mw[c]));
-    const double dr = double(a.opd.cK) * kw[0] + double(a.opd.cM.re) * mw[0], di = double(a.opd.cM.im) * mw[0];
+    for (int q = 0; q < 4; ++q)
+        c.iw[q] = cx<T>(T(double(c.op.cK) * kw[q] + double(c.op.cM.re) * mw[q]), T(double(c.op.cM.im) * mw[q]));
+    const double dr = double(c.opd.cK) * kw[0] + double(c.opd.cM.re) * mw[0], di = double(c.opd.cM.im) * mw[0];
     const double d2 = dr * dr + di * di;
-    const double om = double(a.omega);
-    a.wdinv = d2 > 0 ? cx<T>(T(om * dr / d2), T(-om * di / d2)) : cx<T>(T(0), T(0));
+    c.wdinv = d2 > 0 ? cx<T>(T(omega * dr / d2), T(-omega * di / d2)) : cx<T>(T(0), T(0));
 }
 
-template void interior_weights<float>(MArgs<float>&);
-template void interior_weights<double>(MArgs<double>&);
+template void interior_weights<float>(PCoef<float>&, const GridDesc&, double);
+template void interior_weights<double>(PCoef<double>&, const GridDesc&, double);
+
+template <typename T, int MODE, int ROWS, bool BATCH>
+static cudaError_t run2b(const MArgs<T>& a, int strips, int chunks, cudaStream_t s) {
+    const long long tiles = (long long)strips * chunks * a.nb;
+    // residual-restriction and prolongation tiles carry more rows; they run one tile per warp
+    if constexpr (MODE != M_PROLONG_JACOBI && MODE != M_RESID_RESTRICT) {
+        // persistent once there are several tiles per resident warp: exactly the resident blocks
+        static int per_sm = 0;
+        if (!per_sm) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march2p<T, MODE, ROWS, BATCH>, 128, 0) !=
+                    cudaSuccess ||
+                per_sm < 1) {
+                cudaGetLastError();
+                per_sm = 1;
+            }
+        }
+        const long long resident_blocks = 152LL * per_sm;
+        if (tiles >= 16 * resident_blocks && tiles < (1LL << 31))
+            return klaunch(k_march2p<T, MODE, ROWS, BATCH>, dim3((unsigned)resident_blocks), dim3(128), 0, s, 1, a,
+                           strips, strips * chunks, (int)tiles);
+    }
+    dim3 grd((unsigned)strips, (unsigned)((chunks + 3) / 4), (unsigned)a.nb);
+    return klaunch(k_march2<T, MODE, ROWS, BATCH>, grd, dim3(128), 0, s, 1, a, chunks);
+}
 
 template <typename T, int MODE, int ROWS>
 static cudaError_t run2(const MArgs<T>& a, int strips, int chunks, cudaStream_t s) {
-    const long long tiles = (long long)strips * chunks;
-    // persistent once there are several tiles per resident warp: exactly the resident blocks
-    static int per_sm = 0;
-    if (!per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march2p<T, MODE, ROWS>, 128, 0) != cudaSuccess ||
-            per_sm < 1) {
-            cudaGetLastError();
-            per_sm = 1;
-        }
-    }
-    const long long resident_blocks = 152LL * per_sm;
-    // (residual-restriction and prolongation tiles carry more rows; they run one tile per warp)
-    if (MODE != M_PROLONG_JACOBI && MODE != M_RESID_RESTRICT && tiles >= 16 * resident_blocks &&
-        tiles < (1LL << 31)) {
-        return klaunch(k_march2p<T, MODE, ROWS>, dim3((unsigned)resident_blocks), dim3(128), 0, s, 1, a, strips,
-                       (int)tiles);
-    }
-    dim3 grd((unsigned)strips, (unsigned)((chunks + 3) / 4), 1);
-    return klaunch(k_march2<T, MODE, ROWS>, grd, dim3(128), 0, s, 1, a, chunks);
+    if (a.pc) return run2b<T, MODE, ROWS, true>(a, strips, chunks, s);
+    if (a.nb != 1) return cudaErrorInvalidValue;
+    return run2b<T, MODE, ROWS, false>(a, strips, chunks, s);
 }
 
 // Rows per warp tile: the largest that still leaves about 24 warps per SM (loads in flight),
@@ -331,21 +380,20 @@ template <typename T, int MODE>
 static cudaError_t go2(MArgs<T> a, cudaStream_t s) {
     a.h = T(a.g.h);
     a.ih = T(1.0 / a.g.h);
-    interior_weights(a);
     const long long want = 152LL * 24;
     if constexpr (MODE == M_RESID_RESTRICT) {
         const int nnc = a.g.n / 2 + 1;
         const int strips = (nnc + 13) / 14;
-        int rows = ((long long)strips * ((nnc + 3) / 4) >= want) ? 4 : 2;
+        int rows = ((long long)strips * ((nnc + 3) / 4) * a.nb >= want) ? 4 : 2;
         if (a.tile_rows == 2 || a.tile_rows == 4) rows = a.tile_rows;
         if (rows == 4) return run2<T, MODE, 4>(a, strips, (nnc + 3) / 4, s);
         return run2<T, MODE, 2>(a, strips, (nnc + 1) / 2, s);
     } else {
         const int strips = (a.g.nn + 29) / 30;
         int rows = 2;
-        if ((long long)strips * ((a.g.nn + 3) / 4) >= want) rows = 4;
+        if ((long long)strips * ((a.g.nn + 3) / 4) * a.nb >= want) rows = 4;
         // large grids run persistent 8-row tiles (measured best on 4097^2)
-        if (sizeof(T) == 4 && MODE != M_PROLONG_JACOBI && (long long)strips * ((a.g.nn + 7) / 8) >= 16 * want)
+        if (sizeof(T) == 4 && MODE != M_PROLONG_JACOBI && (long long)strips * ((a.g.nn + 7) / 8) * a.nb >= 16 * want)
             rows = 8;
         if (a.tile_rows == 2 || a.tile_rows == 4 || (a.tile_rows == 8 && sizeof(T) == 4)) rows = a.tile_rows;
         if constexpr (sizeof(T) == 4) {

@@ -37,17 +37,17 @@ __device__ __forceinline__ bool coarse_dir(int I, int nc, int lo, int hi) { retu
 
 // Value of the stencil field at node (i, j, l) (all clamped into the grid).
 template <typename T, int MODE>
-__device__ __forceinline__ Cx<T> field3(const MArgs<T>& a, int i, int j, int l, const Row1<T>& rx,
-                                        const Row1<T>& ry, T h, T ih) {
+__device__ __forceinline__ Cx<T> field3(const MArgs<T>& a, const PCoef<T>& c, const VPtrs<T>& v, int i, int j, int l,
+                                        const Row1<T>& rx, const Row1<T>& ry, T h, T ih) {
     const int n = a.g.n, nn = a.g.nn;
     const long long p = ((long long)l * nn + j) * nn + i;
     if (MODE == M_JACOBI2_ZERO) {
         // first sweep from x = 0: x1 = omega D^{-1} b (zero at Dirichlet nodes)
-        const Cx<T> b = ld<T>(a.z, p);
-        if (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1 && l >= 1 && l <= n - 1) return cmul(a.wdinv, b);
+        const Cx<T> b = ld<T>(v.z, p);
+        if (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1 && l >= 1 && l <= n - 1) return cmul(c.wdinv, b);
         const Row1<T> rz = row1<T>(l, n, a.g.dir[4], a.g.dir[5], h, ih);
         if (rx.masked || ry.masked || rz.masked) return cx<T>(0, 0);
-        return a.omega * cmul(cinv(diag3(rx, ry, rz, a.op)), b);
+        return a.omega * cmul(cinv(diag3(rx, ry, rz, c.op)), b);
     } else if (MODE == M_PROLONG_JACOBI) {
         // x + P e_c: trilinear interpolation of the coarse correction
         if (rx.masked || ry.masked) return cx<T>(0, 0);
@@ -75,13 +75,13 @@ __device__ __forceinline__ Cx<T> field3(const MArgs<T>& a, int i, int j, int l, 
                     const int I = I0 + ai;
                     if (coarse_dir(I, nc, a.g.dir[0], a.g.dir[1])) continue;
                     const T w = oi ? T(0.5) * wj : wj;
-                    e = fma_r(w, ld<T>(a.ec, ((long long)L * nnc + J) * nnc + I), e);
+                    e = fma_r(w, ld<T>(v.ec, ((long long)L * nnc + J) * nnc + I), e);
                 }
             }
         }
-        return ld<T>(a.x, p) + e;
+        return ld<T>(v.x, p) + e;
     } else {
-        return a.xzero ? cx<T>(0, 0) : ld<T>(a.x, p);
+        return a.xzero ? cx<T>(0, 0) : ld<T>(v.x, p);
     }
 }
 
@@ -89,9 +89,14 @@ constexpr int kWarps3 = 8;  // y-rows per tile, including the two halo rows
 
 }  // namespace
 
-template <typename T, int MODE, int R>
-__global__ void __launch_bounds__(32 * kWarps3) k_march3(MArgs<T> a) {
+// BATCH = false: a batch of one, coefficients from the kernel parameters, no activity flags.
+template <typename T, int MODE, int R, bool BATCH>
+__global__ void __launch_bounds__(32 * kWarps3) k_march3(MArgs<T> a, int zt) {
     pdl_entry();
+    const int b = BATCH ? (int)blockIdx.z / zt : 0;  // problem; blockIdx.z % zt: z-tile
+    if (BATCH && problem_skipped(a, b)) return;
+    const PCoef<T> cf = BATCH ? a.pc[b] : a.c0;
+    const VPtrs<T> v = problem_ptrs(a, b, false);
     constexpr int NP = R + 2;  // planes loaded
     constexpr bool NEEDZ = MODE != M_APPLY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -104,19 +109,19 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(MArgs<T> a) {
     const T h = a.h, ih = a.ih;
     const int i = blockIdx.x * 30 + lane - 1;
     const int j = blockIdx.y * (kWarps3 - 2) + w - 1;
-    const int l0 = blockIdx.z * R;
+    const int l0 = (blockIdx.z - b * zt) * R;
     const int ic = clampi3(i, 0, n), jc = clampi3(j, 0, n);
     const Row1<T> rx = row1<T>(ic, n, a.g.dir[0], a.g.dir[1], h, ih);
     const Row1<T> ry = row1<T>(jc, n, a.g.dir[2], a.g.dir[3], h, ih);
 
     Cx<T> fv[NP], xs[NP];
 #pragma unroll
-    for (int t = 0; t < NP; ++t) fv[t] = field3<T, MODE>(a, ic, jc, clampi3(l0 - 1 + t, 0, n), rx, ry, h, ih);
+    for (int t = 0; t < NP; ++t) fv[t] = field3<T, MODE>(a, cf, v, ic, jc, clampi3(l0 - 1 + t, 0, n), rx, ry, h, ih);
     Cx<T> zv[R];
     const bool out_row = w >= 1 && w <= kWarps3 - 2;
 #pragma unroll
     for (int t = 0; t < R; ++t)
-        zv[t] = (NEEDZ && out_row) ? ld<T>(a.z, ((long long)clampi3(l0 + t, 0, n) * nn + jc) * nn + ic) : cx<T>(0, 0);
+        zv[t] = (NEEDZ && out_row) ? ld<T>(v.z, ((long long)clampi3(l0 + t, 0, n) * nn + jc) * nn + ic) : cx<T>(0, 0);
 #pragma unroll
     for (int t = 0; t < NP; ++t) {
         xs[t] = shfl_up3(fv[t]) + shfl_dn3(fv[t]);
@@ -145,8 +150,8 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(MArgs<T> a) {
             const Cx<T> face = xs[tp] + vy1 + (fv[tp - 1] + fv[tp + 1]);
             const Cx<T> edge = sy1 + (xs[tp - 1] + xs[tp + 1]) + (vy0 + vy2);
             const Cx<T> corner = sy0 + sy2;
-            ax = fma_c(a.iw[3], corner, fma_c(a.iw[2], edge, fma_c(a.iw[1], face, cmul(a.iw[0], fv[tp]))));
-            dinv_w = a.wdinv;
+            ax = fma_c(cf.iw[3], corner, fma_c(cf.iw[2], edge, fma_c(cf.iw[1], face, cmul(cf.iw[0], fv[tp]))));
+            dinv_w = cf.wdinv;
         } else {
             const Row1<T> rz = row1<T>(l, n, a.g.dir[4], a.g.dir[5], h, ih);
             masked = rx.masked || ry.masked || rz.masked;
@@ -179,24 +184,25 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(MArgs<T> a) {
             if (rx.face) F = F + Fxf;
             if (ry.face) F = F + Fyf;
             if (rz.face) F = F + Fzf;
-            ax = a.op.cK * Kx;
-            ax = fma_c(a.op.cM, Mx, ax);
-            ax = fma_c(a.op.cG, F, ax);
-            dinv_w = (MODE == M_APPLY || MODE == M_AXPBY) ? cx<T>(0, 0) : a.omega * cinv(diag3(rx, ry, rz, a.opd));
+            ax = cf.op.cK * Kx;
+            ax = fma_c(cf.op.cM, Mx, ax);
+            ax = fma_c(cf.op.cG, F, ax);
+            dinv_w = (MODE == M_APPLY || MODE == M_AXPBY) ? cx<T>(0, 0) : a.omega * cinv(diag3(rx, ry, rz, cf.opd));
         }
+        const Cx<T> alpha = a.use_pc_ab ? cf.alpha : a.alpha, beta = a.use_pc_ab ? cf.beta : a.beta;
         if (masked) {
-            st<T>(a.y, p, cx<T>(0, 0));
-            if (MODE == M_HSS_FIRST) st<T>(a.y2, p, cx<T>(0, 0));
+            st<T>(v.y, p, cx<T>(0, 0));
+            if (MODE == M_HSS_FIRST) st<T>(v.y2, p, cx<T>(0, 0));
         } else if (MODE == M_APPLY) {
-            st<T>(a.y, p, ax);
+            st<T>(v.y, p, ax);
         } else if (MODE == M_AXPBY) {
-            st<T>(a.y, p, fma_c(a.alpha, ax, cmul(a.beta, zv[t])));
+            st<T>(v.y, p, fma_c(alpha, ax, cmul(beta, zv[t])));
         } else if (MODE == M_HSS_FIRST) {
-            const Cx<T> rhs = fma_c(a.alpha, ax, cmul(a.beta, zv[t]));
-            st<T>(a.y, p, rhs);
-            st<T>(a.y2, p, cmul(dinv_w, rhs));
+            const Cx<T> rhs = fma_c(alpha, ax, cmul(beta, zv[t]));
+            st<T>(v.y, p, rhs);
+            st<T>(v.y2, p, cmul(dinv_w, rhs));
         } else {
-            st<T>(a.y, p, fma_c(dinv_w, zv[t] - ax, fv[tp]));
+            st<T>(v.y, p, fma_c(dinv_w, zv[t] - ax, fv[tp]));
         }
         vy0 = vy1;
         vy1 = vy2;
@@ -210,18 +216,20 @@ static cudaError_t go3(MArgs<T> a, cudaStream_t s) {
     // at most 40 KiB: within the default dynamic shared-memory limit, no opt-in needed
     const size_t smem = 2 * (size_t)kWarps3 * (R + 2) * 32 * sizeof(vec2<T>);
     static_assert(2 * kWarps3 * (R + 2) * 32 * sizeof(vec2<T>) <= 48 * 1024, "tile too large");
+    const int zt = (a.g.nn + R - 1) / R;
     dim3 grd((unsigned)((a.g.nn + 29) / 30), (unsigned)((a.g.nn + kWarps3 - 3) / (kWarps3 - 2)),
-             (unsigned)((a.g.nn + R - 1) / R));
-    return klaunch(k_march3<T, MODE, R>, grd, dim3(32 * kWarps3), smem, s, 1, a);
+             (unsigned)(zt * a.nb));
+    if (a.pc) return klaunch(k_march3<T, MODE, R, true>, grd, dim3(32 * kWarps3), smem, s, 1, a, zt);
+    if (a.nb != 1) return cudaErrorInvalidValue;
+    return klaunch(k_march3<T, MODE, R, false>, grd, dim3(32 * kWarps3), smem, s, 1, a, zt);
 }
 
 template <typename T, int MODE>
 static cudaError_t pick3(MArgs<T> a, cudaStream_t s) {
     a.h = T(a.g.h);
     a.ih = T(1.0 / a.g.h);
-    interior_weights(a);
     // more planes per tile on large grids (fewer halo planes), fewer on small ones (more CTAs)
-    const long long ctas4 = (long long)((a.g.nn + 29) / 30) * ((a.g.nn + 5) / 6) * ((a.g.nn + 3) / 4);
+    const long long ctas4 = (long long)((a.g.nn + 29) / 30) * ((a.g.nn + 5) / 6) * ((a.g.nn + 3) / 4) * a.nb;
     if constexpr (sizeof(T) == 4) {
         if (a.tile_rows == 2) return go3<T, MODE, 2>(a, s);
         if (a.tile_rows == 4) return go3<T, MODE, 4>(a, s);

@@ -63,7 +63,8 @@ extern "C" hh_status hh_multidot_noalloc(const void* V, long long ld, int nvec, 
     cudaError_t e = partials_on_current_device(&partials);
     if (e == cudaSuccess)
         e = hh::launch_multidot(static_cast<const double2*>(V), ld, nvec, static_cast<const double2*>(w), n,
-                                partials, static_cast<double2*>(out), (cudaStream_t)cuda_stream);
+                                partials, static_cast<double2*>(out), hh::KBatch{1, 0, 0, 0, nullptr},
+                                (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) {
         hh::set_last_error(cudaGetErrorString(e));
         return HH_ERR_CUDA;

@@ -1,7 +1,14 @@
-// Problem set-up, multigrid V-cycle, shifted-HSS preconditioner (Def. 4.1) and the
-// FP64 flexible GMRES outer iteration (Sec. 5.1), behind the C ABI of include/hh.h.
+// Problems and batches of problems, the multigrid V-cycle, the shifted-HSS preconditioner
+// (Def. 4.1) and the FP64 flexible GMRES outer iteration (Sec. 5.1), behind the C ABI of
+// include/hh.h.
+//
+// A problem object holds nb >= 1 independent Helmholtz problems on the same grid (each with
+// its own k, delta, delta_hat, HSS length and Krylov basis).  Every kernel launch covers all
+// of them; a problem whose HSS loop has ended, or whose outer iteration has converged, is
+// skipped on the device.  hh_create_problem is the batch of one.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -16,6 +23,7 @@
 using hh::Cx;
 using hh::GridDesc;
 using hh::OpCoef;
+using hh::PCoef;
 using zc = std::complex<double>;
 
 namespace {
@@ -39,6 +47,12 @@ hh_status fail(hh_status s, const std::string& msg) {
     do {                                \
         hh_status s_ = (call);          \
         if (s_ != HH_OK) return s_;     \
+    } while (0)
+
+#define HH_LAUNCH(call)                                                                                \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return fail(HH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
 struct Triple {
@@ -70,7 +84,10 @@ int n_hss(double k, double theta) {
     return (int)std::ceil(v);
 }
 
-// Device buffers of the multigrid hierarchy in one precision.
+// Operators with a coefficient table (per problem and level).
+enum Role { R_K = 0, R_M, R_MG, R_AL, R_AR, R_B, R_BHAT, R_COUNT };
+
+// Device buffers of the multigrid hierarchy in one precision (nb problems per vector).
 struct Hier {
     bool ready = false;
     size_t elem = 0;                  // bytes per complex entry
@@ -80,8 +97,10 @@ struct Hier {
     void* ca = nullptr;               // extra level-0 buffers for cycles_per_hss > 1
     void* cb = nullptr;
     void* cres = nullptr;
+    void* pc = nullptr;               // coefficient tables: [role][level][problem] PCoef<T>
+    std::vector<unsigned char> pc_host;  // host copy of the tables
+    void** usrc = nullptr;            // device: per problem, the buffer holding u after the HSS loop
     cudaGraphExec_t graph = nullptr;  // one preconditioner application (the HSS loop)
-    void* graph_out = nullptr;        // buffer that holds u after the graph
     long long graph_kernels = 0;      // kernel nodes in the graph
 };
 
@@ -94,26 +113,31 @@ void set_last_error(const char* msg) { g_last_error = msg; }
 struct hh_problem {
     int device = 0;
     hh_grid grid{};
-    double k = 0, delta = 0, dh = 0;
+    int nb = 1;
+    std::vector<double> k, delta, dh;
+    std::vector<int> nhss;
+    int max_nhss = 0;
     int bc[6] = {0, 0, 0, 0, 0, 0};
     hh_options o{};
     std::vector<GridDesc> lv;
-    Triple AL, AR, B, Bhat;
     cudaStream_t user = nullptr;
     cudaStream_t s = nullptr;  // the problem's own stream (capturable)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int* d_nhss = nullptr;     // device: HSS iterations per problem
+    int* d_active = nullptr;   // device: 1 = problem takes part in the launches
+    int* h_active = nullptr;   // pinned mirror
     Hier hier[2];
-    // FP64 Krylov storage (level 0)
+    // FP64 Krylov storage (level 0), laid out [vector][problem][node]
     long long N = 0;
-    double2* V = nullptr;     // (restart+1) * N
-    double2* Z = nullptr;     // restart * N
-    double2* x = nullptr;     // iterate
-    double2* bvec = nullptr;  // masked right side
-    double2* r = nullptr;     // residual / scratch
+    double2* V = nullptr;       // (restart+1) x nb x N
+    double2* Z = nullptr;       // restart x nb x N
+    double2* x = nullptr;       // nb x N
+    double2* bvec = nullptr;    // nb x N masked right side
+    double2* r = nullptr;       // nb x N residual / scratch
     double2* partials = nullptr;
-    double2* hbuf = nullptr;  // [hA (restart+1) | hB (restart+1) | nrm2]
-    double2* ybuf = nullptr;  // back-substitution result
-    double2* h_host = nullptr;  // pinned mirror of hbuf
+    double2* hbuf = nullptr;    // nb x [hA (restart+1) | hB (restart+1) | nrm2]
+    double2* ybuf = nullptr;    // nb x restart back-substitution results
+    double2* h_host = nullptr;  // pinned mirror of hbuf (and of ybuf)
     size_t bytes = 0;
     std::vector<void*> allocs;
 };
@@ -132,40 +156,104 @@ hh_status dmalloc(hh_problem* p, void** ptr, size_t bytes) {
     return HH_OK;
 }
 
-GridDesc level_desc(const hh_problem* p, int l) {
+GridDesc level_desc(const hh_grid& grid, const int* bc, int l) {
     GridDesc g;
-    g.dim = p->grid.dim;
-    g.n = p->grid.n >> l;
+    g.dim = grid.dim;
+    g.n = grid.n >> l;
     g.nn = g.n + 1;
     g.N = 1;
     for (int d = 0; d < g.dim; ++d) g.N *= g.nn;
     g.h = 1.0 / g.n;
-    for (int s = 0; s < 6; ++s) g.dir[s] = (s < 2 * g.dim) ? (p->bc[s] == HH_BC_DIRICHLET) : 0;
+    for (int s = 0; s < 6; ++s) g.dir[s] = (s < 2 * g.dim) ? (bc[s] == HH_BC_DIRICHLET) : 0;
     return g;
 }
 
-size_t hier_bytes(const hh_grid* grid, int levels, size_t elem) {
+// Device bytes of the Krylov storage and batch bookkeeping for nb problems (matches create).
+size_t krylov_bytes(const hh_grid* grid, int restart, int nb) {
+    long long nn = grid->n + 1;
+    long long N = nn * nn * (grid->dim == 3 ? nn : 1);
+    const size_t m = (size_t)restart, B = (size_t)nb;
+    size_t tot = 2 * sizeof(int) * B;                      // nhss, active
+    tot += (2 * m + 1 + 3) * B * (size_t)N * 16;           // V, Z, x, bvec, r
+    tot += B * (m + 1) * hh::kRedBlocks * 16;              // partials
+    tot += B * (2 * (m + 1) + 1) * 16 + B * m * 16;        // hbuf, ybuf
+    return tot;
+}
+
+// Coefficient table entry of operator `role` on grid g for problem b.
+template <typename T>
+PCoef<T> make_pcoef(const hh_problem* p, int role, const GridDesc& g, int b) {
+    const double k = p->k[b], dh = p->dh[b], delta = p->delta[b];
+    Triple op, opd = triple_AL(k, dh);
+    double al = 0.0, be = 0.0;
+    switch (role) {
+        case R_K: op = {1.0, 0.0, 0.0}; break;
+        case R_M: op = {0.0, 1.0, 0.0}; break;
+        case R_MG: op = {0.0, 0.0, 1.0}; break;
+        case R_AL: op = opd; break;
+        case R_AR:
+            op = triple_AR(k, dh);
+            al = (k - 1.0) / (k + 1.0);
+            be = 2.0 * k / (k + 1.0);
+            break;
+        case R_B: op = triple_B(k, delta); break;
+        default: op = triple_B(k, dh); break;
+    }
+    if (role != R_AR && role != R_AL) opd = op;
+    PCoef<T> c{};
+    c.op = to_coef<T>(op);
+    c.opd = to_coef<T>(opd);
+    c.alpha = Cx<T>{T(al), T(0)};
+    c.beta = Cx<T>{T(be), T(0)};
+    hh::interior_weights<T>(c, g, p->o.omega);
+    return c;
+}
+
+template <typename T>
+hh_status build_tables(hh_problem* p, Hier& H) {
+    const int L = p->o.levels, nb = p->nb;
+    std::vector<PCoef<T>> tab((size_t)R_COUNT * L * nb);
+    for (int role = 0; role < R_COUNT; ++role)
+        for (int l = 0; l < L; ++l)
+            for (int b = 0; b < nb; ++b) tab[((size_t)role * L + l) * nb + b] = make_pcoef<T>(p, role, p->lv[l], b);
+    const size_t bytes = tab.size() * sizeof(PCoef<T>);
+    H.pc_host.assign((const unsigned char*)tab.data(), (const unsigned char*)tab.data() + bytes);
+    HH_TRY(dmalloc(p, &H.pc, bytes));
+    HH_CUDA(cudaMemcpyAsync(H.pc, tab.data(), bytes, cudaMemcpyHostToDevice, p->s));
+    HH_CUDA(cudaStreamSynchronize(p->s));
+    return HH_OK;
+}
+
+// Device bytes of one precision's multigrid buffers for nb problems plus the coefficient
+// tables (matches ensure_hier and ensure_tables).
+size_t hier_bytes(const hh_grid* grid, int levels, int prec, int nb) {
+    const size_t elem = prec == HH_C64 ? 8 : 16, B = (size_t)nb;
     size_t tot = 0;
     for (int l = 0; l < levels; ++l) {
         long long nn = (grid->n >> l) + 1;
         long long N = nn * nn * (grid->dim == 3 ? nn : 1);
-        tot += 4 * (size_t)N * elem;  // xa, xb, b, t
-        if (l == 0) tot += 5 * (size_t)N * elem;
+        tot += 4 * (size_t)N * elem * B;  // xa, xb, b, t
+        if (l == 0) tot += 5 * (size_t)N * elem * B;  // r_lo, rhs, ca, cb, cres
     }
+    tot += sizeof(void*) * B;  // usrc
+    // coefficient tables of both precisions
+    tot += (size_t)R_COUNT * levels * B * (sizeof(PCoef<float>) + sizeof(PCoef<double>));
     return tot;
 }
 
-size_t krylov_bytes(const hh_grid* grid, int restart) {
-    long long nn = grid->n + 1;
-    long long N = nn * nn * (grid->dim == 3 ? nn : 1);
-    size_t tot = (size_t)(2 * restart + 1) * N * 16 + 3 * (size_t)N * 16;
-    tot += (size_t)(restart + 1) * hh::kRedBlocks * 16 + (2 * (restart + 1) + 1) * 16 + (restart + 1) * 16;
-    return tot;
+// Coefficient tables of both precisions (small; built at creation, so that the FP64 outer
+// operator never needs the FP64 multigrid buffers).
+hh_status ensure_tables(hh_problem* p) {
+    if (!p->hier[HH_C64].pc) HH_TRY(build_tables<float>(p, p->hier[HH_C64]));
+    if (!p->hier[HH_C128].pc) HH_TRY(build_tables<double>(p, p->hier[HH_C128]));
+    return HH_OK;
 }
 
+// Multigrid buffers of one precision (allocated on first use).
 hh_status ensure_hier(hh_problem* p, int prec) {
     Hier& H = p->hier[prec];
     if (H.ready) return HH_OK;
+    HH_TRY(ensure_tables(p));
     H.elem = prec == HH_C64 ? 8 : 16;
     const int L = p->o.levels;
     H.xa.assign(L, nullptr);
@@ -173,22 +261,23 @@ hh_status ensure_hier(hh_problem* p, int prec) {
     H.b.assign(L, nullptr);
     H.t.assign(L, nullptr);
     for (int l = 0; l < L; ++l) {
-        const size_t nb = (size_t)p->lv[l].N * H.elem;
-        HH_TRY(dmalloc(p, &H.xa[l], nb));
-        HH_TRY(dmalloc(p, &H.xb[l], nb));
-        HH_TRY(dmalloc(p, &H.b[l], nb));
-        HH_TRY(dmalloc(p, &H.t[l], nb));
-        HH_CUDA(cudaMemsetAsync(H.xa[l], 0, nb, p->s));
-        HH_CUDA(cudaMemsetAsync(H.xb[l], 0, nb, p->s));
-        HH_CUDA(cudaMemsetAsync(H.b[l], 0, nb, p->s));
-        HH_CUDA(cudaMemsetAsync(H.t[l], 0, nb, p->s));
+        const size_t nbytes = (size_t)p->lv[l].N * p->nb * H.elem;
+        HH_TRY(dmalloc(p, &H.xa[l], nbytes));
+        HH_TRY(dmalloc(p, &H.xb[l], nbytes));
+        HH_TRY(dmalloc(p, &H.b[l], nbytes));
+        HH_TRY(dmalloc(p, &H.t[l], nbytes));
+        HH_CUDA(cudaMemsetAsync(H.xa[l], 0, nbytes, p->s));
+        HH_CUDA(cudaMemsetAsync(H.xb[l], 0, nbytes, p->s));
+        HH_CUDA(cudaMemsetAsync(H.b[l], 0, nbytes, p->s));
+        HH_CUDA(cudaMemsetAsync(H.t[l], 0, nbytes, p->s));
     }
-    const size_t n0 = (size_t)p->lv[0].N * H.elem;
+    const size_t n0 = (size_t)p->lv[0].N * p->nb * H.elem;
     HH_TRY(dmalloc(p, &H.r_lo, n0));
     HH_TRY(dmalloc(p, &H.rhs, n0));
     HH_TRY(dmalloc(p, &H.ca, n0));
     HH_TRY(dmalloc(p, &H.cb, n0));
     HH_TRY(dmalloc(p, &H.cres, n0));
+    HH_TRY(dmalloc(p, (void**)&H.usrc, sizeof(void*) * p->nb));
     // one-time kernel configuration now: nothing may call into the runtime's
     // configuration API later, while the stream is being captured
     HH_CUDA(prec == HH_C64 ? hh::prepare_coarse<float>() : hh::prepare_coarse<double>());
@@ -209,42 +298,71 @@ hh_status join_out(hh_problem* p) {
     return HH_OK;
 }
 
-// ------------------------------------------------------------------ V-cycle
-#define HH_LAUNCH(call)                                                                  \
-    do {                                                                                 \
-        cudaError_t e_ = (call);                                                         \
-        if (e_ != cudaSuccess) return fail(HH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-    } while (0)
+// Set the device activity flags of the batch (all problems when flags == nullptr).
+hh_status set_active(hh_problem* p, const std::vector<char>* flags) {
+    for (int b = 0; b < p->nb; ++b) p->h_active[b] = flags ? (*flags)[b] : 1;
+    HH_CUDA(cudaMemcpyAsync(p->d_active, p->h_active, sizeof(int) * p->nb, cudaMemcpyHostToDevice, p->s));
+    // the pinned mirror may be rewritten right after: wait for the copy
+    HH_CUDA(cudaStreamSynchronize(p->s));
+    return HH_OK;
+}
 
+// Device activity flags for the kernels.  A batch of one is never launched while inactive
+// (its outer loop ends first) and its HSS loop is the whole loop: no flags to read.
+const int* active_flags(const hh_problem* p) { return p->nb == 1 ? nullptr : p->d_active; }
+
+// ------------------------------------------------------------------ V-cycle
 template <typename T>
 struct MG {
     using V2 = hh::vec2<T>;
     hh_problem* p;
     Hier* H;
     cudaStream_t s;
-    OpCoef<T> al;
     T omega;
+    int hss_it = -1;  // HSS iteration being recorded (problems whose loop has ended are skipped)
 
     bool d2() const { return p->grid.dim == 2; }
+    long long Nl(int l) const { return p->lv[l].N; }
+
+    const PCoef<T>* table(int role, int l) const {
+        return (const PCoef<T>*)H->pc + ((size_t)role * p->o.levels + l) * p->nb;
+    }
+
+    hh::MArgs<T> margs(int l, int role) const {
+        hh::MArgs<T> a{};
+        a.g = p->lv[l];
+        if (p->nb == 1) {
+            // a batch of one: coefficients in the kernel parameters, no device flags to read
+            a.pc = nullptr;
+            std::memcpy(&a.c0, H->pc_host.data() + ((size_t)role * p->o.levels + l) * sizeof(PCoef<T>),
+                        sizeof(PCoef<T>));
+        } else {
+            a.pc = table(role, l);
+        }
+        a.nb = p->nb;
+        a.bs = Nl(l);
+        a.bsc = l + 1 < p->o.levels ? Nl(l + 1) : 0;
+        a.omega = omega;
+        a.tile_rows = p->o.tile_rows;
+        a.hss_it = p->nb == 1 ? -1 : hss_it;
+        a.nhss = p->d_nhss;
+        a.active = active_flags(p);
+        return a;
+    }
+
+    hh::Batch batch(int l) const {
+        return hh::Batch{p->nb, Nl(l), l + 1 < p->o.levels ? Nl(l + 1) : 0, p->nb == 1 ? -1 : hss_it, p->d_nhss,
+                         active_flags(p)};
+    }
 
     cudaError_t march(int mode, const hh::MArgs<T>& a) const {
         return d2() ? hh::launch_march2<T>(mode, a, s) : hh::launch_march3<T>(mode, a, s);
     }
 
-    hh::MArgs<T> margs(int l, const OpCoef<T>& op) const {
-        hh::MArgs<T> a{};
-        a.g = p->lv[l];
-        a.op = op;
-        a.opd = al;
-        a.omega = omega;
-        a.tile_rows = p->o.tile_rows;
-        return a;
-    }
-
-    // ---- level kernels: fused 2D marching kernels, composed generic kernels in 3D ----
+    // ---- level kernels ----
     // x_out = x_in + omega D^{-1} (b - A_L x_in); x_in == nullptr means 0
     hh_status jacobi(int l, const V2* b, const V2* xin, V2* xout) {
-        hh::MArgs<T> a = margs(l, al);
+        hh::MArgs<T> a = margs(l, R_AL);
         a.x = xin;
         a.xzero = xin == nullptr;
         a.z = b;
@@ -254,7 +372,7 @@ struct MG {
     }
     // two sweeps from x = 0
     hh_status jacobi2_zero(int l, const V2* b, V2* xout) {
-        hh::MArgs<T> a = margs(l, al);
+        hh::MArgs<T> a = margs(l, R_AL);
         a.z = b;
         a.y = xout;
         HH_LAUNCH(march(hh::M_JACOBI2_ZERO, a));
@@ -262,27 +380,24 @@ struct MG {
     }
     // rc = P^T (b - A_L x)
     hh_status resid_restrict(int l, const V2* b, const V2* x, V2* rc) {
+        hh::MArgs<T> a = margs(l, R_AL);
+        a.x = x;
+        a.z = b;
         if (d2()) {
-            hh::MArgs<T> a = margs(l, al);
-            a.x = x;
-            a.z = b;
             a.y = rc;
             HH_LAUNCH(hh::launch_march2<T>(hh::M_RESID_RESTRICT, a, s));
         } else {
-            hh::MArgs<T> a = margs(l, al);
-            a.x = x;
-            a.z = b;
             a.y = (V2*)H->t[l];
             a.alpha = Cx<T>{-1, 0};
             a.beta = Cx<T>{1, 0};
             HH_LAUNCH(hh::launch_march3<T>(hh::M_AXPBY, a, s));
-            HH_LAUNCH(hh::launch_restrict<T>(p->lv[l + 1], (const V2*)H->t[l], rc, s));
+            HH_LAUNCH(hh::launch_restrict<T>(p->lv[l + 1], (const V2*)H->t[l], rc, batch(l), s));
         }
         return HH_OK;
     }
     // xout = x~ + omega D^{-1} (b - A_L x~), x~ = x + P ec
     hh_status prolong_jacobi(int l, V2* x, const V2* ec, const V2* b, V2* xout) {
-        hh::MArgs<T> a = margs(l, al);
+        hh::MArgs<T> a = margs(l, R_AL);
         a.x = x;
         a.ec = ec;
         a.z = b;
@@ -291,28 +406,24 @@ struct MG {
         return HH_OK;
     }
     // rhs = c1 A_R u + c2 r and the first Jacobi sweep x1 = omega D^{-1} rhs (u == nullptr: u = 0)
-    hh_status hss_first(const V2* u, const V2* r, V2* rhs, V2* x1, T c1, T c2) {
-        const OpCoef<T> ar = to_coef<T>(p->AR);
-        hh::MArgs<T> a = margs(0, ar);
+    hh_status hss_first(const V2* u, const V2* r, V2* rhs, V2* x1) {
+        hh::MArgs<T> a = margs(0, R_AR);
         a.x = u;
         a.xzero = u == nullptr;
         a.z = r;
         a.y = rhs;
         a.y2 = x1;
-        a.alpha = Cx<T>{c1, 0};
-        a.beta = Cx<T>{c2, 0};
+        a.use_pc_ab = 1;
         HH_LAUNCH(march(hh::M_HSS_FIRST, a));
         return HH_OK;
     }
-    hh_status hss_rhs(const V2* u, const V2* r, V2* rhs, T c1, T c2) {
-        const OpCoef<T> ar = to_coef<T>(p->AR);
-        hh::MArgs<T> a = margs(0, ar);
+    hh_status hss_rhs(const V2* u, const V2* r, V2* rhs) {
+        hh::MArgs<T> a = margs(0, R_AR);
         a.x = u;
         a.xzero = u == nullptr;
         a.z = r;
         a.y = rhs;
-        a.alpha = Cx<T>{c1, 0};
-        a.beta = Cx<T>{c2, 0};
+        a.use_pc_ab = 1;
         HH_LAUNCH(march(hh::M_AXPBY, a));
         return HH_OK;
     }
@@ -335,7 +446,7 @@ struct MG {
     hh_status smooth_from_zero(int l, const V2* b, int nsweeps, V2** out) {
         V2* cur = (V2*)H->xa[l];
         if (nsweeps == 0) {
-            HH_CUDA(cudaMemsetAsync(cur, 0, (size_t)p->lv[l].N * sizeof(V2), s));
+            HH_LAUNCH(hh::launch_zero<T>(cur, Nl(l), batch(l), s));
         } else if (nsweeps == 1) {
             HH_TRY(jacobi(l, b, nullptr, cur));
         } else {
@@ -355,8 +466,11 @@ struct MG {
             if (xstart) {
                 x = xstart;
                 HH_TRY(smooth(l, b, p->o.nu_coarse - 1, &x));
-            } else if (p->o.nu_coarse >= 1 && p->lv[l].N <= p->o.coarse_cluster_nodes && hh::coarse_fits<T>(p->lv[l])) {
-                HH_LAUNCH(hh::launch_coarse_solve<T>(p->lv[l], al, b, x, p->o.nu_coarse, omega, s));
+            } else if (p->o.nu_coarse >= 1 && Nl(l) <= p->o.coarse_cluster_nodes && hh::coarse_fits<T>(p->lv[l])) {
+                hh::MArgs<T> a = margs(l, R_AL);
+                a.z = b;
+                a.y = x;
+                HH_LAUNCH(hh::launch_coarse_solve<T>(a, p->o.nu_coarse, s));
             } else {
                 HH_TRY(smooth_from_zero(l, b, p->o.nu_coarse, &x));
             }
@@ -374,7 +488,7 @@ struct MG {
         V2* ec;
         HH_TRY(vcycle(l + 1, (const V2*)H->b[l + 1], nullptr, &ec));
         if (p->o.nu_post == 0) {
-            HH_LAUNCH(hh::launch_prolong<T>(p->lv[l], ec, x, s));
+            HH_LAUNCH(hh::launch_prolong<T>(p->lv[l], ec, x, batch(l), s));
         } else {
             V2* oth = other(l, x);
             HH_TRY(prolong_jacobi(l, x, ec, b, oth));
@@ -389,12 +503,12 @@ struct MG {
     hh_status mg_solve(const V2* b, V2* xstart, V2** out) {
         V2* x;
         HH_TRY(vcycle(0, b, xstart, &x));
-        const long long N = p->lv[0].N;
+        const long long N = Nl(0);
         for (int c = 1; c < p->o.cycles_per_hss; ++c) {
             // keep x outside the level-0 ping-pong buffers the next cycle overwrites
             V2* keep = (V2*)((x == (V2*)H->ca) ? H->cb : H->ca);
-            HH_CUDA(cudaMemcpyAsync(keep, x, (size_t)N * sizeof(V2), cudaMemcpyDeviceToDevice, s));
-            hh::MArgs<T> a = margs(0, al);
+            HH_LAUNCH(hh::launch_copy<T>(keep, x, N, batch(0), s));
+            hh::MArgs<T> a = margs(0, R_AL);
             a.x = keep;
             a.z = b;
             a.y = (V2*)H->cres;
@@ -403,37 +517,46 @@ struct MG {
             HH_LAUNCH(march(hh::M_AXPBY, a));
             V2* corr;
             HH_TRY(vcycle(0, (const V2*)H->cres, nullptr, &corr));
-            HH_LAUNCH(hh::launch_add<T>(keep, corr, N, s));
+            HH_LAUNCH(hh::launch_add<T>(keep, corr, N, batch(0), s));
             x = keep;
         }
         *out = x;
         return HH_OK;
     }
 
-    // The HSS loop of Def. 4.1 on r_lo (already in this precision); result buffer in *out.
-    hh_status hss_loop(V2** out) {
-        const double k = p->k;
-        const T c1 = T((k - 1.0) / (k + 1.0)), c2 = T(2.0 * k / (k + 1.0));
-        const int nh = n_hss(k, p->o.theta);
-        const bool fuse = p->o.nu_pre >= 1 && p->o.levels >= 1 &&
-                          !(p->o.levels == 1 && p->o.nu_coarse == 0);
+    // The HSS loop of Def. 4.1 on r_lo (already in this precision).  src[b] receives the
+    // buffer that holds problem b's result (its loop may end before the others').
+    hh_status hss_loop(std::vector<V2*>* src) {
+        const bool fuse = p->o.nu_pre >= 1 && !(p->o.levels == 1 && p->o.nu_coarse == 0);
+        std::vector<V2*> after(p->max_nhss, nullptr);
         V2* u = nullptr;
-        for (int it = 0; it < nh; ++it) {
+        for (int it = 0; it < p->max_nhss; ++it) {
+            hss_it = it;
             if (fuse) {
                 // the first pre-smoothing sweep of the fine level is fused with the right side
                 V2* x1 = (u == (V2*)H->xa[0]) ? (V2*)H->xb[0] : (V2*)H->xa[0];
-                HH_TRY(hss_first(u, (const V2*)H->r_lo, (V2*)H->rhs, x1, c1, c2));
+                HH_TRY(hss_first(u, (const V2*)H->r_lo, (V2*)H->rhs, x1));
                 HH_TRY(mg_solve((const V2*)H->rhs, x1, &u));
             } else {
-                HH_TRY(hss_rhs(u, (const V2*)H->r_lo, (V2*)H->rhs, c1, c2));
+                HH_TRY(hss_rhs(u, (const V2*)H->r_lo, (V2*)H->rhs));
                 HH_TRY(mg_solve((const V2*)H->rhs, nullptr, &u));
             }
+            after[it] = u;
         }
-        if (!u) {  // theta such that no iteration runs: u = 0
-            u = (V2*)H->xa[0];
-            HH_CUDA(cudaMemsetAsync(u, 0, (size_t)p->lv[0].N * sizeof(V2), s));
+        hss_it = -1;
+        // problems with no HSS iteration (theta such that ceil(k^theta) = 0) get u = 0
+        V2* zero = (V2*)H->cres;
+        bool need_zero = false;
+        src->assign(p->nb, nullptr);
+        for (int b = 0; b < p->nb; ++b) {
+            if (p->nhss[b] > 0) {
+                (*src)[b] = after[p->nhss[b] - 1] + (long long)b * Nl(0);
+            } else {
+                (*src)[b] = zero + (long long)b * Nl(0);
+                need_zero = true;
+            }
         }
-        *out = u;
+        if (need_zero) HH_CUDA(cudaMemsetAsync(zero, 0, (size_t)Nl(0) * p->nb * sizeof(V2), s));
         return HH_OK;
     }
 };
@@ -444,40 +567,46 @@ MG<T> make_mg(hh_problem* p, int prec, cudaStream_t s) {
     m.p = p;
     m.H = &p->hier[prec];
     m.s = s;
-    m.al = to_coef<T>(p->AL);
     m.omega = T(p->o.omega);
     return m;
 }
 
-// z (c128) = shifted-HSS preconditioner of r (c128), on the problem stream.
+template <typename T>
+hh_status record_hss(hh_problem* p, int prec) {
+    MG<T> m = make_mg<T>(p, prec, p->s);
+    std::vector<hh::vec2<T>*> src;
+    HH_TRY(m.hss_loop(&src));
+    Hier& H = p->hier[prec];
+    // the pointer table is read by the gather kernel after the loop (constant per problem)
+    static_assert(sizeof(void*) == sizeof(hh::vec2<T>*), "pointer size");
+    HH_CUDA(cudaMemcpyAsync(H.usrc, src.data(), sizeof(void*) * p->nb, cudaMemcpyHostToDevice, p->s));
+    return HH_OK;
+}
+
+// z (c128, nb x N) = shifted-HSS preconditioner of r (c128), on the problem stream, for the
+// active problems.
 hh_status precondition_async(hh_problem* p, const double2* r, double2* z) {
     const int prec = p->o.precision;
     HH_TRY(ensure_hier(p, prec));
     Hier& H = p->hier[prec];
     const long long N = p->lv[0].N;
+    const long long NT = N * p->nb;
     if (prec == HH_C64) {
-        HH_CUDA(hh::launch_cast_d2f(r, (float2*)H.r_lo, N, p->s));
+        HH_LAUNCH(hh::launch_cast_d2f(r, (float2*)H.r_lo, NT, p->s));
     } else {
-        HH_CUDA(cudaMemcpyAsync(H.r_lo, r, (size_t)N * 16, cudaMemcpyDeviceToDevice, p->s));
+        HH_CUDA(cudaMemcpyAsync(H.r_lo, r, (size_t)NT * 16, cudaMemcpyDeviceToDevice, p->s));
     }
-    void* u = nullptr;
     if (p->o.use_graphs) {
         if (!H.graph) {
+            // the pointer table of the results is written once, outside the graph
             cudaGraph_t g;
             const long long k0 = hh::g_kernel_launches;
             HH_CUDA(cudaStreamBeginCapture(p->s, cudaStreamCaptureModeThreadLocal));
-            hh_status st;
-            if (prec == HH_C64) {
-                MG<float> m = make_mg<float>(p, prec, p->s);
-                float2* uo;
-                st = m.hss_loop(&uo);
-                u = uo;
-            } else {
-                MG<double> m = make_mg<double>(p, prec, p->s);
-                double2* uo;
-                st = m.hss_loop(&uo);
-                u = uo;
-            }
+            MG<float> mf = make_mg<float>(p, prec, p->s);
+            MG<double> md = make_mg<double>(p, prec, p->s);
+            std::vector<float2*> sf;
+            std::vector<double2*> sd;
+            hh_status st = prec == HH_C64 ? mf.hss_loop(&sf) : md.hss_loop(&sd);
             cudaError_t ec = cudaStreamEndCapture(p->s, &g);
             if (st != HH_OK) {
                 if (ec == cudaSuccess) cudaGraphDestroy(g);
@@ -487,175 +616,224 @@ hh_status precondition_async(hh_problem* p, const double2* r, double2* z) {
             cudaError_t ei = cudaGraphInstantiate(&H.graph, g, 0);
             cudaGraphDestroy(g);
             HH_CUDA(ei);
-            H.graph_out = u;
             H.graph_kernels = hh::g_kernel_launches - k0;
             hh::g_kernel_launches = k0;
+            const void* srcp = prec == HH_C64 ? (const void*)sf.data() : (const void*)sd.data();
+            HH_CUDA(cudaMemcpyAsync(H.usrc, srcp, sizeof(void*) * p->nb, cudaMemcpyHostToDevice, p->s));
+            HH_CUDA(cudaStreamSynchronize(p->s));
         }
         HH_CUDA(cudaGraphLaunch(H.graph, p->s));
         hh::g_kernel_launches += H.graph_kernels;
-        u = H.graph_out;
     } else {
         if (prec == HH_C64) {
-            MG<float> m = make_mg<float>(p, prec, p->s);
-            float2* uo;
-            HH_TRY(m.hss_loop(&uo));
-            u = uo;
+            HH_TRY(record_hss<float>(p, prec));
         } else {
-            MG<double> m = make_mg<double>(p, prec, p->s);
-            double2* uo;
-            HH_TRY(m.hss_loop(&uo));
-            u = uo;
+            HH_TRY(record_hss<double>(p, prec));
         }
     }
     if (prec == HH_C64) {
-        HH_CUDA(hh::launch_cast_f2d((const float2*)u, z, N, p->s));
+        HH_LAUNCH(hh::launch_gather_c128<float>((const float2* const*)H.usrc, z, N, p->nb, active_flags(p), p->s));
     } else {
-        HH_CUDA(cudaMemcpyAsync(z, u, (size_t)N * 16, cudaMemcpyDeviceToDevice, p->s));
+        HH_LAUNCH(hh::launch_gather_c128<double>((const double2* const*)H.usrc, z, N, p->nb, active_flags(p), p->s));
     }
     return HH_OK;
 }
 
 // ------------------------------------------------------------------ FP64 helpers
-// y = alpha (op x) + beta z  (z == nullptr: y = op x) on level l, stream st
+// y = alpha (op x) + beta z  (z == nullptr: y = op x) on level l for every active problem
 template <typename T>
-hh_status op_axpby(hh_problem* p, int l, const Triple& t, const hh::vec2<T>* x, const hh::vec2<T>* z,
-                   hh::vec2<T>* y, Cx<T> alpha, Cx<T> beta, cudaStream_t st) {
-    const OpCoef<T> op = to_coef<T>(t);
-    hh::MArgs<T> a{};
-    a.g = p->lv[l];
-    a.op = op;
-    a.opd = op;
+hh_status op_axpby(hh_problem* p, int l, int role, const hh::vec2<T>* x, const hh::vec2<T>* z, hh::vec2<T>* y,
+                   Cx<T> alpha, Cx<T> beta, cudaStream_t st) {
+    const int prec = sizeof(T) == 4 ? HH_C64 : HH_C128;
+    HH_TRY(ensure_tables(p));
+    MG<T> m = make_mg<T>(p, prec, st);
+    hh::MArgs<T> a = m.margs(l, role);
     a.x = x;
     a.z = z;
     a.y = y;
     a.alpha = alpha;
     a.beta = beta;
-    a.tile_rows = p->o.tile_rows;
-    const int mode = z ? hh::M_AXPBY : hh::M_APPLY;
-    HH_LAUNCH(p->grid.dim == 2 ? hh::launch_march2<T>(mode, a, st) : hh::launch_march3<T>(mode, a, st));
+    HH_LAUNCH(m.march(z ? hh::M_AXPBY : hh::M_APPLY, a));
     return HH_OK;
 }
 
 hh_status apply_B(hh_problem* p, const double2* x, double2* y) {
-    return op_axpby<double>(p, 0, p->B, x, nullptr, y, Cx<double>{1, 0}, Cx<double>{0, 0}, p->s);
+    return op_axpby<double>(p, 0, R_B, x, nullptr, y, Cx<double>{1, 0}, Cx<double>{0, 0}, p->s);
 }
 
 // r = bvec - B x
 hh_status residual_B(hh_problem* p, const double2* x, double2* r) {
-    return op_axpby<double>(p, 0, p->B, x, p->bvec, r, Cx<double>{-1, 0}, Cx<double>{1, 0}, p->s);
+    return op_axpby<double>(p, 0, R_B, x, p->bvec, r, Cx<double>{-1, 0}, Cx<double>{1, 0}, p->s);
 }
 
-// ||v||^2 into hbuf[slot] (device), and optionally fetched to the host.
+int hstride(const hh_problem* p) { return 2 * (p->o.restart + 1) + 1; }
+
+// ||v_b||^2 into hbuf[b][slot] (device) for every active problem (v_b = v + b N)
 hh_status norm2_dev(hh_problem* p, const double2* v, int slot) {
-    HH_CUDA(hh::launch_multidot(v, 0, 1, v, p->N, p->partials, p->hbuf + slot, p->s));
+    const hh::KBatch kb{p->nb, p->N, p->N, hstride(p), active_flags(p)};
+    HH_CUDA(hh::launch_multidot(v, 0, 1, v, p->N, p->partials, p->hbuf + slot, kb, p->s));
     return HH_OK;
 }
 
-hh_status fetch(hh_problem* p, int count) {
-    HH_CUDA(cudaMemcpyAsync(p->h_host, p->hbuf, (size_t)count * sizeof(double2), cudaMemcpyDeviceToHost, p->s));
+hh_status fetch(hh_problem* p) {
+    HH_CUDA(cudaMemcpyAsync(p->h_host, p->hbuf, (size_t)p->nb * hstride(p) * sizeof(double2), cudaMemcpyDeviceToHost,
+                            p->s));
     HH_CUDA(cudaStreamSynchronize(p->s));
     return HH_OK;
 }
 
 bool finite(double v) { return std::isfinite(v); }
 
-// Flexible GMRES(m) with classical Gram-Schmidt applied twice (CGS2) and Givens rotations.
+// Flexible GMRES(m) with classical Gram-Schmidt applied twice (CGS2) and Givens rotations,
+// the nb problems in lockstep: a problem that converges leaves the launches at once.
 hh_status fgmres(hh_problem* p, double tol, hh_info* info) {
-    const int m = p->o.restart;
+    const int m = p->o.restart, nb = p->nb, hs = hstride(p);
     const long long N = p->N;
-    const int nrm_slot = 2 * (m + 1);
-    HH_TRY(norm2_dev(p, p->bvec, nrm_slot));
-    HH_TRY(fetch(p, nrm_slot + 1));
-    const double bnorm = std::sqrt(p->h_host[nrm_slot].x);
-    if (!finite(bnorm)) return fail(HH_ERR_NONFINITE, "right-hand side is not finite");
-    if (bnorm == 0.0) {
-        HH_CUDA(cudaMemsetAsync(p->x, 0, (size_t)N * 16, p->s));
-        info->rel_residual = 0.0;
-        return HH_OK;
+    const int nrm = 2 * (m + 1);
+    auto H = [&](int b, int i) -> double2& { return p->h_host[(size_t)b * hs + i]; };
+    std::vector<char> solving(nb, 1), in_cycle(nb, 0), ran(nb, 0);
+    HH_TRY(set_active(p, nullptr));
+    HH_TRY(norm2_dev(p, p->bvec, nrm));
+    HH_TRY(fetch(p));
+    std::vector<double> bnorm(nb), beta(nb), rel(nb);
+    for (int b = 0; b < nb; ++b) {
+        bnorm[b] = std::sqrt(H(b, nrm).x);
+        if (!finite(bnorm[b])) return fail(HH_ERR_NONFINITE, "right-hand side " + std::to_string(b) + " is not finite");
     }
     HH_TRY(residual_B(p, p->x, p->r));
-    HH_TRY(norm2_dev(p, p->r, nrm_slot));
-    HH_TRY(fetch(p, nrm_slot + 1));
-    double beta = std::sqrt(p->h_host[nrm_slot].x);
-    if (!finite(beta)) return fail(HH_ERR_NONFINITE, "initial residual is not finite");
-    int its = 0;
-    std::vector<zc> Hm((size_t)(m + 1) * m), g(m + 1), sn(m), y(m);
-    std::vector<double> cs(m);
-    auto Hc = [&](int i, int j) -> zc& { return Hm[(size_t)j * (m + 1) + i]; };
-    double rel = beta / bnorm;
-    while (rel > tol && its < p->o.max_outer) {
-        // V_0 = r / beta
-        HH_CUDA(cudaMemcpyAsync(p->V, p->r, (size_t)N * 16, cudaMemcpyDeviceToDevice, p->s));
-        HH_CUDA(hh::launch_scale(p->V, 1.0 / beta, N, p->s));
-        std::fill(g.begin(), g.end(), zc(0));
-        g[0] = beta;
-        int jend = 0;
+    HH_TRY(norm2_dev(p, p->r, nrm));
+    HH_TRY(fetch(p));
+    for (int b = 0; b < nb; ++b) {
+        beta[b] = std::sqrt(H(b, nrm).x);
+        if (!finite(beta[b])) return fail(HH_ERR_NONFINITE, "initial residual is not finite");
+        rel[b] = bnorm[b] > 0 ? beta[b] / bnorm[b] : 0.0;
+        info[b].outer_its = 0;
+        if (bnorm[b] == 0.0 || rel[b] <= tol || p->o.max_outer == 0) solving[b] = 0;
+    }
+    // zero right sides: u = 0 exactly
+    for (int b = 0; b < nb; ++b)
+        if (bnorm[b] == 0.0) HH_CUDA(cudaMemsetAsync(p->x + (long long)b * N, 0, (size_t)N * 16, p->s));
+    std::vector<zc> Hm((size_t)nb * (m + 1) * m), g((size_t)nb * (m + 1)), sn((size_t)nb * m), y((size_t)nb * m);
+    std::vector<double> cs((size_t)nb * m);
+    std::vector<int> jend(nb, 0);
+    auto Hc = [&](int b, int i, int j) -> zc& { return Hm[((size_t)b * m + j) * (m + 1) + i]; };
+    // Krylov layout [vector][problem][node]: basis vector j of the whole batch is one block
+    const long long blk = (long long)nb * N;
+    while (std::any_of(solving.begin(), solving.end(), [](char c) { return c != 0; })) {
+        in_cycle = solving;
+        std::fill(jend.begin(), jend.end(), 0);
+        HH_TRY(set_active(p, &in_cycle));
+        // V_0 = r / beta (the residual norms are still in hbuf)
+        HH_CUDA(cudaMemcpyAsync(p->V, p->r, (size_t)blk * 16, cudaMemcpyDeviceToDevice, p->s));
+        HH_CUDA(hh::launch_scale_by_rnorm(p->V, p->hbuf + nrm, N, hh::KBatch{nb, N, N, hs, active_flags(p)}, p->s));
+        for (int b = 0; b < nb; ++b) {
+            std::fill(g.begin() + (size_t)b * (m + 1), g.begin() + (size_t)(b + 1) * (m + 1), zc(0));
+            g[(size_t)b * (m + 1)] = beta[b];
+        }
         for (int j = 0; j < m; ++j) {
-            double2* vj = p->V + (long long)j * N;
-            double2* zj = p->Z + (long long)j * N;
-            double2* w = p->V + (long long)(j + 1) * N;
+            double2* vj = p->V + (long long)j * blk;
+            double2* zj = p->Z + (long long)j * blk;
+            double2* w = p->V + (long long)(j + 1) * blk;
             HH_TRY(precondition_async(p, vj, zj));
-            info->hss_its += n_hss(p->k, p->o.theta);
-            info->vcycles += (long long)n_hss(p->k, p->o.theta) * p->o.cycles_per_hss;
+            for (int b = 0; b < nb; ++b)
+                if (in_cycle[b]) {
+                    info[b].hss_its += p->nhss[b];
+                    info[b].vcycles += (long long)p->nhss[b] * p->o.cycles_per_hss;
+                }
             HH_TRY(apply_B(p, zj, w));
             // CGS2: two passes of h = V^H w, w -= V h
+            const hh::KBatch kb{nb, N, N, hs, active_flags(p)};
             double2* hA = p->hbuf;
             double2* hB = p->hbuf + (m + 1);
-            HH_CUDA(hh::launch_multidot(p->V, N, j + 1, w, N, p->partials, hA, p->s));
-            HH_CUDA(hh::launch_multi_axpy(w, p->V, N, j + 1, hA, -1.0, N, p->s));
-            HH_CUDA(hh::launch_multidot(p->V, N, j + 1, w, N, p->partials, hB, p->s));
-            HH_CUDA(hh::launch_multi_axpy(w, p->V, N, j + 1, hB, -1.0, N, p->s));
-            HH_TRY(norm2_dev(p, w, nrm_slot));
-            HH_CUDA(hh::launch_scale_by_rnorm(w, p->hbuf + nrm_slot, N, p->s));
-            HH_TRY(fetch(p, nrm_slot + 1));
-            for (int i = 0; i <= j; ++i)
-                Hc(i, j) = zc(p->h_host[i].x + p->h_host[m + 1 + i].x, p->h_host[i].y + p->h_host[m + 1 + i].y);
-            const double hn = std::sqrt(p->h_host[nrm_slot].x);
-            if (!finite(hn)) return fail(HH_ERR_NONFINITE, "Arnoldi produced a non-finite value");
-            Hc(j + 1, j) = hn;
-            for (int i = 0; i < j; ++i) {
-                const zc t = cs[i] * Hc(i, j) + sn[i] * Hc(i + 1, j);
-                Hc(i + 1, j) = -std::conj(sn[i]) * Hc(i, j) + cs[i] * Hc(i + 1, j);
-                Hc(i, j) = t;
+            HH_CUDA(hh::launch_multidot(p->V, blk, j + 1, w, N, p->partials, hA, kb, p->s));
+            HH_CUDA(hh::launch_multi_axpy(w, p->V, blk, j + 1, hA, -1.0, N, kb, p->s));
+            HH_CUDA(hh::launch_multidot(p->V, blk, j + 1, w, N, p->partials, hB, kb, p->s));
+            HH_CUDA(hh::launch_multi_axpy(w, p->V, blk, j + 1, hB, -1.0, N, kb, p->s));
+            HH_CUDA(hh::launch_multidot(w, 0, 1, w, N, p->partials, p->hbuf + nrm, kb, p->s));
+            HH_CUDA(hh::launch_scale_by_rnorm(w, p->hbuf + nrm, N, kb, p->s));
+            HH_TRY(fetch(p));
+            bool changed = false;
+            for (int b = 0; b < nb; ++b) {
+                if (!in_cycle[b]) continue;
+                for (int i = 0; i <= j; ++i)
+                    Hc(b, i, j) = zc(H(b, i).x + H(b, m + 1 + i).x, H(b, i).y + H(b, m + 1 + i).y);
+                const double hn = std::sqrt(H(b, nrm).x);
+                if (!finite(hn)) return fail(HH_ERR_NONFINITE, "Arnoldi produced a non-finite value");
+                Hc(b, j + 1, j) = hn;
+                double* csb = &cs[(size_t)b * m];
+                zc* snb = &sn[(size_t)b * m];
+                zc* gb = &g[(size_t)b * (m + 1)];
+                for (int i = 0; i < j; ++i) {
+                    const zc t = csb[i] * Hc(b, i, j) + snb[i] * Hc(b, i + 1, j);
+                    Hc(b, i + 1, j) = -std::conj(snb[i]) * Hc(b, i, j) + csb[i] * Hc(b, i + 1, j);
+                    Hc(b, i, j) = t;
+                }
+                const zc h1 = Hc(b, j, j), h2 = Hc(b, j + 1, j);
+                const double den = std::hypot(std::abs(h1), std::abs(h2));
+                if (std::abs(h1) == 0.0) {
+                    csb[j] = 0.0;
+                    snb[j] = 1.0;
+                } else {
+                    csb[j] = std::abs(h1) / den;
+                    snb[j] = (h1 / std::abs(h1)) * std::conj(h2) / den;
+                }
+                Hc(b, j, j) = csb[j] * h1 + snb[j] * h2;
+                Hc(b, j + 1, j) = 0.0;
+                gb[j + 1] = -std::conj(snb[j]) * gb[j];
+                gb[j] = csb[j] * gb[j];
+                info[b].outer_its += 1;
+                jend[b] = j + 1;
+                if (std::abs(gb[j + 1]) / bnorm[b] <= tol || info[b].outer_its >= p->o.max_outer || hn == 0.0) {
+                    in_cycle[b] = 0;
+                    changed = true;
+                }
             }
-            const zc h1 = Hc(j, j), h2 = Hc(j + 1, j);
-            const double den = std::hypot(std::abs(h1), std::abs(h2));
-            if (std::abs(h1) == 0.0) {
-                cs[j] = 0.0;
-                sn[j] = 1.0;
-            } else {
-                cs[j] = std::abs(h1) / den;
-                sn[j] = (h1 / std::abs(h1)) * std::conj(h2) / den;
+            if (!std::any_of(in_cycle.begin(), in_cycle.end(), [](char c) { return c != 0; })) break;
+            if (changed) HH_TRY(set_active(p, &in_cycle));
+        }
+        // x += Z y for every problem that ran this cycle
+        int jmax = 0;
+        for (int b = 0; b < nb; ++b) {
+            ran[b] = jend[b] > 0;
+            jmax = std::max(jmax, jend[b]);
+            zc* yb = &y[(size_t)b * m];
+            std::fill(yb, yb + m, zc(0));
+            for (int i = jend[b] - 1; i >= 0; --i) {
+                zc acc = g[(size_t)b * (m + 1) + i];
+                for (int c = i + 1; c < jend[b]; ++c) acc -= Hc(b, i, c) * yb[c];
+                yb[i] = acc / Hc(b, i, i);
+                if (!finite(yb[i].real()) || !finite(yb[i].imag()))
+                    return fail(HH_ERR_NONFINITE, "least-squares update is not finite");
             }
-            Hc(j, j) = cs[j] * h1 + sn[j] * h2;
-            Hc(j + 1, j) = 0.0;
-            g[j + 1] = -std::conj(sn[j]) * g[j];
-            g[j] = cs[j] * g[j];
-            ++its;
-            jend = j + 1;
-            if (std::abs(g[j + 1]) / bnorm <= tol || its >= p->o.max_outer || hn == 0.0) break;
+            for (int i = 0; i < m; ++i) p->h_host[(size_t)b * m + i] = make_double2(yb[i].real(), yb[i].imag());
         }
-        for (int i = jend - 1; i >= 0; --i) {
-            zc acc = g[i];
-            for (int c = i + 1; c < jend; ++c) acc -= Hc(i, c) * y[c];
-            y[i] = acc / Hc(i, i);
-            if (!finite(y[i].real()) || !finite(y[i].imag()))
-                return fail(HH_ERR_NONFINITE, "least-squares update is not finite");
-        }
-        for (int i = 0; i < jend; ++i) p->h_host[i] = make_double2(y[i].real(), y[i].imag());
-        HH_CUDA(cudaMemcpyAsync(p->ybuf, p->h_host, (size_t)jend * 16, cudaMemcpyHostToDevice, p->s));
-        HH_CUDA(hh::launch_multi_axpy(p->x, p->Z, N, jend, p->ybuf, 1.0, N, p->s));
+        HH_CUDA(cudaMemcpyAsync(p->ybuf, p->h_host, (size_t)nb * m * 16, cudaMemcpyHostToDevice, p->s));
+        HH_TRY(set_active(p, &ran));  // also waits for the copy above
+        HH_CUDA(hh::launch_multi_axpy(p->x, p->Z, blk, jmax, p->ybuf, 1.0, N, hh::KBatch{nb, N, N, m, active_flags(p)},
+                                      p->s));
         HH_TRY(residual_B(p, p->x, p->r));
-        HH_TRY(norm2_dev(p, p->r, nrm_slot));
-        HH_TRY(fetch(p, nrm_slot + 1));
-        beta = std::sqrt(p->h_host[nrm_slot].x);
-        if (!finite(beta)) return fail(HH_ERR_NONFINITE, "residual is not finite");
-        rel = beta / bnorm;
+        HH_TRY(norm2_dev(p, p->r, nrm));
+        HH_TRY(fetch(p));
+        for (int b = 0; b < nb; ++b) {
+            if (!ran[b]) continue;
+            beta[b] = std::sqrt(H(b, nrm).x);
+            if (!finite(beta[b])) return fail(HH_ERR_NONFINITE, "residual is not finite");
+            rel[b] = beta[b] / bnorm[b];
+            if (rel[b] <= tol || info[b].outer_its >= p->o.max_outer) solving[b] = 0;
+        }
     }
-    info->outer_its = its;
-    info->rel_residual = rel;
-    return rel <= tol ? HH_OK : HH_NOT_CONVERGED;
+    HH_TRY(set_active(p, nullptr));
+    bool all = true;
+    for (int b = 0; b < nb; ++b) {
+        info[b].rel_residual = rel[b];
+        all = all && rel[b] <= tol;
+    }
+    return all ? HH_OK : HH_NOT_CONVERGED;
 }
+
+}  // namespace
+
+namespace {
 
 hh_status validate_level(const hh_problem* p, int level, int need_coarser) {
     if (!p) return fail(HH_ERR_INVALID, "null problem");
@@ -666,6 +844,61 @@ hh_status validate_level(const hh_problem* p, int level, int need_coarser) {
 hh_status validate_prec(int prec) {
     if (prec != HH_C64 && prec != HH_C128) return fail(HH_ERR_INVALID, "precision must be HH_C128 or HH_C64");
     return HH_OK;
+}
+
+hh_status check_args(const hh_grid* grid, int nb, const double* k, const double* delta, const double* dh,
+                     const int* bc, const hh_options* o) {
+    if (!grid || !o) return fail(HH_ERR_INVALID, "null grid or options");
+    if (grid->dim != 2 && grid->dim != 3) return fail(HH_ERR_INVALID, "dim must be 2 or 3");
+    // problems index grid.z (2D) or share it with the planes of a 3D level
+    if (nb < 1 || nb > 65535) return fail(HH_ERR_INVALID, "batch size must be in 1..65535");
+    if (grid->dim == 3 && (long long)(grid->n + 1) * nb > 65535)
+        return fail(HH_ERR_INVALID, "3D batch: (n + 1) * nb must not exceed 65535");
+    if (!k || !delta || !dh) return fail(HH_ERR_INVALID, "null k, delta or delta_hat");
+    for (int b = 0; b < nb; ++b)
+        if (!(k[b] > 0) || !(delta[b] >= 0) || !(dh[b] > 0) || !std::isfinite(k[b]) || !std::isfinite(delta[b]) ||
+            !std::isfinite(dh[b]))
+            return fail(HH_ERR_INVALID, "need k > 0, delta >= 0, delta_hat > 0 (finite)");
+    if (o->levels < 1 || o->levels > 16) return fail(HH_ERR_INVALID, "levels must be in 1..16");
+    if (grid->n < 2 || grid->n > (1 << 20)) return fail(HH_ERR_INVALID, "n out of range");
+    if (grid->n % (1 << (o->levels - 1)) != 0 || (grid->n >> (o->levels - 1)) < 1)
+        return fail(HH_ERR_INVALID, "n must be divisible by 2^(levels-1)");
+    if (o->nu_pre < 0 || o->nu_post < 0 || o->nu_coarse < 0 || o->cycles_per_hss < 1)
+        return fail(HH_ERR_INVALID, "negative sweep count or cycles_per_hss < 1");
+    if (o->restart < 1 || o->restart > 63) return fail(HH_ERR_INVALID, "restart must be in 1..63");
+    if (o->max_outer < 0) return fail(HH_ERR_INVALID, "max_outer < 0");
+    if (!(o->theta >= 0) || !(o->omega >= 0) || !(o->omega < 2))
+        return fail(HH_ERR_INVALID, "theta >= 0 and 0 <= omega < 2 required");
+    if (o->precision != HH_C64 && o->precision != HH_C128) return fail(HH_ERR_INVALID, "bad precision");
+    if (o->coarse_cluster_nodes < 0) return fail(HH_ERR_INVALID, "coarse_cluster_nodes < 0");
+    if (o->tile_rows != 0 && o->tile_rows != 2 && o->tile_rows != 4 && o->tile_rows != 8)
+        return fail(HH_ERR_INVALID, "tile_rows must be 0, 2, 4 or 8");
+    if (!bc) return fail(HH_ERR_INVALID, "null bc");
+    for (int s = 0; s < 2 * grid->dim; ++s)
+        if (bc[s] != HH_BC_SOMMERFELD && bc[s] != HH_BC_DIRICHLET) return fail(HH_ERR_INVALID, "bad boundary tag");
+    return HH_OK;
+}
+
+hh_status solve_core(hh_problem* p, double tol, hh_info* info) {
+    const long long k0 = hh::g_kernel_launches;
+    hh_status st = fgmres(p, tol, info);
+    for (int b = 0; b < p->nb; ++b) info[b].device_bytes = p->bytes;
+    info[0].kernel_launches += hh::g_kernel_launches - k0;
+    return st;
+}
+
+void op_role(int op, bool* ok, int* role) {
+    *ok = true;
+    switch (op) {
+        case HH_OP_K: *role = R_K; break;
+        case HH_OP_M: *role = R_M; break;
+        case HH_OP_MGAMMA: *role = R_MG; break;
+        case HH_OP_AL: *role = R_AL; break;
+        case HH_OP_AR: *role = R_AR; break;
+        case HH_OP_B: *role = R_B; break;
+        case HH_OP_BHAT: *role = R_BHAT; break;
+        default: *ok = false; *role = 0;
+    }
 }
 
 }  // namespace
@@ -691,38 +924,15 @@ void hh_options_default(hh_options* o) {
     o->tile_rows = 0;
 }
 
-static hh_status check_args(const hh_grid* grid, double k, double delta, double dh, const int* bc,
-                            const hh_options* o) {
-    if (!grid || !o) return fail(HH_ERR_INVALID, "null grid or options");
-    if (grid->dim != 2 && grid->dim != 3) return fail(HH_ERR_INVALID, "dim must be 2 or 3");
-    if (!(k > 0) || !(delta >= 0) || !(dh > 0) || !std::isfinite(k) || !std::isfinite(delta) ||
-        !std::isfinite(dh))
-        return fail(HH_ERR_INVALID, "need k > 0, delta >= 0, delta_hat > 0 (finite)");
-    if (o->levels < 1 || o->levels > 16) return fail(HH_ERR_INVALID, "levels must be in 1..16");
-    if (grid->n < 2 || grid->n > (1 << 20)) return fail(HH_ERR_INVALID, "n out of range");
-    if (grid->n % (1 << (o->levels - 1)) != 0 || (grid->n >> (o->levels - 1)) < 1)
-        return fail(HH_ERR_INVALID, "n must be divisible by 2^(levels-1)");
-    if (o->nu_pre < 0 || o->nu_post < 0 || o->nu_coarse < 0 || o->cycles_per_hss < 1)
-        return fail(HH_ERR_INVALID, "negative sweep count or cycles_per_hss < 1");
-    if (o->restart < 1 || o->restart > 63) return fail(HH_ERR_INVALID, "restart must be in 1..63");
-    if (o->max_outer < 0) return fail(HH_ERR_INVALID, "max_outer < 0");
-    if (!(o->theta >= 0) || !(o->omega >= 0) || !(o->omega < 2)) return fail(HH_ERR_INVALID, "theta >= 0 and 0 <= omega < 2 required");
-    if (o->precision != HH_C64 && o->precision != HH_C128) return fail(HH_ERR_INVALID, "bad precision");
-    if (o->coarse_cluster_nodes < 0) return fail(HH_ERR_INVALID, "coarse_cluster_nodes < 0");
-    if (o->tile_rows != 0 && o->tile_rows != 2 && o->tile_rows != 4 && o->tile_rows != 8)
-        return fail(HH_ERR_INVALID, "tile_rows must be 0, 2, 4 or 8");
-    if (!bc) return fail(HH_ERR_INVALID, "null bc");
-    for (int s = 0; s < 2 * grid->dim; ++s)
-        if (bc[s] != HH_BC_SOMMERFELD && bc[s] != HH_BC_DIRICHLET) return fail(HH_ERR_INVALID, "bad boundary tag");
-    return HH_OK;
+size_t hh_footprint_batch_bytes(const hh_grid* grid, const hh_options* o, int nb) {
+    if (!grid || !o || nb < 1) return 0;
+    const int bc0[6] = {0, 0, 0, 0, 0, 0};
+    std::vector<double> one(nb, 1.0), zero(nb, 0.0);
+    if (check_args(grid, nb, one.data(), zero.data(), one.data(), bc0, o) != HH_OK) return 0;
+    return hier_bytes(grid, o->levels, o->precision, nb) + krylov_bytes(grid, o->restart, nb);
 }
 
-size_t hh_footprint_bytes(const hh_grid* grid, const hh_options* o) {
-    if (!grid || !o) return 0;
-    const int bc0[6] = {0, 0, 0, 0, 0, 0};
-    if (check_args(grid, 1.0, 0.0, 1.0, bc0, o) != HH_OK) return 0;
-    return hier_bytes(grid, o->levels, o->precision == HH_C64 ? 8 : 16) + krylov_bytes(grid, o->restart);
-}
+size_t hh_footprint_bytes(const hh_grid* grid, const hh_options* o) { return hh_footprint_batch_bytes(grid, o, 1); }
 
 void hh_destroy(hh_problem* p) {
     if (!p) return;
@@ -734,6 +944,7 @@ void hh_destroy(hh_problem* p) {
         if (p->hier[i].graph) cudaGraphExecDestroy(p->hier[i].graph);
     for (void* a : p->allocs) cudaFree(a);
     if (p->h_host) cudaFreeHost(p->h_host);
+    if (p->h_active) cudaFreeHost(p->h_active);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);
     if (p->s) cudaStreamDestroy(p->s);
@@ -741,28 +952,29 @@ void hh_destroy(hh_problem* p) {
     delete p;
 }
 
-hh_status hh_create_problem(const hh_grid* grid, double k, double delta, double delta_hat, const int* bc,
-                            const hh_options* opts, void* cuda_stream, hh_problem** out) {
+hh_status hh_create_batch(const hh_grid* grid, int nb, const double* k, const double* delta, const double* delta_hat,
+                          const int* bc, const hh_options* opts, void* cuda_stream, hh_problem** out) {
     if (!out) return fail(HH_ERR_INVALID, "null out");
     *out = nullptr;
-    HH_TRY(check_args(grid, k, delta, delta_hat, bc, opts));
+    HH_TRY(check_args(grid, nb, k, delta, delta_hat, bc, opts));
     hh_problem* p = new hh_problem();
     cudaGetDevice(&p->device);
     p->grid = *grid;
-    p->k = k;
-    p->delta = delta;
-    p->dh = delta_hat;
+    p->nb = nb;
+    p->k.assign(k, k + nb);
+    p->delta.assign(delta, delta + nb);
+    p->dh.assign(delta_hat, delta_hat + nb);
     for (int s = 0; s < 6; ++s) p->bc[s] = s < 2 * grid->dim ? bc[s] : 0;
     p->o = *opts;
     // automatic damping: on levels where the shifted mass term dominates, D^{-1} A_L has
     // spectrum close to D^{-1} M, which reaches 9/4 in 2D and 27/8 in 3D; omega must stay
     // below 2 / 27 * 8 = 0.59 in 3D for the sweeps not to amplify smooth modes
     if (p->o.omega == 0.0) p->o.omega = grid->dim == 3 ? 0.5 : 0.6;
-    p->AL = triple_AL(k, delta_hat);
-    p->AR = triple_AR(k, delta_hat);
-    p->B = triple_B(k, delta);
-    p->Bhat = triple_B(k, delta_hat);
-    for (int l = 0; l < opts->levels; ++l) p->lv.push_back(level_desc(p, l));
+    for (int b = 0; b < nb; ++b) {
+        p->nhss.push_back(n_hss(k[b], p->o.theta));
+        p->max_nhss = std::max(p->max_nhss, p->nhss.back());
+    }
+    for (int l = 0; l < opts->levels; ++l) p->lv.push_back(level_desc(*grid, p->bc, l));
     p->N = p->lv[0].N;
     p->user = (cudaStream_t)cuda_stream;
     hh_status st = HH_OK;
@@ -774,122 +986,122 @@ hh_status hh_create_problem(const hh_grid* grid, double k, double delta, double 
         cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(HH_ERR_CUDA, "stream/event creation failed"));
-    if ((st = ensure_hier(p, opts->precision)) != HH_OK) return bail(st);
     const int m = opts->restart;
     const long long N = p->N;
-    if ((st = dmalloc(p, (void**)&p->V, (size_t)(m + 1) * N * 16)) != HH_OK) return bail(st);
-    if ((st = dmalloc(p, (void**)&p->Z, (size_t)m * N * 16)) != HH_OK) return bail(st);
-    if ((st = dmalloc(p, (void**)&p->x, (size_t)N * 16)) != HH_OK) return bail(st);
-    if ((st = dmalloc(p, (void**)&p->bvec, (size_t)N * 16)) != HH_OK) return bail(st);
-    if ((st = dmalloc(p, (void**)&p->r, (size_t)N * 16)) != HH_OK) return bail(st);
-    if ((st = dmalloc(p, (void**)&p->partials, (size_t)(m + 1) * hh::kRedBlocks * 16)) != HH_OK) return bail(st);
-    if ((st = dmalloc(p, (void**)&p->hbuf, (size_t)(2 * (m + 1) + 1) * 16)) != HH_OK) return bail(st);
-    if ((st = dmalloc(p, (void**)&p->ybuf, (size_t)(m + 1) * 16)) != HH_OK) return bail(st);
-    if (cudaMallocHost((void**)&p->h_host, (size_t)(2 * (m + 1) + 1) * 16) != cudaSuccess) {
-        p->h_host = nullptr;
+    const size_t hs = (size_t)(2 * (m + 1) + 1);
+    if ((st = dmalloc(p, (void**)&p->d_nhss, sizeof(int) * nb)) != HH_OK) return bail(st);
+    if ((st = dmalloc(p, (void**)&p->d_active, sizeof(int) * nb)) != HH_OK) return bail(st);
+    if ((st = dmalloc(p, (void**)&p->V, (size_t)(m + 1) * nb * N * 16)) != HH_OK) return bail(st);
+    if ((st = dmalloc(p, (void**)&p->Z, (size_t)m * nb * N * 16)) != HH_OK) return bail(st);
+    if ((st = dmalloc(p, (void**)&p->x, (size_t)nb * N * 16)) != HH_OK) return bail(st);
+    if ((st = dmalloc(p, (void**)&p->bvec, (size_t)nb * N * 16)) != HH_OK) return bail(st);
+    if ((st = dmalloc(p, (void**)&p->r, (size_t)nb * N * 16)) != HH_OK) return bail(st);
+    if ((st = dmalloc(p, (void**)&p->partials, (size_t)nb * (m + 1) * hh::kRedBlocks * 16)) != HH_OK) return bail(st);
+    if ((st = dmalloc(p, (void**)&p->hbuf, (size_t)nb * hs * 16)) != HH_OK) return bail(st);
+    if ((st = dmalloc(p, (void**)&p->ybuf, (size_t)nb * m * 16)) != HH_OK) return bail(st);
+    if (cudaMallocHost((void**)&p->h_host, (size_t)nb * hs * 16) != cudaSuccess ||
+        cudaMallocHost((void**)&p->h_active, sizeof(int) * nb) != cudaSuccess)
         return bail(fail(HH_ERR_OOM, "pinned host allocation failed"));
-    }
-    if (cudaMemsetAsync(p->V, 0, (size_t)(m + 1) * N * 16, p->s) != cudaSuccess ||
-        cudaMemsetAsync(p->Z, 0, (size_t)m * N * 16, p->s) != cudaSuccess ||
+    if (cudaMemcpyAsync(p->d_nhss, p->nhss.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, p->s) != cudaSuccess)
+        return bail(fail(HH_ERR_CUDA, "initialisation failed"));
+    if ((st = set_active(p, nullptr)) != HH_OK) return bail(st);
+    if ((st = ensure_hier(p, opts->precision)) != HH_OK) return bail(st);
+    if (cudaMemsetAsync(p->V, 0, (size_t)(m + 1) * nb * N * 16, p->s) != cudaSuccess ||
+        cudaMemsetAsync(p->Z, 0, (size_t)m * nb * N * 16, p->s) != cudaSuccess ||
         cudaStreamSynchronize(p->s) != cudaSuccess)
         return bail(fail(HH_ERR_CUDA, "initialisation failed"));
     *out = p;
     return HH_OK;
 }
 
+hh_status hh_create_problem(const hh_grid* grid, double k, double delta, double delta_hat, const int* bc,
+                            const hh_options* opts, void* cuda_stream, hh_problem** out) {
+    return hh_create_batch(grid, 1, &k, &delta, &delta_hat, bc, opts, cuda_stream, out);
+}
+
+int hh_batch_size(const hh_problem* p) { return p ? p->nb : 0; }
+
 long long hh_level_nodes(const hh_problem* p, int level) {
     if (!p || level < 0 || level >= p->o.levels) return 0;
     return p->lv[level].N;
 }
 
-static hh_status solve_core(hh_problem* p, double tol, hh_info* info) {
-    const long long k0 = hh::g_kernel_launches;
-    hh_status st = fgmres(p, tol, info);
-    info->device_bytes = p->bytes;
-    info->kernel_launches += hh::g_kernel_launches - k0;
-    return st;
-}
-
 hh_status hh_solve(hh_problem* p, const void* rhs, double tol, void* u, const void* x0, hh_info* info) {
     if (!p || !rhs || !u) return fail(HH_ERR_INVALID, "null argument");
     if (!(tol > 0)) return fail(HH_ERR_INVALID, "tol must be > 0");
-    hh_info local{};
-    hh_info* inf = info ? info : &local;
-    *inf = hh_info{};
-    inf->rel_residual = NAN;
+    std::vector<hh_info> local(p->nb);
+    hh_info* inf = info ? info : local.data();
+    for (int b = 0; b < p->nb; ++b) {
+        inf[b] = hh_info{};
+        inf[b].rel_residual = NAN;
+    }
     auto t0 = std::chrono::steady_clock::now();
     HH_TRY(join_in(p));
-    HH_CUDA(hh::launch_mask_copy(p->lv[0], (const double2*)rhs, p->bvec, p->s));
+    HH_LAUNCH(hh::launch_mask_copy(p->lv[0], (const double2*)rhs, p->bvec, p->nb, p->s));
     if (x0) {
-        HH_CUDA(hh::launch_mask_copy(p->lv[0], (const double2*)x0, p->x, p->s));
+        HH_LAUNCH(hh::launch_mask_copy(p->lv[0], (const double2*)x0, p->x, p->nb, p->s));
     } else {
-        HH_CUDA(cudaMemsetAsync(p->x, 0, (size_t)p->N * 16, p->s));
+        HH_CUDA(cudaMemsetAsync(p->x, 0, (size_t)p->nb * p->N * 16, p->s));
     }
     hh_status st = solve_core(p, tol, inf);
     if (st == HH_OK || st == HH_NOT_CONVERGED) {
-        HH_CUDA(cudaMemcpyAsync(u, p->x, (size_t)p->N * 16, cudaMemcpyDeviceToDevice, p->s));
+        HH_CUDA(cudaMemcpyAsync(u, p->x, (size_t)p->nb * p->N * 16, cudaMemcpyDeviceToDevice, p->s));
     } else {
-        inf->rel_residual = NAN;
+        for (int b = 0; b < p->nb; ++b) inf[b].rel_residual = NAN;
+        set_active(p, nullptr);
     }
     HH_TRY(join_out(p));
     HH_CUDA(cudaStreamSynchronize(p->s));
-    inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int b = 0; b < p->nb; ++b) inf[b].seconds = sec;
     return st;
 }
 
 hh_status hh_solve_host(hh_problem* p, const void* rhs_host, double tol, void* u_host, hh_info* info) {
     if (!p || !rhs_host || !u_host) return fail(HH_ERR_INVALID, "null argument");
     if (!(tol > 0)) return fail(HH_ERR_INVALID, "tol must be > 0");
-    hh_info local{};
-    hh_info* inf = info ? info : &local;
-    *inf = hh_info{};
-    inf->rel_residual = NAN;
+    std::vector<hh_info> local(p->nb);
+    hh_info* inf = info ? info : local.data();
+    for (int b = 0; b < p->nb; ++b) {
+        inf[b] = hh_info{};
+        inf[b].rel_residual = NAN;
+    }
+    const size_t bytes = (size_t)p->nb * p->N * 16;
     auto t0 = std::chrono::steady_clock::now();
     HH_TRY(join_in(p));
     // stage the right side through r, then mask into bvec
-    HH_CUDA(cudaMemcpyAsync(p->r, rhs_host, (size_t)p->N * 16, cudaMemcpyHostToDevice, p->s));
-    HH_CUDA(hh::launch_mask_copy(p->lv[0], p->r, p->bvec, p->s));
-    HH_CUDA(cudaMemsetAsync(p->x, 0, (size_t)p->N * 16, p->s));
+    HH_CUDA(cudaMemcpyAsync(p->r, rhs_host, bytes, cudaMemcpyHostToDevice, p->s));
+    HH_LAUNCH(hh::launch_mask_copy(p->lv[0], p->r, p->bvec, p->nb, p->s));
+    HH_CUDA(cudaMemsetAsync(p->x, 0, bytes, p->s));
     hh_status st = solve_core(p, tol, inf);
     if (st == HH_OK || st == HH_NOT_CONVERGED) {
-        HH_CUDA(cudaMemcpyAsync(u_host, p->x, (size_t)p->N * 16, cudaMemcpyDeviceToHost, p->s));
+        HH_CUDA(cudaMemcpyAsync(u_host, p->x, bytes, cudaMemcpyDeviceToHost, p->s));
     } else {
-        inf->rel_residual = NAN;
+        for (int b = 0; b < p->nb; ++b) inf[b].rel_residual = NAN;
+        set_active(p, nullptr);
     }
     HH_TRY(join_out(p));
     HH_CUDA(cudaStreamSynchronize(p->s));
-    inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int b = 0; b < p->nb; ++b) inf[b].seconds = sec;
     return st;
 }
 
 // ---------------------------------------------------------------- building blocks
-static Triple op_triple(const hh_problem* p, int op, bool* ok) {
-    *ok = true;
-    switch (op) {
-        case HH_OP_K: return {1.0, 0.0, 0.0};
-        case HH_OP_M: return {0.0, 1.0, 0.0};
-        case HH_OP_MGAMMA: return {0.0, 0.0, 1.0};
-        case HH_OP_AL: return p->AL;
-        case HH_OP_AR: return p->AR;
-        case HH_OP_B: return p->B;
-        case HH_OP_BHAT: return p->Bhat;
-        default: *ok = false; return {0.0, 0.0, 0.0};
-    }
-}
-
 hh_status hh_apply(hh_problem* p, int level, int op, int precision, const void* x, void* y) {
     HH_TRY(validate_level(p, level, 0));
     HH_TRY(validate_prec(precision));
     if (!x || !y) return fail(HH_ERR_INVALID, "null vector");
     bool ok;
-    Triple t = op_triple(p, op, &ok);
+    int role;
+    op_role(op, &ok, &role);
     if (!ok) return fail(HH_ERR_INVALID, "unknown operator");
     HH_TRY(join_in(p));
     if (precision == HH_C64) {
-        HH_TRY(op_axpby<float>(p, level, t, (const float2*)x, nullptr, (float2*)y, Cx<float>{1, 0}, Cx<float>{0, 0},
-                               p->s));
+        HH_TRY(op_axpby<float>(p, level, role, (const float2*)x, nullptr, (float2*)y, Cx<float>{1, 0},
+                               Cx<float>{0, 0}, p->s));
     } else {
-        HH_TRY(op_axpby<double>(p, level, t, (const double2*)x, nullptr, (double2*)y, Cx<double>{1, 0},
+        HH_TRY(op_axpby<double>(p, level, role, (const double2*)x, nullptr, (double2*)y, Cx<double>{1, 0},
                                 Cx<double>{0, 0}, p->s));
     }
     return join_out(p);
@@ -899,6 +1111,7 @@ hh_status hh_jacobi(hh_problem* p, int level, int precision, const void* b, cons
     HH_TRY(validate_level(p, level, 0));
     HH_TRY(validate_prec(precision));
     if (!b || !x_out || x_out == x_in || x_out == b) return fail(HH_ERR_INVALID, "bad vectors");
+    HH_TRY(ensure_tables(p));
     HH_TRY(join_in(p));
     if (precision == HH_C64) {
         MG<float> m = make_mg<float>(p, precision, p->s);
@@ -931,10 +1144,11 @@ hh_status hh_prolong_correct(hh_problem* p, int level, int precision, const void
     HH_TRY(validate_prec(precision));
     if (!ec || !x) return fail(HH_ERR_INVALID, "null vector");
     HH_TRY(join_in(p));
+    const hh::Batch bt{p->nb, p->lv[level].N, p->lv[level + 1].N, -1, nullptr, nullptr};
     if (precision == HH_C64) {
-        HH_CUDA(hh::launch_prolong<float>(p->lv[level], (const float2*)ec, (float2*)x, p->s));
+        HH_LAUNCH(hh::launch_prolong<float>(p->lv[level], (const float2*)ec, (float2*)x, bt, p->s));
     } else {
-        HH_CUDA(hh::launch_prolong<double>(p->lv[level], (const double2*)ec, (double2*)x, p->s));
+        HH_LAUNCH(hh::launch_prolong<double>(p->lv[level], (const double2*)ec, (double2*)x, bt, p->s));
     }
     return join_out(p);
 }
@@ -945,17 +1159,17 @@ hh_status hh_vcycle(hh_problem* p, int precision, const void* b, void* x) {
     if (!b || !x) return fail(HH_ERR_INVALID, "null vector");
     HH_TRY(ensure_hier(p, precision));
     HH_TRY(join_in(p));
-    const size_t nb = (size_t)p->N * (precision == HH_C64 ? 8 : 16);
+    const size_t nbytes = (size_t)p->nb * p->N * (precision == HH_C64 ? 8 : 16);
     if (precision == HH_C64) {
         MG<float> m = make_mg<float>(p, precision, p->s);
         float2* out;
         HH_TRY(m.vcycle(0, (const float2*)b, nullptr, &out));
-        HH_CUDA(cudaMemcpyAsync(x, out, nb, cudaMemcpyDeviceToDevice, p->s));
+        HH_CUDA(cudaMemcpyAsync(x, out, nbytes, cudaMemcpyDeviceToDevice, p->s));
     } else {
         MG<double> m = make_mg<double>(p, precision, p->s);
         double2* out;
         HH_TRY(m.vcycle(0, (const double2*)b, nullptr, &out));
-        HH_CUDA(cudaMemcpyAsync(x, out, nb, cudaMemcpyDeviceToDevice, p->s));
+        HH_CUDA(cudaMemcpyAsync(x, out, nbytes, cudaMemcpyDeviceToDevice, p->s));
     }
     return join_out(p);
 }
@@ -964,14 +1178,14 @@ hh_status hh_hss_rhs(hh_problem* p, int precision, const void* u, const void* r,
     HH_TRY(validate_level(p, 0, 0));
     HH_TRY(validate_prec(precision));
     if (!r || !rhs) return fail(HH_ERR_INVALID, "null vector");
-    const double k = p->k, c1 = (k - 1.0) / (k + 1.0), c2 = 2.0 * k / (k + 1.0);
+    HH_TRY(ensure_tables(p));
     HH_TRY(join_in(p));
     if (precision == HH_C64) {
         MG<float> m = make_mg<float>(p, precision, p->s);
-        HH_TRY(m.hss_rhs((const float2*)u, (const float2*)r, (float2*)rhs, float(c1), float(c2)));
+        HH_TRY(m.hss_rhs((const float2*)u, (const float2*)r, (float2*)rhs));
     } else {
         MG<double> m = make_mg<double>(p, precision, p->s);
-        HH_TRY(m.hss_rhs((const double2*)u, (const double2*)r, (double2*)rhs, c1, c2));
+        HH_TRY(m.hss_rhs((const double2*)u, (const double2*)r, (double2*)rhs));
     }
     return join_out(p);
 }
@@ -988,18 +1202,22 @@ hh_status hh_precondition(hh_problem* p, const void* r, void* z) {
 hh_status hh_load_vector(hh_problem* p, const void* f, void* b) {
     if (!p || !f || !b) return fail(HH_ERR_INVALID, "null argument");
     HH_TRY(join_in(p));
-    HH_TRY(op_axpby<double>(p, 0, Triple{0.0, 1.0, 0.0}, (const double2*)f, nullptr, (double2*)b, Cx<double>{1, 0},
-                            Cx<double>{0, 0}, p->s));
+    HH_TRY(op_axpby<double>(p, 0, R_M, (const double2*)f, nullptr, (double2*)b, Cx<double>{1, 0}, Cx<double>{0, 0},
+                            p->s));
     return join_out(p);
 }
 
 hh_status hh_dot(hh_problem* p, const void* x, const void* y, double* out) {
     if (!p || !x || !y || !out) return fail(HH_ERR_INVALID, "null argument");
     HH_TRY(join_in(p));
-    HH_CUDA(hh::launch_multidot((const double2*)x, 0, 1, (const double2*)y, p->N, p->partials, p->hbuf, p->s));
-    HH_TRY(fetch(p, 1));
-    out[0] = p->h_host[0].x;
-    out[1] = p->h_host[0].y;
+    const int hs = hstride(p);
+    HH_CUDA(hh::launch_multidot((const double2*)x, 0, 1, (const double2*)y, p->N, p->partials, p->hbuf,
+                                hh::KBatch{p->nb, p->N, p->N, hs, nullptr}, p->s));
+    HH_TRY(fetch(p));
+    for (int b = 0; b < p->nb; ++b) {
+        out[2 * b] = p->h_host[(size_t)b * hs].x;
+        out[2 * b + 1] = p->h_host[(size_t)b * hs].y;
+    }
     return HH_OK;
 }
 

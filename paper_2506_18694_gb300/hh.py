@@ -22,7 +22,8 @@ SOMMERFELD, DIRICHLET = 0, 1
 OP = {"K": 0, "M": 1, "MGAMMA": 2, "AL": 3, "AR": 4, "B": 5, "BHAT": 6}
 
 EXPORTED = (
-    "hh_options_default", "hh_footprint_bytes", "hh_create_problem", "hh_destroy", "hh_solve",
+    "hh_options_default", "hh_footprint_bytes", "hh_footprint_batch_bytes", "hh_create_problem",
+    "hh_create_batch", "hh_batch_size", "hh_destroy", "hh_solve",
     "hh_solve_host", "hh_level_nodes", "hh_apply", "hh_jacobi", "hh_residual_restrict",
     "hh_prolong_correct", "hh_vcycle", "hh_hss_rhs", "hh_precondition", "hh_load_vector", "hh_dot",
     "hh_multidot_noalloc", "hh_status_string", "hh_last_error",
@@ -75,8 +76,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     sig = {
         "hh_options_default": (V, [ctypes.POINTER(Options)]),
         "hh_footprint_bytes": (ctypes.c_size_t, [ctypes.POINTER(Grid), ctypes.POINTER(Options)]),
+        "hh_footprint_batch_bytes": (ctypes.c_size_t, [ctypes.POINTER(Grid), ctypes.POINTER(Options), I]),
         "hh_create_problem": (I, [ctypes.POINTER(Grid), D, D, D, ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(Options), P, ctypes.POINTER(P)]),
+        "hh_create_batch": (I, [ctypes.POINTER(Grid), I, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
+                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Options), P, ctypes.POINTER(P)]),
+        "hh_batch_size": (I, [P]),
         "hh_destroy": (V, [P]),
         "hh_solve": (I, [P, P, D, P, P, ctypes.POINTER(Info)]),
         "hh_solve_host": (I, [P, P, D, P, ctypes.POINTER(Info)]),
@@ -119,16 +124,19 @@ def default_options(**kw) -> Options:
     return o
 
 
-def footprint_bytes(dim: int, n: int, options: Options | None = None) -> int:
+def footprint_bytes(dim: int, n: int, options: Options | None = None, nb: int = 1) -> int:
+    """Device bytes of a problem (nb = 1) or a batch of nb problems; 0 if invalid."""
     o = options or default_options()
-    return int(load_library().hh_footprint_bytes(ctypes.byref(Grid(dim, n)), ctypes.byref(o)))
+    return int(load_library().hh_footprint_batch_bytes(ctypes.byref(Grid(dim, n)), ctypes.byref(o), int(nb)))
 
 
-def _ptr(t):
+def _ptr(t, numel=None):
     if t is None:
         return None
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("vectors must be contiguous CUDA tensors")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"vector has {t.numel()} entries, expected {numel}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -140,12 +148,28 @@ def _prec_of(t):
     raise TypeError("vectors must be complex64 or complex128")
 
 
+def _vec(v, nb):
+    a = np.atleast_1d(np.asarray(v, dtype=np.float64))
+    if a.size == 1 and nb > 1:
+        a = np.full(nb, a[0])
+    return a
+
+
 class Problem:
-    """One Helmholtz problem: grid, wavenumber k, delta, delta_hat, boundary tags, options."""
+    """A Helmholtz problem (scalar k, delta, delta_hat) or a batch of them (sequences of
+    equal length): one grid, boundary tags and options, its own k/delta/delta_hat per
+    problem.  Vectors of a batch hold the nb problems' level vectors one after another
+    (flat, or shaped (nb, nodes))."""
 
     def __init__(self, dim, n, k, delta, delta_hat, bc, options: Options | None = None, stream=None):
         lib = load_library()
-        self.dim, self.n, self.k = dim, n, k
+        batched = any(np.ndim(v) > 0 for v in (k, delta, delta_hat))
+        nb = max(np.size(v) for v in (k, delta, delta_hat))
+        ks, ds, dhs = (_vec(v, nb) for v in (k, delta, delta_hat))
+        if not (ks.size == ds.size == dhs.size == nb):
+            raise ValueError("k, delta and delta_hat need the same number of problems")
+        self.dim, self.n, self.nb, self.batched = dim, n, int(nb), batched
+        self.k = ks if batched else float(ks[0])
         self.options = options or default_options()
         bc = list(bc) + [0] * (6 - len(bc))
         arr = (ctypes.c_int * 6)(*bc)
@@ -153,8 +177,10 @@ class Problem:
         self._stream = s
         handle = ctypes.c_void_p(s.cuda_stream)
         out = ctypes.c_void_p()
-        _check(lib.hh_create_problem(ctypes.byref(Grid(dim, n)), float(k), float(delta), float(delta_hat),
-                                     arr, ctypes.byref(self.options), handle, ctypes.byref(out)))
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._keep = (np.ascontiguousarray(ks), np.ascontiguousarray(ds), np.ascontiguousarray(dhs))
+        _check(lib.hh_create_batch(ctypes.byref(Grid(dim, n)), self.nb, *(a.ctypes.data_as(dp) for a in self._keep),
+                                   arr, ctypes.byref(self.options), handle, ctypes.byref(out)))
         self._p = out
         self._lib = lib
 
@@ -176,69 +202,92 @@ class Problem:
         self.close()
 
     def nodes(self, level=0) -> int:
+        """Nodes of one problem's level-`level` vector."""
         return int(self._lib.hh_level_nodes(self._p, level))
 
+    def size(self, level=0) -> int:
+        """Entries of a batch vector of level `level` (nb x nodes)."""
+        return self.nb * self.nodes(level)
+
     def zeros(self, level=0, dtype=torch.complex128):
-        return torch.zeros(self.nodes(level), dtype=dtype, device="cuda")
+        return torch.zeros(self.size(level), dtype=dtype, device="cuda")
+
+    def _info(self, infos):
+        return infos[0] if not self.batched else list(infos)
 
     # -- solver ------------------------------------------------------------
     def solve(self, rhs, tol=1e-8, x0=None, u=None):
         u = torch.empty_like(rhs) if u is None else u
-        info = Info()
-        st = self._lib.hh_solve(self._p, _ptr(rhs), float(tol), _ptr(u), _ptr(x0), ctypes.byref(info))
+        infos = (Info * self.nb)()
+        n0 = self.size(0)
+        st = self._lib.hh_solve(self._p, _ptr(rhs, n0), float(tol), _ptr(u, n0), _ptr(x0, n0), infos)
         _check(st, allow_not_converged=True)
-        return u, info
+        return u, self._info(infos)
 
     def solve_host(self, rhs: np.ndarray, tol=1e-8, out: np.ndarray | None = None):
         rhs = np.ascontiguousarray(rhs, dtype=np.complex128)
         out = np.empty_like(rhs) if out is None else out
-        info = Info()
+        if rhs.size != self.size(0) or out.size != rhs.size or out.dtype != np.complex128 \
+                or not out.flags.c_contiguous:
+            raise ValueError("host vectors must be contiguous complex128 of nb x nodes entries")
+        infos = (Info * self.nb)()
         st = self._lib.hh_solve_host(self._p, rhs.ctypes.data_as(ctypes.c_void_p), float(tol),
-                                     out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info))
+                                     out.ctypes.data_as(ctypes.c_void_p), infos)
         _check(st, allow_not_converged=True)
-        return out, info
+        return out, self._info(infos)
 
     # -- building blocks ------------------------------------------------------
     def apply(self, level, op, x, y=None):
         y = torch.empty_like(x) if y is None else y
-        _check(self._lib.hh_apply(self._p, level, OP[op], _prec_of(x), _ptr(x), _ptr(y)))
+        nl = self.size(level)
+        _check(self._lib.hh_apply(self._p, level, OP[op], _prec_of(x), _ptr(x, nl), _ptr(y, nl)))
         return y
 
     def jacobi(self, level, b, x_in=None, x_out=None):
         x_out = torch.empty_like(b) if x_out is None else x_out
-        _check(self._lib.hh_jacobi(self._p, level, _prec_of(b), _ptr(b), _ptr(x_in), _ptr(x_out)))
+        nl = self.size(level)
+        _check(self._lib.hh_jacobi(self._p, level, _prec_of(b), _ptr(b, nl), _ptr(x_in, nl), _ptr(x_out, nl)))
         return x_out
 
     def residual_restrict(self, level, b, x, rc=None):
-        rc = torch.empty(self.nodes(level + 1), dtype=b.dtype, device=b.device) if rc is None else rc
-        _check(self._lib.hh_residual_restrict(self._p, level, _prec_of(b), _ptr(b), _ptr(x), _ptr(rc)))
+        rc = torch.empty(self.size(level + 1), dtype=b.dtype, device=b.device) if rc is None else rc
+        nl, nc = self.size(level), self.size(level + 1)
+        _check(self._lib.hh_residual_restrict(self._p, level, _prec_of(b), _ptr(b, nl), _ptr(x, nl), _ptr(rc, nc)))
         return rc
 
     def prolong_correct(self, level, ec, x):
-        _check(self._lib.hh_prolong_correct(self._p, level, _prec_of(x), _ptr(ec), _ptr(x)))
+        nl, nc = self.size(level), self.size(level + 1)
+        _check(self._lib.hh_prolong_correct(self._p, level, _prec_of(x), _ptr(ec, nc), _ptr(x, nl)))
         return x
 
     def vcycle(self, b, x=None):
         x = torch.empty_like(b) if x is None else x
-        _check(self._lib.hh_vcycle(self._p, _prec_of(b), _ptr(b), _ptr(x)))
+        n0 = self.size(0)
+        _check(self._lib.hh_vcycle(self._p, _prec_of(b), _ptr(b, n0), _ptr(x, n0)))
         return x
 
     def hss_rhs(self, u, r, rhs=None):
         rhs = torch.empty_like(r) if rhs is None else rhs
-        _check(self._lib.hh_hss_rhs(self._p, _prec_of(r), _ptr(u), _ptr(r), _ptr(rhs)))
+        n0 = self.size(0)
+        _check(self._lib.hh_hss_rhs(self._p, _prec_of(r), _ptr(u, n0), _ptr(r, n0), _ptr(rhs, n0)))
         return rhs
 
     def precondition(self, r, z=None):
         z = torch.empty_like(r) if z is None else z
-        _check(self._lib.hh_precondition(self._p, _ptr(r), _ptr(z)))
+        n0 = self.size(0)
+        _check(self._lib.hh_precondition(self._p, _ptr(r, n0), _ptr(z, n0)))
         return z
 
     def load_vector(self, f, b=None):
         b = torch.empty_like(f) if b is None else b
-        _check(self._lib.hh_load_vector(self._p, _ptr(f), _ptr(b)))
+        n0 = self.size(0)
+        _check(self._lib.hh_load_vector(self._p, _ptr(f, n0), _ptr(b, n0)))
         return b
 
-    def dot(self, x, y) -> complex:
-        out = (ctypes.c_double * 2)()
-        _check(self._lib.hh_dot(self._p, _ptr(x), _ptr(y), out))
-        return complex(out[0], out[1])
+    def dot(self, x, y):
+        """x_b^H y_b per problem: a complex (single problem) or a list (batch)."""
+        out = (ctypes.c_double * (2 * self.nb))()
+        n0 = self.size(0)
+        _check(self._lib.hh_dot(self._p, _ptr(x, n0), _ptr(y, n0), out))
+        vals = [complex(out[2 * b], out[2 * b + 1]) for b in range(self.nb)]
+        return vals if self.batched else vals[0]

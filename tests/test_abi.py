@@ -61,6 +61,39 @@ def test_invalid_arguments_rejected_on_host(libhh, dim, n, k, delta, dh, bc):
     assert libhh.hh_last_error()
 
 
+def test_footprint_is_linear_in_batch(libhh):
+    for dim, n in ((2, 256), (3, 32)):
+        for prec in (hh.HH_C64, hh.HH_C128):
+            o = hh.default_options(precision=prec)
+            one = hh.footprint_bytes(dim, n, o)
+            assert one > 0 and hh.footprint_bytes(dim, n, o, nb=64) == 64 * one
+    assert hh.footprint_bytes(2, 256, hh.default_options(), nb=0) == 0
+    assert hh.footprint_bytes(3, 128, hh.default_options(), nb=600) == 0  # 129 * 600 > 65535
+
+
+def _create_batch(libhh, dim, n, ks, ds, dhs, nb=None):
+    o = hh.default_options()
+    arr = (ctypes.c_int * 6)(*([0] * 6))
+    D = ctypes.c_double * max(1, len(ks))
+    out = ctypes.c_void_p(1234)
+    st = libhh.hh_create_batch(ctypes.byref(hh.Grid(dim, n)), len(ks) if nb is None else nb, D(*ks), D(*ds), D(*dhs),
+                               arr, ctypes.byref(o), None, ctypes.byref(out))
+    return st, out
+
+
+@pytest.mark.parametrize("dim,n,ks,ds,dhs,nb", [
+    (2, 16, [10.0], [0.0], [2.0], 0),                       # empty batch
+    (2, 16, [10.0, -3.0], [0.0, 0.0], [2.0, 2.0], None),    # one bad k
+    (2, 16, [10.0, 5.0], [0.0, 0.0], [2.0, 0.0], None),     # one bad delta_hat
+    (2, 16, [10.0, float("nan")], [0.0, 0.0], [2.0, 2.0], None),
+    (3, 1024, [10.0] * 64, [0.0] * 64, [2.0] * 64, None),    # 1025 * 64 > 65535 launch planes
+])
+def test_invalid_batches_rejected_on_host(libhh, dim, n, ks, ds, dhs, nb):
+    st, out = _create_batch(libhh, dim, n, ks, ds, dhs, nb)
+    assert st == -1 and not out.value
+    assert libhh.hh_last_error()
+
+
 def test_status_strings(libhh):
     for s in (0, 1, -1, -2, -3, -4, -5):
         assert libhh.hh_status_string(s)
