@@ -110,6 +110,7 @@ typedef struct {
                               /* the level in distributed shared memory; 0 = never           */
     int tile_rows;       /* rows (2D) / z-planes (3D) per warp tile of the stencil kernels:   */
                          /* 2, 4 or 8; 0 = chosen from the grid size                          */
+    int autotune;        /* 1: run hh_autotune for `precision` when the problem is created    */
 } hh_options;
 
 typedef struct {
@@ -126,7 +127,7 @@ typedef struct hh_problem hh_problem;
 
 /* Defaults: theta 1, 4 levels, V(2,2), 8 coarse sweeps, omega automatic, restart 30,
  * max_outer 1000, complex FP32 V-cycles, graphs and programmatic launch on,
- * coarse_cluster_nodes 100000. */
+ * coarse_cluster_nodes 100000, tile shapes from the grid size (no autotuning). */
 HH_API void hh_options_default(hh_options* opts);
 
 /* Device bytes a problem with this grid and these options allocates for its solves
@@ -163,6 +164,21 @@ HH_API hh_status hh_create_batch(const hh_grid* grid, int nb, const double* k, c
 
 /* Problems in the batch (0 for NULL). */
 HH_API int hh_batch_size(const hh_problem* p);
+
+/*
+ * Tile-shape autotuner (a service of this library; the paper has none).  Times every
+ * candidate tile shape (rows or planes per warp tile, one tile per warp or persistent
+ * warps) of each stencil kernel the solver runs on each level in `precision`, and of the
+ * FP64 outer operator, on the problem's own scratch buffers, and keeps the fastest for
+ * this problem; later solves use them (the preconditioner graph is captured again).
+ * Every shape gives the same result bit for bit.  Choices are remembered per process for
+ * (device, dim, level size, batch size, precision, kernel), so problems of the same shape
+ * reuse them without timing.  Blocking.  shapes, if not NULL, receives levels x 7 x 2 ints:
+ * for level l and kernel mode m (y = op x, axpby, Jacobi, HSS first step, two Jacobi
+ * sweeps from 0, prolongation + Jacobi, residual + restriction), {rows, form} at
+ * [(l * 7 + m) * 2], 0 where nothing was tuned.
+ */
+HH_API hh_status hh_autotune(hh_problem* p, int precision, int* shapes);
 
 HH_API void hh_destroy(hh_problem* p);
 

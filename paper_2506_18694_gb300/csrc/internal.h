@@ -133,6 +133,7 @@ template <typename T> struct MArgs {
     T omega;
     int xzero;           // 1: x is identically zero
     int tile_rows;       // 0: automatic; else 2, 4 or 8 rows (2D) / planes (3D) per tile
+    int tile_form;       // 2D: 0 automatic, 1 one tile per warp, 2 persistent warps walking the tiles
     int hss_it;          // >= 0: problem b is skipped when hss_it >= nhss[b]
     const int* nhss;     // device: HSS iterations of each problem
     const int* active;   // device: 0 = problem skipped (nullptr: all active)

@@ -7,6 +7,8 @@
 // side mass) are the same as in stencil.cu; the modes below fuse the V-cycle's vector
 // updates into the stencil pass so that each fine-level sweep reads and writes each
 // vector once.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace hh {
@@ -348,7 +350,6 @@ static cudaError_t run2b(const MArgs<T>& a, int strips, int chunks, cudaStream_t
     const long long tiles = (long long)strips * chunks * a.nb;
     // residual-restriction and prolongation tiles carry more rows; they run one tile per warp
     if constexpr (MODE != M_PROLONG_JACOBI && MODE != M_RESID_RESTRICT) {
-        // persistent once there are several tiles per resident warp: exactly the resident blocks
         static int per_sm = 0;
         if (!per_sm) {
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march2p<T, MODE, ROWS, BATCH>, 128, 0) !=
@@ -359,9 +360,13 @@ static cudaError_t run2b(const MArgs<T>& a, int strips, int chunks, cudaStream_t
             }
         }
         const long long resident_blocks = 152LL * per_sm;
-        if (tiles >= 16 * resident_blocks && tiles < (1LL << 31))
-            return klaunch(k_march2p<T, MODE, ROWS, BATCH>, dim3((unsigned)resident_blocks), dim3(128), 0, s, 1, a,
-                           strips, strips * chunks, (int)tiles);
+        // automatic: persistent once there are several tiles per resident warp
+        const bool persist = a.tile_form == 2 || (a.tile_form == 0 && tiles >= 16 * resident_blocks);
+        if (persist && tiles < (1LL << 31)) {
+            const long long blocks = std::min(resident_blocks, (tiles + 3) / 4);
+            return klaunch(k_march2p<T, MODE, ROWS, BATCH>, dim3((unsigned)blocks), dim3(128), 0, s, 1, a, strips,
+                           strips * chunks, (int)tiles);
+        }
     }
     dim3 grd((unsigned)strips, (unsigned)((chunks + 3) / 4), (unsigned)a.nb);
     return klaunch(k_march2<T, MODE, ROWS, BATCH>, grd, dim3(128), 0, s, 1, a, chunks);

@@ -9,6 +9,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -84,6 +88,8 @@ int n_hss(double k, double theta) {
     return (int)std::ceil(v);
 }
 
+constexpr int kModes = 7;  // hh::MarchMode values
+
 // Operators with a coefficient table (per problem and level).
 enum Role { R_K = 0, R_M, R_MG, R_AL, R_AR, R_B, R_BHAT, R_COUNT };
 
@@ -140,6 +146,8 @@ struct hh_problem {
     double2* h_host = nullptr;  // pinned mirror of hbuf (and of ybuf)
     size_t bytes = 0;
     std::vector<void*> allocs;
+    // tile shapes of the stencil kernels per precision, level and mode: {rows, form}, 0 = automatic
+    std::vector<std::array<std::array<int, 2>, kModes>> tune[2];
 };
 
 namespace {
@@ -355,8 +363,18 @@ struct MG {
                          active_flags(p)};
     }
 
+    // the tuned tile shape of (level of a.g, mode), if any
     cudaError_t march(int mode, const hh::MArgs<T>& a) const {
-        return d2() ? hh::launch_march2<T>(mode, a, s) : hh::launch_march3<T>(mode, a, s);
+        hh::MArgs<T> t = a;
+        const int prec = sizeof(T) == 4 ? HH_C64 : HH_C128;
+        const auto& tab = p->tune[prec];
+        int l = 0;
+        while ((p->grid.n >> l) != a.g.n) ++l;
+        if (l < (int)tab.size() && tab[l][mode][0] != 0) {
+            t.tile_rows = tab[l][mode][0];
+            t.tile_form = tab[l][mode][1];
+        }
+        return d2() ? hh::launch_march2<T>(mode, t, s) : hh::launch_march3<T>(mode, t, s);
     }
 
     // ---- level kernels ----
@@ -385,7 +403,7 @@ struct MG {
         a.z = b;
         if (d2()) {
             a.y = rc;
-            HH_LAUNCH(hh::launch_march2<T>(hh::M_RESID_RESTRICT, a, s));
+            HH_LAUNCH(march(hh::M_RESID_RESTRICT, a));
         } else {
             a.y = (V2*)H->t[l];
             a.alpha = Cx<T>{-1, 0};
@@ -666,6 +684,137 @@ hh_status residual_B(hh_problem* p, const double2* x, double2* r) {
     return op_axpby<double>(p, 0, R_B, x, p->bvec, r, Cx<double>{-1, 0}, Cx<double>{1, 0}, p->s);
 }
 
+// ------------------------------------------------------------------ autotuner
+// Every tile shape gives the same result bit for bit (each node's arithmetic does not depend
+// on the tiling); only the time differs.  Measured choices are kept per process, keyed by
+// (device, dim, level grid n, batch size, precision, mode), so that problems of the same shape
+// reuse them.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int>, std::array<int, 2>> g_tune_cache;
+
+// Candidate {rows, form} of a stencil kernel (form: 1 one tile per warp, 2 persistent).
+std::vector<std::array<int, 2>> tile_candidates(int dim, int prec, int mode) {
+    std::vector<std::array<int, 2>> c;
+    if (dim == 2) {
+        std::vector<int> rows = {2, 4};
+        if (prec == HH_C64 && mode != hh::M_RESID_RESTRICT) rows.push_back(8);
+        const bool persist_ok = mode != hh::M_PROLONG_JACOBI && mode != hh::M_RESID_RESTRICT;
+        for (int r : rows) {
+            c.push_back({r, 1});
+            if (persist_ok) c.push_back({r, 2});
+        }
+    } else if (prec == HH_C64) {
+        c = {{2, 0}, {4, 0}, {8, 0}};
+    }
+    return c;
+}
+
+// Average device time of one launch of `mode` on level l with tile shape cand (scratch buffers).
+template <typename T>
+hh_status time_shape(hh_problem* p, int l, int mode, const std::array<int, 2>& cand, float* ms) {
+    using V2 = hh::vec2<T>;
+    const int prec = sizeof(T) == 4 ? HH_C64 : HH_C128;
+    MG<T> m = make_mg<T>(p, prec, p->s);
+    const bool fgm = prec == HH_C128 && l == 0 && (mode == hh::M_APPLY || mode == hh::M_AXPBY) &&
+                     !p->hier[HH_C128].ready;
+    const int role = mode == hh::M_HSS_FIRST ? R_AR : (mode == hh::M_APPLY ? R_B : R_AL);
+    hh::MArgs<T> a = m.margs(l, role);
+    if (fgm) {
+        // the FP64 outer operator: Krylov buffers stand in for the hierarchy
+        a.x = (const V2*)p->V;
+        a.z = (const V2*)p->r;
+        a.y = (V2*)(p->V + (long long)p->nb * p->N);
+    } else {
+        Hier& H = p->hier[prec];
+        a.x = (const V2*)H.xa[l];
+        a.z = (const V2*)H.b[l];
+        a.y = (V2*)H.xb[l];
+        a.y2 = (V2*)H.t[l];
+        if (l + 1 < p->o.levels) a.ec = (const V2*)H.xa[l + 1];
+        if (mode == hh::M_RESID_RESTRICT) a.y = (V2*)H.t[l + 1];
+    }
+    a.use_pc_ab = mode == hh::M_HSS_FIRST;
+    a.alpha = Cx<T>{-1, 0};
+    a.beta = Cx<T>{1, 0};
+    a.tile_rows = cand[0];
+    a.tile_form = cand[1];
+    auto launch = [&]() { return m.d2() ? hh::launch_march2<T>(mode, a, p->s) : hh::launch_march3<T>(mode, a, p->s); };
+    cudaEvent_t e0, e1;
+    HH_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(HH_ERR_CUDA, "event creation failed");
+    }
+    cudaError_t err = cudaSuccess;
+    for (int i = 0; i < 2 && err == cudaSuccess; ++i) err = launch();
+    const int reps = 5;
+    if (err == cudaSuccess) err = cudaEventRecord(e0, p->s);
+    for (int i = 0; i < reps && err == cudaSuccess; ++i) err = launch();
+    if (err == cudaSuccess) err = cudaEventRecord(e1, p->s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    HH_CUDA(err);
+    *ms = t / reps;
+    return HH_OK;
+}
+
+// Pick the fastest tile shape of every (level, mode) the solver runs in precision prec, and of
+// the FP64 outer operator on level 0.
+hh_status autotune(hh_problem* p, int prec) {
+    HH_TRY(ensure_hier(p, prec));
+    const int L = p->o.levels;
+    for (int q = 0; q < 2; ++q)
+        if (p->tune[q].empty()) p->tune[q].assign(L, {});
+    std::vector<std::tuple<int, int, int>> work;  // (precision, level, mode)
+    for (int l = 0; l < L; ++l)
+        for (int mode = 0; mode < kModes; ++mode) {
+            if ((mode == hh::M_PROLONG_JACOBI || mode == hh::M_RESID_RESTRICT) && l == L - 1) continue;
+            if (mode == hh::M_RESID_RESTRICT && p->grid.dim == 3) continue;
+            if (mode == hh::M_HSS_FIRST && l != 0) continue;
+            work.emplace_back(prec, l, mode);
+        }
+    if (prec == HH_C64) {
+        work.emplace_back(HH_C128, 0, (int)hh::M_APPLY);
+        work.emplace_back(HH_C128, 0, (int)hh::M_AXPBY);
+    }
+    const int nb = p->nb;
+    for (auto& [q, l, mode] : work) {
+        const auto key = std::make_tuple(p->device, p->grid.dim, p->lv[l].n, nb, q, mode);
+        std::array<int, 2> best{0, 0};
+        {
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) best = it->second;
+        }
+        if (best[0] == 0) {
+            const auto cands = tile_candidates(p->grid.dim, q, mode);
+            if (cands.size() < 2) continue;
+            float tbest = 0.f;
+            for (const auto& c : cands) {
+                float ms = 0.f;
+                HH_TRY(q == HH_C64 ? time_shape<float>(p, l, mode, c, &ms) : time_shape<double>(p, l, mode, c, &ms));
+                if (best[0] == 0 || ms < tbest) {
+                    best = c;
+                    tbest = ms;
+                }
+            }
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            g_tune_cache[key] = best;
+        }
+        p->tune[q][l][mode] = best;
+    }
+    // captured preconditioner graphs hold the old shapes
+    for (int q = 0; q < 2; ++q)
+        if (p->hier[q].graph) {
+            cudaGraphExecDestroy(p->hier[q].graph);
+            p->hier[q].graph = nullptr;
+        }
+    return HH_OK;
+}
+
 int hstride(const hh_problem* p) { return 2 * (p->o.restart + 1) + 1; }
 
 // ||v_b||^2 into hbuf[b][slot] (device) for every active problem (v_b = v + b N)
@@ -873,6 +1022,7 @@ hh_status check_args(const hh_grid* grid, int nb, const double* k, const double*
     if (o->coarse_cluster_nodes < 0) return fail(HH_ERR_INVALID, "coarse_cluster_nodes < 0");
     if (o->tile_rows != 0 && o->tile_rows != 2 && o->tile_rows != 4 && o->tile_rows != 8)
         return fail(HH_ERR_INVALID, "tile_rows must be 0, 2, 4 or 8");
+    if (o->autotune != 0 && o->autotune != 1) return fail(HH_ERR_INVALID, "autotune must be 0 or 1");
     if (!bc) return fail(HH_ERR_INVALID, "null bc");
     for (int s = 0; s < 2 * grid->dim; ++s)
         if (bc[s] != HH_BC_SOMMERFELD && bc[s] != HH_BC_DIRICHLET) return fail(HH_ERR_INVALID, "bad boundary tag");
@@ -922,6 +1072,7 @@ void hh_options_default(hh_options* o) {
     o->use_pdl = 1;
     o->coarse_cluster_nodes = 100000;
     o->tile_rows = 0;
+    o->autotune = 0;
 }
 
 size_t hh_footprint_batch_bytes(const hh_grid* grid, const hh_options* o, int nb) {
@@ -1008,8 +1159,10 @@ hh_status hh_create_batch(const hh_grid* grid, int nb, const double* k, const do
     if ((st = ensure_hier(p, opts->precision)) != HH_OK) return bail(st);
     if (cudaMemsetAsync(p->V, 0, (size_t)(m + 1) * nb * N * 16, p->s) != cudaSuccess ||
         cudaMemsetAsync(p->Z, 0, (size_t)m * nb * N * 16, p->s) != cudaSuccess ||
+        cudaMemsetAsync(p->r, 0, (size_t)nb * N * 16, p->s) != cudaSuccess ||
         cudaStreamSynchronize(p->s) != cudaSuccess)
         return bail(fail(HH_ERR_CUDA, "initialisation failed"));
+    if (opts->autotune && (st = autotune(p, opts->precision)) != HH_OK) return bail(st);
     *out = p;
     return HH_OK;
 }
@@ -1020,6 +1173,20 @@ hh_status hh_create_problem(const hh_grid* grid, double k, double delta, double 
 }
 
 int hh_batch_size(const hh_problem* p) { return p ? p->nb : 0; }
+
+hh_status hh_autotune(hh_problem* p, int precision, int* shapes) {
+    if (!p) return fail(HH_ERR_INVALID, "null problem");
+    HH_TRY(validate_prec(precision));
+    HH_TRY(join_in(p));
+    HH_TRY(autotune(p, precision));
+    HH_TRY(join_out(p));
+    if (shapes) {
+        for (int l = 0; l < p->o.levels; ++l)
+            for (int mode = 0; mode < kModes; ++mode)
+                for (int c = 0; c < 2; ++c) shapes[((size_t)l * kModes + mode) * 2 + c] = p->tune[precision][l][mode][c];
+    }
+    return HH_OK;
+}
 
 long long hh_level_nodes(const hh_problem* p, int level) {
     if (!p || level < 0 || level >= p->o.levels) return 0;

@@ -23,7 +23,7 @@ OP = {"K": 0, "M": 1, "MGAMMA": 2, "AL": 3, "AR": 4, "B": 5, "BHAT": 6}
 
 EXPORTED = (
     "hh_options_default", "hh_footprint_bytes", "hh_footprint_batch_bytes", "hh_create_problem",
-    "hh_create_batch", "hh_batch_size", "hh_destroy", "hh_solve",
+    "hh_create_batch", "hh_batch_size", "hh_autotune", "hh_destroy", "hh_solve",
     "hh_solve_host", "hh_level_nodes", "hh_apply", "hh_jacobi", "hh_residual_restrict",
     "hh_prolong_correct", "hh_vcycle", "hh_hss_rhs", "hh_precondition", "hh_load_vector", "hh_dot",
     "hh_multidot_noalloc", "hh_status_string", "hh_last_error",
@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
         ("nu_post", ctypes.c_int), ("nu_coarse", ctypes.c_int), ("cycles_per_hss", ctypes.c_int),
         ("omega", ctypes.c_double), ("restart", ctypes.c_int), ("max_outer", ctypes.c_int),
         ("precision", ctypes.c_int), ("use_graphs", ctypes.c_int), ("use_pdl", ctypes.c_int),
-        ("coarse_cluster_nodes", ctypes.c_int), ("tile_rows", ctypes.c_int),
+        ("coarse_cluster_nodes", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
     ]
 
 
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "hh_create_batch": (I, [ctypes.POINTER(Grid), I, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Options), P, ctypes.POINTER(P)]),
         "hh_batch_size": (I, [P]),
+        "hh_autotune": (I, [P, I, ctypes.POINTER(ctypes.c_int)]),
         "hh_destroy": (V, [P]),
         "hh_solve": (I, [P, P, D, P, P, ctypes.POINTER(Info)]),
         "hh_solve_host": (I, [P, P, D, P, ctypes.POINTER(Info)]),
@@ -200,6 +201,18 @@ class Problem:
 
     def __exit__(self, *a):
         self.close()
+
+    MODES = ("apply", "axpby", "jacobi", "hss_first", "jacobi2_zero", "prolong_jacobi", "resid_restrict")
+
+    def autotune(self, precision=None):
+        """Time the tile shapes of every stencil kernel and keep the fastest; returns
+        {(level, mode): (rows, form)} for the tuned kernels."""
+        prec = self.options.precision if precision is None else precision
+        L = self.options.levels
+        out = (ctypes.c_int * (L * 7 * 2))()
+        _check(self._lib.hh_autotune(self._p, prec, out))
+        return {(l, m): (out[(l * 7 + i) * 2], out[(l * 7 + i) * 2 + 1])
+                for l in range(L) for i, m in enumerate(self.MODES) if out[(l * 7 + i) * 2]}
 
     def nodes(self, level=0) -> int:
         """Nodes of one problem's level-`level` vector."""

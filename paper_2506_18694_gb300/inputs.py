@@ -89,3 +89,45 @@ def batch_sources(count: int = 64, n: int = 256, seed: int = 4):
     centres = rng.uniform(0.0, 1.0, size=(count, 2))
     amps = rng.standard_normal(count) + 1j * rng.standard_normal(count)
     return [(float(ks[i]), tuple(centres[i]), complex(amps[i])) for i in range(count)]
+
+
+@dataclass(frozen=True)
+class BatchWorkload:
+    """A batch of 2D problems on one grid: per-problem k, source centre and amplitude."""
+
+    name: str
+    dim: int
+    n: int
+    ks: tuple
+    centres: tuple
+    amplitudes: tuple
+    delta: float
+    delta_hats: tuple
+    bc: tuple
+    sigma: float = 0.05
+    tol: float = 1e-8
+
+    @property
+    def count(self) -> int:
+        return len(self.ks)
+
+    @property
+    def nodes(self) -> int:
+        return (self.n + 1) ** self.dim
+
+    def sources(self) -> np.ndarray:
+        """(count, nodes) nodal source values, problem after problem."""
+        return np.stack([gaussian_source(self.dim, self.n, c, self.sigma, a)
+                         for c, a in zip(self.centres, self.amplitudes)])
+
+
+def batch_workload(name: str = "2d_batch64_n256", delta_hat: str | float = "k") -> BatchWorkload:
+    """64 right sides on the 2D 256^2 grid (Sommerfeld on all sides), k drawn from {20, 40, 80}
+    with seed 4, uniform centres, complex normal amplitudes; delta_hat = k or a number."""
+    if name != "2d_batch64_n256":
+        raise KeyError(name)
+    src = batch_sources(64, 256, 4)
+    ks = tuple(s[0] for s in src)
+    dhs = ks if delta_hat == "k" else tuple(float(delta_hat) for _ in ks)
+    return BatchWorkload(name, 2, 256, ks, tuple(s[1] for s in src), tuple(s[2] for s in src), 0.0, dhs,
+                         (SOMMERFELD,) * 4)
