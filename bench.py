@@ -416,6 +416,12 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
     out["delta_hat_2"] = {"cycles_per_hss": 2, "solve_ms": 1e3 * t2, "outer_its": i2.outer_its, "vcycles": i2.vcycles,
                           "rel_residual": i2.rel_residual, "value": prob.nodes() * i2.vcycles / t2}
 
+    # batched: 64 right sides on 2D 256^2, k from {20, 40, 80}, one problem object
+    try:
+        out["batch64"] = measure_batch(hh, inputs, torch)
+    except Exception as e:  # report, do not hide the other numbers
+        out["batch64"] = {"failed": str(e)}
+
     # FP64 CPU oracle on a bounded sample of the same workload
     try:
         v, cycles, dt = oracle_vcycle_rate(w)
@@ -425,6 +431,66 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
     except Exception as e:  # the CPU leg must not hide the GPU numbers
         out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle", "sample": f"failed: {e}"}
     return out
+
+
+def measure_batch(hh, inputs, torch):
+    """The 64-problem batch solved at once (complex64 V-cycles, autotuned tile shapes) against
+    solving the problems one after another, in mixed precision and in FP64.  The sequential
+    times are estimated from one solo solve per k class (that problem's own right side),
+    multiplied by the class size."""
+    w = inputs.batch_workload()
+    N = w.nodes
+    f = torch.from_numpy(w.sources().reshape(-1)).cuda()
+    ks = np.array(w.ks)
+    opts = hh.default_options(precision=hh.HH_C64, autotune=1)
+    t0 = time.perf_counter()
+    pb = hh.Problem(2, w.n, ks, w.delta, np.array(w.delta_hats), w.bc, opts)
+    create_s = time.perf_counter() - t0
+    b = pb.load_vector(f)
+    u = torch.empty_like(b)
+    pb.solve(b, w.tol, u=u)  # graph capture
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    _, infos = pb.solve(b, w.tol, u=u)
+    e1.record(s)
+    e1.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    shapes = pb.autotune()
+    pb.close()
+    its = [i.outer_its for i in infos]
+    vcycles = sum(i.vcycles for i in infos)
+    solo = {}
+    for kk in sorted(set(w.ks)):
+        i = list(w.ks).index(kk)
+        bi = b[i * N:(i + 1) * N].clone()
+        for name, prec in (("mixed", hh.HH_C64), ("fp64", hh.HH_C128)):
+            with hh.Problem(2, w.n, kk, w.delta, w.delta_hats[i], w.bc, hh.default_options(precision=prec)) as p:
+                p.solve(bi, w.tol)
+                torch.cuda.synchronize()
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                _, info = p.solve(bi, w.tol)
+                z.record(s)
+                z.synchronize()
+                solo[(kk, name)] = (a.elapsed_time(z) / 1e3, info.outer_its, info.rel_residual)
+    count = {kk: list(w.ks).count(kk) for kk in set(w.ks)}
+    seq = {name: sum(count[kk] * solo[(kk, name)][0] for kk in count) for name in ("mixed", "fp64")}
+    return {
+        "workload": w.name, "problems": w.count, "grid": "2D 256^2 Q1 cells (257^2 nodes) each, Sommerfeld",
+        "k_counts": {str(k): c for k, c in sorted(count.items())}, "delta_hat": "k", "tol": w.tol,
+        "solve_s": t_batch, "solves_per_s": w.count / t_batch, "value": N * vcycles / t_batch, "unit": UNIT,
+        "outer_its": {"min": min(its), "max": max(its)},
+        "max_rel_residual": max(i.rel_residual for i in infos),
+        "create_s_with_autotune": create_s, "tuned_kernels": len(shapes),
+        "solo": {f"k{int(kk)}_{name}": {"solve_s": v[0], "outer_its": v[1], "rel_residual": v[2]}
+                 for (kk, name), v in sorted(solo.items())},
+        "sequential_estimate_s": seq,
+        "speedup_vs_sequential_mixed": seq["mixed"] / t_batch,
+        "speedup_vs_sequential_fp64": seq["fp64"] / t_batch,
+        "note": "sequential times = class size x one solo solve per k class",
+    }
 
 
 if __name__ == "__main__":

@@ -37,7 +37,8 @@ static SlabPlan slab_plan(const GridDesc& g, int cs) {
 // One cluster per problem of the batch: problem = blockIdx.x / cluster size.  Coefficients
 // from the table entry of A_L on this level (interior weights and omega D^{-1} included).
 template <typename T>
-__global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem(MArgs<T> a, int nsweeps, int per) {
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem(const __grid_constant__ MArgs<T> a, int nsweeps,
+                                                                 int per) {
     pdl_entry();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cl = cg::this_cluster();
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem(MArgs<T> a, int
     const int prob = blockIdx.x / (int)cl.num_blocks();
     if (problem_skipped(a, prob)) return;  // uniform over the cluster: no barrier is left waiting
     const GridDesc& g = a.g;
-    const PCoef<T> pcf = coef_of(a, prob);
+    const PCoef<T>& pcf = coef_of(a, prob);
     const OpCoef<T> op = pcf.op;
     const vec2<T>* __restrict__ b = a.z + (long long)prob * a.bs;
     vec2<T>* __restrict__ xout = a.y + (long long)prob * a.bs;
@@ -207,9 +208,24 @@ cudaError_t prepare_coarse() {
     return cudaSuccess;
 }
 
+// Cluster size for nb problems: the largest (fastest for one problem) unless the batch's
+// clusters would not all be resident at once; then halve it while the slabs still fit.
+// Every size gives the same sweeps bit for bit (the slab cut only moves work between CTAs).
+template <typename T>
+static int batch_cluster_size(const GridDesc& g, int nb) {
+    int cs = coarse_cluster_size();
+    while (cs > 1 && (long long)nb * cs > 2LL * 152) {
+        const SlabPlan sp = slab_plan<T>(g, cs / 2);
+        if (sp.smem > kCoarseSmemMax || (long long)sp.per * sp.S > (long long)kCoarseNodesPerThread * kCoarseThreads)
+            break;
+        cs /= 2;
+    }
+    return cs;
+}
+
 template <typename T>
 cudaError_t launch_coarse_solve(const MArgs<T>& a, int nsweeps, cudaStream_t s) {
-    const int cs = coarse_cluster_size();
+    const int cs = batch_cluster_size<T>(a.g, a.nb);
     const SlabPlan sp = slab_plan<T>(a.g, cs);
     if (sp.smem > kCoarseSmemMax || nsweeps < 1) return cudaErrorInvalidValue;
     if ((long long)sp.per * sp.S > (long long)kCoarseNodesPerThread * kCoarseThreads) return cudaErrorInvalidValue;

@@ -108,9 +108,14 @@ template <typename T> struct PCoef {
     Cx<T> iw[4];
     Cx<T> wdinv;
     Cx<T> alpha, beta;
+    // 2D nodes on a side of the square, by class (y type * 3 + x type, the interior class
+    // 4 left out; type 0: first node of the axis, 1: inner, 2: last): weights of the centre,
+    // the x-neighbours, the y-neighbours and the diagonal neighbours, and omega / diag(opd)
+    Cx<T> bw[8][4];
+    Cx<T> bdinv[8];
 };
 
-// Host: fill the interior weights and wdinv of c for grid g and damping omega.
+// Host: fill the interior and boundary-class weights of c for grid g and damping omega.
 template <typename T>
 void interior_weights(PCoef<T>& c, const GridDesc& g, double omega);
 
@@ -163,9 +168,10 @@ __device__ __forceinline__ VPtrs<T> problem_ptrs(const MArgs<T>& a, int b, bool 
     return v;
 }
 
-// Coefficients of problem b.
+// Coefficients of problem b (a reference into the table or into the kernel parameters:
+// kernels taking it declare their MArgs __grid_constant__).
 template <typename T>
-__device__ __forceinline__ PCoef<T> coef_of(const MArgs<T>& a, int b) {
+__device__ __forceinline__ const PCoef<T>& coef_of(const MArgs<T>& a, int b) {
     return a.pc ? a.pc[b] : a.c0;
 }
 

@@ -22,66 +22,49 @@ __device__ __forceinline__ Cx<T> shfl_dn(Cx<T> v) {
     return Cx<T>{__shfl_down_sync(0xffffffffu, v.re, 1), __shfl_down_sync(0xffffffffu, v.im, 1)};
 }
 
-template <typename T>
-__device__ __forceinline__ Cx<T> diag2(const Row1<T>& rx, const Row1<T>& ry, const OpCoef<T>& op) {
-    const T dr = op.cK * (rx.kc * ry.mc + rx.mc * ry.kc);
-    const T dm = rx.mc * ry.mc;
-    const T dg = (rx.face ? ry.mc : T(0)) + (ry.face ? rx.mc : T(0));
-    return cx<T>(dr + op.cM.re * dm + op.cG.re * dg, op.cM.im * dm + op.cG.im * dg);
-}
-
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// Value of the stencil field at node (i, r) (both clamped into the grid).
-template <typename T, int MODE>
-__device__ __forceinline__ Cx<T> field2(const MArgs<T>& a, const PCoef<T>& c, const VPtrs<T>& v, int ic, int rc,
-                                        const Row1<T>& rx, T h, T ih, Cx<T>* bval) {
-    const long long p = (long long)rc * a.g.nn + ic;
-    if (MODE == M_JACOBI2_ZERO) {
-        // first sweep from x = 0: x1 = omega D^{-1} b (zero at Dirichlet nodes)
-        const Cx<T> b = ld<T>(v.z, p);
-        *bval = b;
-        if (ic >= 1 && ic <= a.g.n - 1 && rc >= 1 && rc <= a.g.n - 1) return cmul(c.wdinv, b);
-        const Row1<T> ry = row1<T>(rc, a.g.n, a.g.dir[2], a.g.dir[3], h, ih);
-        if (rx.masked || ry.masked) return cx<T>(0, 0);
-        return a.omega * cmul(cinv(diag2(rx, ry, c.op)), b);
-    } else if (MODE == M_PROLONG_JACOBI) {
-        // x + P e_c: bilinear interpolation of the coarse correction (coarse Dirichlet
-        // nodes carry no basis function and are skipped)
-        const Row1<T> ry = row1<T>(rc, a.g.n, a.g.dir[2], a.g.dir[3], h, ih);
-        if (rx.masked || ry.masked) return cx<T>(0, 0);
-        const int nc = a.g.n >> 1, nnc = nc + 1;
-        const int I0 = ic >> 1, J0 = rc >> 1;
-        const bool oi = ic & 1, oj = rc & 1;
-        Cx<T> e = cx<T>(0, 0);
+// Boundary-class index of a node with axis types tx, ty (0 first node, 1 inner, 2 last);
+// not called for the inner class.
+__device__ __forceinline__ int bclass2(int tx, int ty) {
+    const int c = ty * 3 + tx;
+    return c - (c > 4);
+}
+
+// x + P e_c at node (ic, rc) inside the grid and not on a Dirichlet side: bilinear
+// interpolation of the coarse correction (coarse Dirichlet nodes carry no basis function).
+template <typename T>
+__device__ __forceinline__ Cx<T> prolonged2(const MArgs<T>& a, const VPtrs<T>& v, int ic, int rc, long long p) {
+    const int nc = a.g.n >> 1, nnc = nc + 1;
+    const int I0 = ic >> 1, J0 = rc >> 1;
+    const bool oi = ic & 1, oj = rc & 1;
+    Cx<T> e = cx<T>(0, 0);
 #pragma unroll
-        for (int bj = 0; bj < 2; ++bj) {
-            if (bj == 1 && !oj) break;
-            const int J = J0 + bj;
-            if ((J == 0 && a.g.dir[2]) || (J == nc && a.g.dir[3])) continue;
-            const T wj = oj ? T(0.5) : T(1);
+    for (int bj = 0; bj < 2; ++bj) {
+        if (bj == 1 && !oj) break;
+        const int J = J0 + bj;
+        if ((J == 0 && a.g.dir[2]) || (J == nc && a.g.dir[3])) continue;
+        const T wj = oj ? T(0.5) : T(1);
 #pragma unroll
-            for (int ai = 0; ai < 2; ++ai) {
-                if (ai == 1 && !oi) break;
-                const int I = I0 + ai;
-                if ((I == 0 && a.g.dir[0]) || (I == nc && a.g.dir[1])) continue;
-                const T w = oi ? T(0.5) * wj : wj;
-                e = fma_r(w, ld<T>(v.ec, (long long)J * nnc + I), e);
-            }
+        for (int ai = 0; ai < 2; ++ai) {
+            if (ai == 1 && !oi) break;
+            const int I = I0 + ai;
+            if ((I == 0 && a.g.dir[0]) || (I == nc && a.g.dir[1])) continue;
+            const T w = oi ? T(0.5) * wj : wj;
+            e = fma_r(w, ld<T>(v.ec, (long long)J * nnc + I), e);
         }
-        return ld<T>(v.x, p) + e;
-    } else {
-        return a.xzero ? cx<T>(0, 0) : ld<T>(v.x, p);
     }
+    return ld<T>(v.x, p) + e;
 }
 
 // One warp tile: a strip of 30 output columns (lanes 1..30; lanes 0 and 31 are the halo)
 // and ROWS consecutive output rows (RESID_RESTRICT: ROWS coarse rows, 2 ROWS + 1 residual
 // rows, 28 fine columns per strip).  tile_load issues every load of the tile (all in
-// flight at once); tile_compute does the arithmetic and the stores.  Nodes at least two
-// cells away from the boundary (none of their neighbours is a boundary node) use the
-// interior weights of the operator (centre, edge, diagonal) and the interior diagonal; the
-// rest build their row from the 1D weight triples.
+// flight at once); tile_compute does the arithmetic and the stores.  The stencil field is
+// loaded as zero outside the grid and at Dirichlet nodes (their unknowns are eliminated),
+// so every node sums its existing neighbours by group: inner nodes with the interior
+// weights (centre, edge, diagonal), nodes on a side with the weights of their boundary
+// class (centre, x-neighbours, y-neighbours, diagonals).
 template <typename T, int MODE, int ROWS> struct Tile2 {
     static constexpr bool RR = MODE == M_RESID_RESTRICT;
     static constexpr int NR = RR ? 2 * ROWS + 3 : ROWS + 2;  // stencil rows
@@ -92,8 +75,18 @@ template <typename T, int MODE, int ROWS> struct Tile2 {
     Cx<T> zv[NZ];  // right side / second vector on the output rows
 };
 
+// Whether node (i, r) of the tile holds no unknown: outside the grid or on a Dirichlet side.
+template <typename T>
+__device__ __forceinline__ bool col_void(const MArgs<T>& a, int i) {
+    return i < 0 || i > a.g.n || (i == 0 && a.g.dir[0]) || (i == a.g.n && a.g.dir[1]);
+}
+template <typename T>
+__device__ __forceinline__ bool row_void(const MArgs<T>& a, int r) {
+    return r < 0 || r > a.g.n || (r == 0 && a.g.dir[2]) || (r == a.g.n && a.g.dir[3]);
+}
+
 template <typename T, int MODE, int ROWS>
-__device__ __forceinline__ void tile_load(const MArgs<T>& a, const PCoef<T>& c, const VPtrs<T>& v, int strip, int cy,
+__device__ __forceinline__ void tile_load(const MArgs<T>& a, const VPtrs<T>& v, int strip, int cy,
                                           Tile2<T, MODE, ROWS>& tl) {
     using TL = Tile2<T, MODE, ROWS>;
     const int lane = threadIdx.x & 31;
@@ -102,17 +95,19 @@ __device__ __forceinline__ void tile_load(const MArgs<T>& a, const PCoef<T>& c, 
     const int base = cy * ROWS;
     const int rfirst = TL::RR ? 2 * base - 2 : base - 1;
     const int ic = clampi(i, 0, n);
+    const bool cvoid = col_void(a, i);
 #pragma unroll
     for (int t = 0; t < TL::NR; ++t) {
-        const int rc = clampi(rfirst + t, 0, n);
+        const int r = rfirst + t;
+        const int rc = clampi(r, 0, n);
+        const long long p = (long long)rc * a.g.nn + ic;
+        const bool vd = cvoid || row_void(a, r);
         if (MODE == M_JACOBI2_ZERO) {
-            tl.bv[t] = ld<T>(v.z, (long long)rc * a.g.nn + ic);
+            tl.bv[t] = ld<T>(v.z, p);
         } else if (MODE == M_PROLONG_JACOBI) {
-            const Row1<T> rx = row1<T>(ic, n, a.g.dir[0], a.g.dir[1], a.h, a.ih);
-            Cx<T> dummy;
-            tl.fv[t] = field2<T, MODE>(a, c, v, ic, rc, rx, a.h, a.ih, &dummy);
+            tl.fv[t] = vd ? cx<T>(0, 0) : prolonged2(a, v, ic, rc, p);
         } else {
-            tl.fv[t] = a.xzero ? cx<T>(0, 0) : ld<T>(v.x, (long long)rc * a.g.nn + ic);
+            tl.fv[t] = (a.xzero || vd) ? cx<T>(0, 0) : ld<T>(v.x, p);
         }
     }
 #pragma unroll
@@ -129,26 +124,27 @@ __device__ __forceinline__ void tile_compute(const MArgs<T>& a, const PCoef<T>& 
     const int lane = threadIdx.x & 31;
     const int n = a.g.n;
     const int nc = n >> 1;
-    const T h = a.h, ih = a.ih;
     const int i = strip * (RR ? 28 : 30) + lane - (RR ? 2 : 1);
     const int base = cy * ROWS;
     const int rfirst = RR ? 2 * base - 2 : base - 1;
     const int ic = clampi(i, 0, n);
     const bool col_in = (i >= 0 && i <= n);
-    const bool col_fast = (i >= 2 && i <= n - 2);
-    const Row1<T> rx = row1<T>(ic, n, a.g.dir[0], a.g.dir[1], h, ih);
+    const bool col_inner = (i >= 1 && i <= n - 1);
+    const bool cvoid = col_void(a, i);
+    const int tx = ic == 0 ? 0 : (ic == n ? 2 : 1);
 
     if (MODE == M_JACOBI2_ZERO) {
-        // first sweep from x = 0: x1 = omega D^{-1} b, zero at Dirichlet nodes
+        // first sweep from x = 0: x1 = omega D^{-1} b, zero where no unknown lives
 #pragma unroll
         for (int t = 0; t < NR; ++t) {
-            const int rc = clampi(rfirst + t, 0, n);
-            if (ic >= 1 && ic <= n - 1 && rc >= 1 && rc <= n - 1) {
+            const int r = rfirst + t;
+            if (cvoid || row_void(a, r)) {
+                tl.fv[t] = cx<T>(0, 0);
+            } else if (col_inner && r >= 1 && r <= n - 1) {
                 tl.fv[t] = cmul(c.wdinv, tl.bv[t]);
             } else {
-                const Row1<T> ry = row1<T>(rc, n, a.g.dir[2], a.g.dir[3], h, ih);
-                tl.fv[t] = (rx.masked || ry.masked) ? cx<T>(0, 0)
-                                                   : a.omega * cmul(cinv(diag2(rx, ry, c.op)), tl.bv[t]);
+                const int ty = r == 0 ? 0 : (r == n ? 2 : 1);
+                tl.fv[t] = cmul(c.bdinv[bclass2(tx, ty)], tl.bv[t]);
             }
         }
     }
@@ -165,7 +161,7 @@ __device__ __forceinline__ void tile_compute(const MArgs<T>& a, const PCoef<T>& 
     for (int t = 1; t < NR - 1; ++t) {
         const int j = rfirst + t;
         const bool row_in = (j >= 0 && j <= n);
-        const bool fast = col_fast && j >= 2 && j <= n - 2;
+        const bool fast = col_inner && j >= 1 && j <= n - 1;
         const int jc = clampi(j, 0, n);
         const long long p = (long long)jc * a.g.nn + ic;
         Cx<T> ax;
@@ -177,25 +173,14 @@ __device__ __forceinline__ void tile_compute(const MArgs<T>& a, const PCoef<T>& 
             ax = fma_c(c.iw[2], diag, fma_c(c.iw[1], edge, cmul(c.iw[0], fv[t])));
             dinv_w = c.wdinv;
         } else {
-            const Row1<T> ry = row1<T>(jc, n, a.g.dir[2], a.g.dir[3], h, ih);
-            Cx<T> mx[3], kx[3];
-#pragma unroll
-            for (int u = 0; u < 3; ++u) {
-                mx[u] = fma_r(rx.mr, rg[t - 1 + u], fma_r(rx.mc, fv[t - 1 + u], rx.ml * lf[t - 1 + u]));
-                kx[u] = fma_r(rx.kr, rg[t - 1 + u], fma_r(rx.kc, fv[t - 1 + u], rx.kl * lf[t - 1 + u]));
-            }
-            Cx<T> Mx = fma_r(ry.mr, mx[2], fma_r(ry.mc, mx[1], ry.ml * mx[0]));
-            Cx<T> Kx = fma_r(ry.mr, kx[2], fma_r(ry.mc, kx[1], ry.ml * kx[0]));
-            Kx = fma_r(ry.kr, mx[2], fma_r(ry.kc, mx[1], fma_r(ry.kl, mx[0], Kx)));
-            Cx<T> F = cx<T>(0, 0);
-            if (rx.face) F = fma_r(ry.mr, fv[t + 1], fma_r(ry.mc, fv[t], ry.ml * fv[t - 1]));
-            if (ry.face) F = F + mx[1];
-            ax = c.op.cK * Kx;
-            ax = fma_c(c.op.cM, Mx, ax);
-            ax = fma_c(c.op.cG, F, ax);
-            masked = rx.masked || ry.masked;
-            dinv_w = (MODE == M_APPLY || MODE == M_AXPBY || RR) ? cx<T>(0, 0)
-                                                                 : a.omega * cinv(diag2(rx, ry, c.opd));
+            const int ty = jc == 0 ? 0 : (jc == n ? 2 : 1);
+            const int q = bclass2(tx, ty);
+            const Cx<T> hx = lf[t] + rg[t];
+            const Cx<T> vy = fv[t - 1] + fv[t + 1];
+            const Cx<T> dg = (lf[t - 1] + rg[t - 1]) + (lf[t + 1] + rg[t + 1]);
+            ax = fma_c(c.bw[q][3], dg, fma_c(c.bw[q][2], vy, fma_c(c.bw[q][1], hx, cmul(c.bw[q][0], fv[t]))));
+            dinv_w = c.bdinv[q];
+            masked = cvoid || row_void(a, j);
         }
         if (RR) {
             const Cx<T> res = (row_in && col_in && !masked) ? tl.zv[t - 1] - ax : cx<T>(0, 0);
@@ -244,16 +229,16 @@ __device__ __forceinline__ void tile_compute(const MArgs<T>& a, const PCoef<T>& 
 // One tile per warp; grid (strips, ceil(chunks / 4), problems).  BATCH = false: a batch of
 // one, coefficients from the kernel parameters and no activity flags.
 template <typename T, int MODE, int ROWS, bool BATCH>
-__global__ void __launch_bounds__(128) k_march2(MArgs<T> a, int chunks) {
+__global__ void __launch_bounds__(128) k_march2(const __grid_constant__ MArgs<T> a, int chunks) {
     pdl_entry();
     const int b = BATCH ? (int)blockIdx.z : 0;
     const int cy = blockIdx.y * 4 + (threadIdx.x >> 5);
     if (cy >= chunks) return;
     if (BATCH && problem_skipped(a, b)) return;
-    const PCoef<T> c = BATCH ? a.pc[b] : a.c0;
+    const PCoef<T>& c = BATCH ? a.pc[b] : a.c0;
     const VPtrs<T> v = problem_ptrs(a, b, MODE == M_RESID_RESTRICT);
     Tile2<T, MODE, ROWS> tl;
-    tile_load<T, MODE, ROWS>(a, c, v, blockIdx.x, cy, tl);
+    tile_load<T, MODE, ROWS>(a, v, blockIdx.x, cy, tl);
     tile_compute<T, MODE, ROWS>(a, c, v, blockIdx.x, cy, tl);
 }
 
@@ -262,20 +247,21 @@ __global__ void __launch_bounds__(128) k_march2(MArgs<T> a, int chunks) {
 // another) and issues the loads of its next tile before computing the current one, so that
 // its loads stay in flight while it computes.
 template <typename T, int MODE, int ROWS, bool BATCH>
-__global__ void __launch_bounds__(128) k_march2p(MArgs<T> a, int strips, int per_problem, int tiles) {
+__global__ void __launch_bounds__(128) k_march2p(const __grid_constant__ MArgs<T> a, int strips, int per_problem,
+                                                 int tiles) {
     pdl_entry();
     const int W = gridDim.x * 4;
     int t = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (t >= tiles) return;
     if constexpr (!BATCH) {
-        const PCoef<T> c = a.c0;
+        const PCoef<T>& c = a.c0;
         const VPtrs<T> v = problem_ptrs(a, 0, false);
         Tile2<T, MODE, ROWS> cur;
-        tile_load<T, MODE, ROWS>(a, c, v, t % strips, t / strips, cur);
+        tile_load<T, MODE, ROWS>(a, v, t % strips, t / strips, cur);
         for (; t < tiles; t += W) {
             Tile2<T, MODE, ROWS> nxt;
             const int tn = t + W;
-            if (tn < tiles) tile_load<T, MODE, ROWS>(a, c, v, tn % strips, tn / strips, nxt);
+            if (tn < tiles) tile_load<T, MODE, ROWS>(a, v, tn % strips, tn / strips, nxt);
             tile_compute<T, MODE, ROWS>(a, c, v, t % strips, t / strips, cur);
             cur = nxt;
         }
@@ -290,7 +276,7 @@ __global__ void __launch_bounds__(128) k_march2p(MArgs<T> a, int strips, int per
         split(t, &b, &strip, &cy);
         Tile2<T, MODE, ROWS> cur;
         bool have = !problem_skipped(a, b);
-        if (have) tile_load<T, MODE, ROWS>(a, a.pc[b], problem_ptrs(a, b, false), strip, cy, cur);
+        if (have) tile_load<T, MODE, ROWS>(a, problem_ptrs(a, b, false), strip, cy, cur);
         for (; t < tiles; t += W) {
             Tile2<T, MODE, ROWS> nxt;
             const int tn = t + W;
@@ -299,7 +285,7 @@ __global__ void __launch_bounds__(128) k_march2p(MArgs<T> a, int strips, int per
             if (tn < tiles) {
                 split(tn, &bn, &sn, &cn);
                 next = !problem_skipped(a, bn);
-                if (next) tile_load<T, MODE, ROWS>(a, a.pc[bn], problem_ptrs(a, bn, false), sn, cn, nxt);
+                if (next) tile_load<T, MODE, ROWS>(a, problem_ptrs(a, bn, false), sn, cn, nxt);
             }
             if (have) tile_compute<T, MODE, ROWS>(a, a.pc[b], problem_ptrs(a, b, false), strip, cy, cur);
             cur = nxt;
@@ -335,11 +321,40 @@ void interior_weights(PCoef<T>& c, const GridDesc& g, double omega) {
             mw[q] = m3[q] * h * h * h;
         }
     }
-    for (int q = 0; q < 4; ++q)
-        c.iw[q] = cx<T>(T(double(c.op.cK) * kw[q] + double(c.op.cM.re) * mw[q]), T(double(c.op.cM.im) * mw[q]));
-    const double dr = double(c.opd.cK) * kw[0] + double(c.opd.cM.re) * mw[0], di = double(c.opd.cM.im) * mw[0];
-    const double d2 = dr * dr + di * di;
-    c.wdinv = d2 > 0 ? cx<T>(T(omega * dr / d2), T(-omega * di / d2)) : cx<T>(T(0), T(0));
+    auto weight = [](const OpCoef<T>& o, double A, double M, double F) {
+        return cx<T>(T(double(o.cK) * A + double(o.cM.re) * M + double(o.cG.re) * F),
+                     T(double(o.cM.im) * M + double(o.cG.im) * F));
+    };
+    auto winv = [&](const OpCoef<T>& o, double A, double M, double F) {
+        const double dr = double(o.cK) * A + double(o.cM.re) * M + double(o.cG.re) * F;
+        const double di = double(o.cM.im) * M + double(o.cG.im) * F;
+        const double d2 = dr * dr + di * di;
+        return d2 > 0 ? cx<T>(T(omega * dr / d2), T(-omega * di / d2)) : cx<T>(T(0), T(0));
+    };
+    for (int q = 0; q < 4; ++q) c.iw[q] = weight(c.op, kw[q], mw[q], 0.0);
+    c.wdinv = winv(c.opd, kw[0], mw[0], 0.0);
+    for (int q = 0; q < 8; ++q) {
+        for (int u = 0; u < 4; ++u) c.bw[q][u] = cx<T>(T(0), T(0));
+        c.bdinv[q] = cx<T>(T(0), T(0));
+    }
+    if (g.dim != 2) return;
+    // 2D side nodes.  1D rows (Q1): stiffness (1/h)(-1, cnt, -1), mass (h/6)(1, 2 cnt, 1) with
+    // cnt = 2 inside, 1 at the ends; a node on a side also carries the 1D boundary mass of
+    // that side (centre: the along-side mass row's centre, neighbours along the side h/6).
+    const double ks = -1.0 / h, ms = h / 6.0;
+    for (int ty = 0; ty < 3; ++ty)
+        for (int tx = 0; tx < 3; ++tx) {
+            if (tx == 1 && ty == 1) continue;
+            const int cl = ty * 3 + tx, q = cl - (cl > 4);
+            const double cnx = tx == 1 ? 2.0 : 1.0, cny = ty == 1 ? 2.0 : 1.0;
+            const double kcx = cnx / h, kcy = cny / h, mcx = cnx * h / 3.0, mcy = cny * h / 3.0;
+            const bool fx = tx != 1, fy = ty != 1;  // on an x-side / a y-side
+            const double A[4] = {kcx * mcy + mcx * kcy, ks * mcy + ms * kcy, kcx * ms + mcx * ks, 2.0 * ks * ms};
+            const double M[4] = {mcx * mcy, ms * mcy, mcx * ms, ms * ms};
+            const double F[4] = {(fx ? mcy : 0.0) + (fy ? mcx : 0.0), fy ? ms : 0.0, fx ? ms : 0.0, 0.0};
+            for (int u = 0; u < 4; ++u) c.bw[q][u] = weight(c.op, A[u], M[u], F[u]);
+            c.bdinv[q] = winv(c.opd, A[0], M[0], F[0]);
+        }
 }
 
 template void interior_weights<float>(PCoef<float>&, const GridDesc&, double);

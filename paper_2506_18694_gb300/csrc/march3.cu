@@ -91,11 +91,11 @@ constexpr int kWarps3 = 8;  // y-rows per tile, including the two halo rows
 
 // BATCH = false: a batch of one, coefficients from the kernel parameters, no activity flags.
 template <typename T, int MODE, int R, bool BATCH>
-__global__ void __launch_bounds__(32 * kWarps3) k_march3(MArgs<T> a, int zt) {
+__global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__ MArgs<T> a, int zt) {
     pdl_entry();
     const int b = BATCH ? (int)blockIdx.z / zt : 0;  // problem; blockIdx.z % zt: z-tile
     if (BATCH && problem_skipped(a, b)) return;
-    const PCoef<T> cf = BATCH ? a.pc[b] : a.c0;
+    const PCoef<T>& cf = BATCH ? a.pc[b] : a.c0;
     const VPtrs<T> v = problem_ptrs(a, b, false);
     constexpr int NP = R + 2;  // planes loaded
     constexpr bool NEEDZ = MODE != M_APPLY;

@@ -33,6 +33,8 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--rows", type=int, default=0, help="tile rows/planes (0 = automatic)")
+    ap.add_argument("--batch", type=int, default=1, help="problems in the batch (vectors nb x nodes)")
+    ap.add_argument("--autotune", action="store_true", help="tune tile shapes first")
     args = ap.parse_args(argv)
     prec = hh.HH_C64 if args.prec == "c64" else hh.HH_C128
     dt = torch.complex64 if prec == hh.HH_C64 else torch.complex128
@@ -40,14 +42,17 @@ def main(argv=None):
     k = 80.0
     bc = [hh.SOMMERFELD] * (2 * args.dim)
     levels = 4 if args.kernel == "vcycle" else 2
-    p = hh.Problem(args.dim, args.n, k, 0.0, k, bc,
+    kk = k if args.batch == 1 else [k] * args.batch
+    p = hh.Problem(args.dim, args.n, kk, 0.0, k, bc,
                    hh.default_options(precision=prec, levels=levels, restart=1, tile_rows=args.rows))
-    N = p.nodes()
+    if args.autotune:
+        p.autotune()
+    N = p.size()
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.randn(N, dtype=dt, device="cuda", generator=g)
     b = torch.randn(N, dtype=dt, device="cuda", generator=g)
     y = torch.empty_like(x)
-    rc = torch.empty(p.nodes(1), dtype=dt, device="cuda")
+    rc = torch.empty(p.size(1), dtype=dt, device="cuda")
     fn = {
         "apply": lambda: p.apply(0, "AL", x, y),
         "jacobi": lambda: p.jacobi(0, b, x, y),
@@ -65,8 +70,8 @@ def main(argv=None):
     end.record(s)
     end.synchronize()
     t = start.elapsed_time(end) / args.reps / 1e3
-    out = {"kernel": args.kernel, "dim": args.dim, "n": args.n, "nodes": N, "prec": args.prec, "rows": args.rows,
-           "us": t * 1e6}
+    out = {"kernel": args.kernel, "dim": args.dim, "n": args.n, "batch": args.batch, "nodes": N, "prec": args.prec,
+           "rows": args.rows, "autotune": args.autotune, "us": t * 1e6}
     if BYTES[args.kernel] is not None:
         byt = BYTES[args.kernel](e, args.dim) * N
         out.update({"bytes": byt, "gbs": byt / t / 1e9})

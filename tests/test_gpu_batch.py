@@ -139,3 +139,21 @@ def test_binding_rejects_wrong_sizes(libhh):
             pb.solve(short)
         with pytest.raises(ValueError):
             pb.apply(0, "AL", short)
+
+
+def test_large_batch_coarse_clusters_equal_solo(libhh):
+    """24 problems: the coarsest-level solve runs smaller clusters per problem than a batch
+    of one does (so that all clusters are resident at once); results stay bit for bit."""
+    dim, n, bc = 2, 64, (S, D, S, S)
+    g = O.Grid(dim, n, bc)
+    mix = [MIX[i % len(MIX)] for i in range(24)]
+    f = _rhs(g, len(mix), 1200)
+    with _batch(dim, n, bc, mix, levels=3) as pb:
+        ub, infos = pb.solve(torch.from_numpy(f.reshape(-1)).cuda(), 1e-9)
+        ub = ub.cpu().numpy().reshape(len(mix), g.N)
+    for b in (0, 5, 11, 23):
+        k, delta, dh = mix[b]
+        with hh.Problem(dim, n, k, delta, dh, bc, hh.default_options(levels=3)) as p:
+            u, info = p.solve(torch.from_numpy(f[b]).cuda(), 1e-9)
+        assert np.array_equal(ub[b], u.cpu().numpy()), b
+        assert infos[b].outer_its == info.outer_its
