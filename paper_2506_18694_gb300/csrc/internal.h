@@ -119,6 +119,15 @@ template <typename T> struct PCoef {
 template <typename T>
 void interior_weights(PCoef<T>& c, const GridDesc& g, double omega);
 
+// 3D nodes on a face, edge or corner of the cube: 26 classes ((z type * 3 + y type) * 3 +
+// x type, the inner class 13 left out), each with the weights of its 8 neighbour groups
+// (centre; x, y, z faces; xy, xz, yz edges; corners) and omega / diag(opd) last.
+constexpr int kClass3 = 26;
+constexpr int kClass3Len = 9;
+// Host: fill out[kClass3][kClass3Len] for the operators of c on grid g.
+template <typename T>
+void boundary_weights3(Cx<T>* out, const PCoef<T>& c, const GridDesc& g, double omega);
+
 // Arguments of the stencil kernels.  Problem b of a batch of nb reads x, z, y, y2 at
 // offset b * bs, ec (and writes the coarse output of RESID_RESTRICT) at offset b * bsc,
 // and its coefficients at pc[b].
@@ -126,6 +135,7 @@ template <typename T> struct MArgs {
     GridDesc g;          // grid of the level the stencil runs on
     const PCoef<T>* pc;  // device coefficient table of this operator and level (nullptr: c0)
     PCoef<T> c0;         // the coefficients of a batch of one, passed by value
+    const Cx<T>* bw3;    // 3D: device boundary-class weights, problem b at b * kClass3 * kClass3Len
     const vec2<T>* x;    // stencil input (ignored for M_JACOBI2_ZERO; nullptr = 0 when xzero)
     const vec2<T>* z;    // right side / second vector
     const vec2<T>* ec;   // coarse correction (M_PROLONG_JACOBI)

@@ -6,8 +6,9 @@
 // x-sum of each plane in shared memory; after one barrier the six output warps read rows
 // j-1 and j+1 from shared memory and keep their own row in registers.  Interior nodes use
 // the four neighbour-class weights of the 27-point Q1 operator (centre, face, edge,
-// corner); nodes near the boundary rebuild their row from the 1D weight triples, as in the
-// 2D kernels.
+// corner).  The field is loaded as zero outside the cube and at Dirichlet nodes, so a node
+// on a face, edge or corner sums its existing neighbours by group (centre; x, y, z faces;
+// xy, xz, yz edges; corners) with the eight weights of its boundary class.
 #include "internal.h"
 
 namespace hh {
@@ -25,34 +26,35 @@ __device__ __forceinline__ Cx<T> shfl_dn3(Cx<T> v) {
     return Cx<T>{__shfl_down_sync(0xffffffffu, v.re, 1), __shfl_down_sync(0xffffffffu, v.im, 1)};
 }
 
-template <typename T>
-__device__ __forceinline__ Cx<T> diag3(const Row1<T>& rx, const Row1<T>& ry, const Row1<T>& rz, const OpCoef<T>& op) {
-    const T dr = op.cK * (rx.kc * ry.mc * rz.mc + rx.mc * ry.kc * rz.mc + rx.mc * ry.mc * rz.kc);
-    const T dm = rx.mc * ry.mc * rz.mc;
-    const T dg = (rx.face ? ry.mc * rz.mc : T(0)) + (ry.face ? rx.mc * rz.mc : T(0)) + (rz.face ? rx.mc * ry.mc : T(0));
-    return cx<T>(dr + op.cM.re * dm + op.cG.re * dg, op.cM.im * dm + op.cG.im * dg);
-}
-
 __device__ __forceinline__ bool coarse_dir(int I, int nc, int lo, int hi) { return (I == 0 && lo) || (I == nc && hi); }
 
-// Value of the stencil field at node (i, j, l) (all clamped into the grid).
+// Whether coordinate v of an axis with Dirichlet flags lo, hi holds no unknown.
+__device__ __forceinline__ bool void1(int v, int n, int lo, int hi) {
+    return v < 0 || v > n || (v == 0 && lo) || (v == n && hi);
+}
+
+__device__ __forceinline__ int type1(int v, int n) { return v <= 0 ? 0 : (v >= n ? 2 : 1); }
+
+// Boundary-class index of a node with axis types tx, ty, tz (not all inner).
+__device__ __forceinline__ int bclass3(int tx, int ty, int tz) {
+    const int c = (tz * 3 + ty) * 3 + tx;
+    return c - (c > 13);
+}
+
+// Value of the stencil field at node (i, j, l) of the grid, which holds an unknown there.
 template <typename T, int MODE>
-__device__ __forceinline__ Cx<T> field3(const MArgs<T>& a, const PCoef<T>& c, const VPtrs<T>& v, int i, int j, int l,
-                                        const Row1<T>& rx, const Row1<T>& ry, T h, T ih) {
+__device__ __forceinline__ Cx<T> field3(const MArgs<T>& a, const PCoef<T>& c, const Cx<T>* bw, const VPtrs<T>& v,
+                                        int i, int j, int l) {
     const int n = a.g.n, nn = a.g.nn;
     const long long p = ((long long)l * nn + j) * nn + i;
     if (MODE == M_JACOBI2_ZERO) {
-        // first sweep from x = 0: x1 = omega D^{-1} b (zero at Dirichlet nodes)
+        // first sweep from x = 0: x1 = omega D^{-1} b
         const Cx<T> b = ld<T>(v.z, p);
         if (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1 && l >= 1 && l <= n - 1) return cmul(c.wdinv, b);
-        const Row1<T> rz = row1<T>(l, n, a.g.dir[4], a.g.dir[5], h, ih);
-        if (rx.masked || ry.masked || rz.masked) return cx<T>(0, 0);
-        return a.omega * cmul(cinv(diag3(rx, ry, rz, c.op)), b);
+        const int q = bclass3(type1(i, n), type1(j, n), type1(l, n));
+        return cmul(bw[q * kClass3Len + 8], b);
     } else if (MODE == M_PROLONG_JACOBI) {
         // x + P e_c: trilinear interpolation of the coarse correction
-        if (rx.masked || ry.masked) return cx<T>(0, 0);
-        const Row1<T> rz = row1<T>(l, n, a.g.dir[4], a.g.dir[5], h, ih);
-        if (rz.masked) return cx<T>(0, 0);
         const int nc = n >> 1, nnc = nc + 1;
         const int I0 = i >> 1, J0 = j >> 1, L0 = l >> 1;
         const bool oi = i & 1, oj = j & 1, ol = l & 1;
@@ -96,6 +98,7 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__
     const int b = BATCH ? (int)blockIdx.z / zt : 0;  // problem; blockIdx.z % zt: z-tile
     if (BATCH && problem_skipped(a, b)) return;
     const PCoef<T>& cf = BATCH ? a.pc[b] : a.c0;
+    const Cx<T>* bw = a.bw3 + (long long)b * kClass3 * kClass3Len;
     const VPtrs<T> v = problem_ptrs(a, b, false);
     constexpr int NP = R + 2;  // planes loaded
     constexpr bool NEEDZ = MODE != M_APPLY;
@@ -106,17 +109,19 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int n = a.g.n, nn = a.g.nn;
-    const T h = a.h, ih = a.ih;
     const int i = blockIdx.x * 30 + lane - 1;
     const int j = blockIdx.y * (kWarps3 - 2) + w - 1;
     const int l0 = (blockIdx.z - b * zt) * R;
     const int ic = clampi3(i, 0, n), jc = clampi3(j, 0, n);
-    const Row1<T> rx = row1<T>(ic, n, a.g.dir[0], a.g.dir[1], h, ih);
-    const Row1<T> ry = row1<T>(jc, n, a.g.dir[2], a.g.dir[3], h, ih);
+    const bool cvoid = void1(i, n, a.g.dir[0], a.g.dir[1]) || void1(j, n, a.g.dir[2], a.g.dir[3]);
 
     Cx<T> fv[NP], xs[NP];
 #pragma unroll
-    for (int t = 0; t < NP; ++t) fv[t] = field3<T, MODE>(a, cf, v, ic, jc, clampi3(l0 - 1 + t, 0, n), rx, ry, h, ih);
+    for (int t = 0; t < NP; ++t) {
+        const int l = l0 - 1 + t;
+        fv[t] = (cvoid || void1(l, n, a.g.dir[4], a.g.dir[5])) ? cx<T>(0, 0)
+                                                               : field3<T, MODE>(a, cf, bw, v, ic, jc, clampi3(l, 0, n));
+    }
     Cx<T> zv[R];
     const bool out_row = w >= 1 && w <= kWarps3 - 2;
 #pragma unroll
@@ -130,7 +135,8 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__
     }
     __syncthreads();
     if (!out_row || !(lane >= 1 && lane <= 30) || i > n || j > n) return;
-    const bool colrow_fast = i >= 2 && i <= n - 2 && j >= 2 && j <= n - 2;
+    const bool colrow_inner = i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1;
+    const int tx = type1(i, n), ty = type1(j, n);
     const int wm = w - 1, wp = w + 1;
     // rows j-1 + j+1 summed (value and x-sum) per plane, in a rolling window of 3 planes
     auto ysum = [&](const vec2<T>* arr, int tpl) {
@@ -146,48 +152,25 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__
         const long long p = ((long long)l * nn + j) * nn + i;
         Cx<T> ax, dinv_w;
         bool masked = false;
-        if (colrow_fast && l >= 2 && l <= n - 2) {
+        if (colrow_inner && l >= 1 && l <= n - 1) {
             const Cx<T> face = xs[tp] + vy1 + (fv[tp - 1] + fv[tp + 1]);
             const Cx<T> edge = sy1 + (xs[tp - 1] + xs[tp + 1]) + (vy0 + vy2);
             const Cx<T> corner = sy0 + sy2;
             ax = fma_c(cf.iw[3], corner, fma_c(cf.iw[2], edge, fma_c(cf.iw[1], face, cmul(cf.iw[0], fv[tp]))));
             dinv_w = cf.wdinv;
         } else {
-            const Row1<T> rz = row1<T>(l, n, a.g.dir[4], a.g.dir[5], h, ih);
-            masked = rx.masked || ry.masked || rz.masked;
-            const T myw[3] = {ry.ml, ry.mc, ry.mr};
-            const T kyw[3] = {ry.kl, ry.kc, ry.kr};
-            const T mzw[3] = {rz.ml, rz.mc, rz.mr};
-            const T kzw[3] = {rz.kl, rz.kc, rz.kr};
-            Cx<T> Mx = cx<T>(0, 0), Kx = cx<T>(0, 0), Fxf = cx<T>(0, 0), Fyf = cx<T>(0, 0), Fzf = cx<T>(0, 0);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                Cx<T> PM = cx<T>(0, 0), PK = cx<T>(0, 0), Pf = cx<T>(0, 0), mxc = cx<T>(0, 0);
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    const int base = ((w - 1 + b) * NP + tp - 1 + c) * 32 + lane;
-                    const Cx<T> v0 = ld<T>(sv, base - 1), v1 = ld<T>(sv, base), v2 = ld<T>(sv, base + 1);
-                    const Cx<T> mx = fma_r(rx.mr, v2, fma_r(rx.mc, v1, rx.ml * v0));
-                    const Cx<T> kx = fma_r(rx.kr, v2, fma_r(rx.kc, v1, rx.kl * v0));
-                    PM = fma_r(myw[b], mx, PM);
-                    PK = fma_r(myw[b], kx, fma_r(kyw[b], mx, PK));
-                    Pf = fma_r(myw[b], v1, Pf);
-                    if (b == 1) mxc = mx;
-                }
-                Mx = fma_r(mzw[c], PM, Mx);
-                Kx = fma_r(mzw[c], PK, fma_r(kzw[c], PM, Kx));
-                Fxf = fma_r(mzw[c], Pf, Fxf);
-                Fyf = fma_r(mzw[c], mxc, Fyf);
-                if (c == 1) Fzf = PM;
-            }
-            Cx<T> F = cx<T>(0, 0);
-            if (rx.face) F = F + Fxf;
-            if (ry.face) F = F + Fyf;
-            if (rz.face) F = F + Fzf;
-            ax = cf.op.cK * Kx;
-            ax = fma_c(cf.op.cM, Mx, ax);
-            ax = fma_c(cf.op.cG, F, ax);
-            dinv_w = (MODE == M_APPLY || MODE == M_AXPBY) ? cx<T>(0, 0) : a.omega * cinv(diag3(rx, ry, rz, cf.opd));
+            // neighbour groups: centre; x, y, z faces; xy, xz, yz edges; corners
+            masked = cvoid || void1(l, n, a.g.dir[4], a.g.dir[5]);
+            const Cx<T>* wq = bw + bclass3(tx, ty, type1(l, n)) * kClass3Len;
+            ax = cmul(wq[0], fv[tp]);
+            ax = fma_c(wq[1], xs[tp], ax);
+            ax = fma_c(wq[2], vy1, ax);
+            ax = fma_c(wq[3], fv[tp - 1] + fv[tp + 1], ax);
+            ax = fma_c(wq[4], sy1, ax);
+            ax = fma_c(wq[5], xs[tp - 1] + xs[tp + 1], ax);
+            ax = fma_c(wq[6], vy0 + vy2, ax);
+            ax = fma_c(wq[7], sy0 + sy2, ax);
+            dinv_w = wq[8];
         }
         const Cx<T> alpha = a.use_pc_ab ? cf.alpha : a.alpha, beta = a.use_pc_ab ? cf.beta : a.beta;
         if (masked) {
@@ -211,6 +194,59 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__
     }
 }
 
+// Weights of the 3D boundary classes.  1D rows (Q1): stiffness (1/h)(-1, cnt, -1), mass
+// (h/6)(1, 2 cnt, 1), cnt = 2 inside and 1 at the ends of the axis.  Group S (the axes along
+// which the neighbour is offset) has stiffness weight sum_a K_a prod_{b != a} M_b and mass
+// weight prod_b M_b, with K_a, M_b the side weights (-1/h, h/6) on offset axes and the
+// centre weights otherwise; a node on the side of axis a also carries the 2D boundary mass
+// of that face, prod_{b != a} M_b, for the groups not offset along a.
+template <typename T>
+void boundary_weights3(Cx<T>* out, const PCoef<T>& c, const GridDesc& g, double omega) {
+    const double h = g.h, ks = -1.0 / h, ms = h / 6.0;
+    // groups: centre; x, y, z faces; xy, xz, yz edges; corners (bit a set: offset along axis a)
+    const int groups[8] = {0, 1, 2, 4, 3, 5, 6, 7};
+    for (int tz = 0; tz < 3; ++tz)
+        for (int ty = 0; ty < 3; ++ty)
+            for (int tx = 0; tx < 3; ++tx) {
+                const int cl = (tz * 3 + ty) * 3 + tx;
+                if (cl == 13) continue;
+                const int q = cl - (cl > 13);
+                const int typ[3] = {tx, ty, tz};
+                double kc[3], mc[3];
+                for (int a = 0; a < 3; ++a) {
+                    const double cnt = typ[a] == 1 ? 2.0 : 1.0;
+                    kc[a] = cnt / h;
+                    mc[a] = cnt * h / 3.0;
+                }
+                double A[8], M[8], F[8];
+                for (int u = 0; u < 8; ++u) {
+                    const int S = groups[u];
+                    double kk[3], mm[3];
+                    for (int a = 0; a < 3; ++a) {
+                        const bool off = (S >> a) & 1;
+                        kk[a] = off ? ks : kc[a];
+                        mm[a] = off ? ms : mc[a];
+                    }
+                    A[u] = kk[0] * mm[1] * mm[2] + mm[0] * kk[1] * mm[2] + mm[0] * mm[1] * kk[2];
+                    M[u] = mm[0] * mm[1] * mm[2];
+                    F[u] = 0.0;
+                    for (int a = 0; a < 3; ++a)
+                        if (typ[a] != 1 && !((S >> a) & 1)) F[u] += mm[(a + 1) % 3] * mm[(a + 2) % 3];
+                }
+                Cx<T>* o = out + (size_t)q * kClass3Len;
+                for (int u = 0; u < 8; ++u)
+                    o[u] = cx<T>(T(double(c.op.cK) * A[u] + double(c.op.cM.re) * M[u] + double(c.op.cG.re) * F[u]),
+                                 T(double(c.op.cM.im) * M[u] + double(c.op.cG.im) * F[u]));
+                const double dr = double(c.opd.cK) * A[0] + double(c.opd.cM.re) * M[0] + double(c.opd.cG.re) * F[0];
+                const double di = double(c.opd.cM.im) * M[0] + double(c.opd.cG.im) * F[0];
+                const double d2 = dr * dr + di * di;
+                o[8] = d2 > 0 ? cx<T>(T(omega * dr / d2), T(-omega * di / d2)) : cx<T>(T(0), T(0));
+            }
+}
+
+template void boundary_weights3<float>(Cx<float>*, const PCoef<float>&, const GridDesc&, double);
+template void boundary_weights3<double>(Cx<double>*, const PCoef<double>&, const GridDesc&, double);
+
 template <typename T, int MODE, int R>
 static cudaError_t go3(MArgs<T> a, cudaStream_t s) {
     // at most 40 KiB: within the default dynamic shared-memory limit, no opt-in needed
@@ -228,12 +264,11 @@ template <typename T, int MODE>
 static cudaError_t pick3(MArgs<T> a, cudaStream_t s) {
     a.h = T(a.g.h);
     a.ih = T(1.0 / a.g.h);
-    // more planes per tile on large grids (fewer halo planes), fewer on small ones (more CTAs)
-    const long long ctas4 = (long long)((a.g.nn + 29) / 30) * ((a.g.nn + 5) / 6) * ((a.g.nn + 3) / 4) * a.nb;
+    // 4 planes per tile unless tuned otherwise (measured best on 257^3: 8 planes halve the
+    // resident CTAs, 2 planes double the halo planes)
     if constexpr (sizeof(T) == 4) {
         if (a.tile_rows == 2) return go3<T, MODE, 2>(a, s);
-        if (a.tile_rows == 4) return go3<T, MODE, 4>(a, s);
-        if (a.tile_rows == 8 || ctas4 >= 152LL * 16) return go3<T, MODE, 8>(a, s);
+        if (a.tile_rows == 8) return go3<T, MODE, 8>(a, s);
         return go3<T, MODE, 4>(a, s);
     } else {
         return go3<T, MODE, 2>(a, s);

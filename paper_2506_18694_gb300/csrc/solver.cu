@@ -104,6 +104,7 @@ struct Hier {
     void* cb = nullptr;
     void* cres = nullptr;
     void* pc = nullptr;               // coefficient tables: [role][level][problem] PCoef<T>
+    void* bw3 = nullptr;              // 3D boundary-class weights: [role][level][problem][26][9] Cx<T>
     std::vector<unsigned char> pc_host;  // host copy of the tables
     void** usrc = nullptr;            // device: per problem, the buffer holding u after the HSS loop
     cudaGraphExec_t graph = nullptr;  // one preconditioner application (the HSS loop)
@@ -228,6 +229,18 @@ hh_status build_tables(hh_problem* p, Hier& H) {
     H.pc_host.assign((const unsigned char*)tab.data(), (const unsigned char*)tab.data() + bytes);
     HH_TRY(dmalloc(p, &H.pc, bytes));
     HH_CUDA(cudaMemcpyAsync(H.pc, tab.data(), bytes, cudaMemcpyHostToDevice, p->s));
+    if (p->grid.dim == 3) {
+        const size_t per = (size_t)hh::kClass3 * hh::kClass3Len;
+        std::vector<Cx<T>> w3(tab.size() * per);
+        for (int role = 0; role < R_COUNT; ++role)
+            for (int l = 0; l < L; ++l)
+                for (int b = 0; b < nb; ++b) {
+                    const size_t e = ((size_t)role * L + l) * nb + b;
+                    hh::boundary_weights3<T>(w3.data() + e * per, tab[e], p->lv[l], p->o.omega);
+                }
+        HH_TRY(dmalloc(p, &H.bw3, w3.size() * sizeof(Cx<T>)));
+        HH_CUDA(cudaMemcpyAsync(H.bw3, w3.data(), w3.size() * sizeof(Cx<T>), cudaMemcpyHostToDevice, p->s));
+    }
     HH_CUDA(cudaStreamSynchronize(p->s));
     return HH_OK;
 }
@@ -244,8 +257,10 @@ size_t hier_bytes(const hh_grid* grid, int levels, int prec, int nb) {
         if (l == 0) tot += 5 * (size_t)N * elem * B;  // r_lo, rhs, ca, cb, cres
     }
     tot += sizeof(void*) * B;  // usrc
-    // coefficient tables of both precisions
+    // coefficient tables of both precisions (and the 3D boundary-class tables)
     tot += (size_t)R_COUNT * levels * B * (sizeof(PCoef<float>) + sizeof(PCoef<double>));
+    if (grid->dim == 3)
+        tot += (size_t)R_COUNT * levels * B * hh::kClass3 * hh::kClass3Len * (sizeof(Cx<float>) + sizeof(Cx<double>));
     return tot;
 }
 
@@ -347,6 +362,8 @@ struct MG {
         } else {
             a.pc = table(role, l);
         }
+        if (H->bw3)
+            a.bw3 = (const Cx<T>*)H->bw3 + ((size_t)role * p->o.levels + l) * p->nb * hh::kClass3 * hh::kClass3Len;
         a.nb = p->nb;
         a.bs = Nl(l);
         a.bsc = l + 1 < p->o.levels ? Nl(l + 1) : 0;
