@@ -34,6 +34,7 @@ WORKLOAD = "2d_n512_k80"
 GRIDS = {"2d_n512_k80": "2D unit square, 512x512 Q1 cells (513^2 nodes), Sommerfeld on all sides",
          "3d_n128_k40": "3D unit cube, 128^3 Q1 cells (129^3 nodes), u=0 on z=0, Sommerfeld elsewhere"}
 L2_FLUSH_BYTES = 256 << 20
+SERVE_REQUESTS = [16]
 
 
 def parse():
@@ -46,6 +47,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=["2d_n512_k80", "3d_n128_k40"],
                     help="2D 512^2 k=80 (default) or 3D 128^3 k=40 (FGMRES restart 60)")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 / roofline / CPU legs")
+    ap.add_argument("--serve-requests", type=int, default=16,
+                    help="requests of the serving workload replayed by the serving leg (its full size is 1000)")
+    ap.add_argument("--serve-only", action="store_true", help="run the serving leg alone and print its line")
     ap.add_argument("--max-outer", type=int, default=0,
                     help="cap FGMRES iterations (profiling runs only; 0 = solve to tolerance)")
     return ap.parse_args()
@@ -206,6 +210,11 @@ def main():
     else:
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
+    SERVE_REQUESTS[0] = args.serve_requests
+    if args.serve_only:
+        if rank == 0:
+            print(json.dumps({"serving": measure_serving(hh, inputs, torch, args.serve_requests)}), flush=True)
+        return
     w = inputs.workload(args.workload, args.delta_hat)
     opts = hh.default_options(precision=hh.HH_C64, restart=60 if w.dim == 3 else 30)
     if args.max_outer > 0:
@@ -416,6 +425,12 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
     out["delta_hat_2"] = {"cycles_per_hss": 2, "solve_ms": 1e3 * t2, "outer_its": i2.outer_its, "vcycles": i2.vcycles,
                           "rel_residual": i2.rel_residual, "value": prob.nodes() * i2.vcycles / t2}
 
+    # serving: Poisson arrivals of mixed 2D/3D requests through the solve server
+    try:
+        out["serving"] = measure_serving(hh, inputs, torch, SERVE_REQUESTS[0])
+    except Exception as e:
+        out["serving"] = {"failed": str(e)}
+
     # batched: 64 right sides on 2D 256^2, k from {20, 40, 80}, one problem object
     try:
         out["batch64"] = measure_batch(hh, inputs, torch)
@@ -431,6 +446,61 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
     except Exception as e:  # the CPU leg must not hide the GPU numbers
         out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle", "sample": f"failed: {e}"}
     return out
+
+
+def measure_serving(hh, inputs, torch, count, slots=4, load=0.8):
+    """The serving workload (mixed 2D/3D grids and wavenumbers, nodal Gaussian sources,
+    delta_hat = k, tol 1e-8, FGMRES restart 60) through the solve server.  Pass 1 runs the
+    requests one at a time (1 slot) and gives the sequential service capacity; pass 2
+    replays them with Poisson arrivals at `load` times that capacity into a server with
+    `slots` slots (latency); pass 3 queues them all at once (throughput with overlap)."""
+    reqs = inputs.serving_requests(count)
+    srcs = [r.source() for r in reqs]
+    opts = hh.default_options(precision=hh.HH_C64, restart=60)
+    budget = int(torch.cuda.mem_get_info()[0] * 0.6)
+
+    def run(slots, arrivals):
+        with hh.Server(slots=slots, budget_bytes=budget, options=opts) as srv:
+            t0 = time.perf_counter()
+            tickets = []
+            for r, f, a in zip(reqs, srcs, arrivals):
+                now = time.perf_counter() - t0
+                if a > now:
+                    time.sleep(a - now)
+                tickets.append(srv.submit(r.dim, r.n, r.k, r.delta, r.delta_hat, r.bc, f, 1e-8, nodal=True))
+            res = [srv.wait(t) for t in tickets]
+            span = time.perf_counter() - t0
+            st = srv.stats()
+        return res, span, st
+
+    seq, seq_span, _ = run(1, [0.0] * len(reqs))
+    service = [x[1].seconds for x in seq]
+    cap = len(reqs) / sum(service)
+    rate = load * cap
+    arr = [r.arrival / reqs[-1].arrival * (len(reqs) / rate) for r in reqs]  # seeded Poisson times, rescaled
+    res, span, st = run(slots, arr)
+    _, sat_span, sat_st = run(slots, [0.0] * len(reqs))  # everything queued at once
+    lat = [x[2] for x in res]
+    work = sum(r.nodes * x[1].vcycles for r, x in zip(reqs, res))
+    return {
+        "workload": "serving: half 2D n in [64,1024], half 3D n in [32,96] (log-uniform, multiple of 8), "
+                    "k uniform [10,160] capped at 2 pi n/10, delta_hat = k, tol 1e-8",
+        "requests": len(reqs), "of_full": 1000, "slots": slots, "budget_bytes": budget,
+        "sequential_capacity_solves_per_s": cap, "arrival_rate_per_s": rate, "load": load,
+        "solves_per_s": len(reqs) / span, "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
+                                                         "p99": 1e3 * float(np.percentile(lat, 99))},
+        "queue_ms_p50": 1e3 * float(np.percentile([x[3] for x in res], 50)),
+        "value": work / span, "unit": UNIT,
+        "max_rel_residual": max(x[1].rel_residual for x in res),
+        "max_concurrent": st["max_concurrent"], "peak_bytes": st["peak_bytes"],
+        "problems_created": st["problems_created"], "problems_reused": st["problems_reused"],
+        "problems_evicted": st["problems_evicted"],
+        "sequential_s": seq_span,
+        "saturated": {"solves_per_s": len(reqs) / sat_span, "vs_sequential": seq_span / sat_span,
+                      "max_concurrent": sat_st["max_concurrent"]},
+        "per_request": [[r.dim, r.n, round(r.k, 1), x[1].outer_its, x[1].rel_residual, round(x[1].seconds, 3)]
+                        for r, x in zip(reqs, seq)],
+    }
 
 
 def measure_batch(hh, inputs, torch):

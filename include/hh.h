@@ -199,6 +199,28 @@ HH_API hh_status hh_solve(hh_problem* p, const void* rhs, double tol, void* u, c
 HH_API hh_status hh_solve_host(hh_problem* p, const void* rhs_host, double tol, void* u_host,
                         hh_info* info);
 
+/* As hh_solve_host, with the nodal values f of the source instead of the load vector:
+ * the right side b = M f (Sec. 2, f in Q1) is formed on the device. */
+HH_API hh_status hh_solve_host_nodal(hh_problem* p, const void* f_host, double tol, void* u_host,
+                                     hh_info* info);
+
+/*
+ * Give every problem of the batch new k[b], delta[b], delta_hat[b] (host arrays of nb
+ * values, checked as in hh_create_batch) on the same grid: the coefficient tables are
+ * rebuilt in place, no device memory is allocated or freed, and the preconditioner graph
+ * is captured again at the next solve (or hh_prepare).  Blocking.  A service of this
+ * library (the paper has none): it lets a serving loop reuse a problem's hierarchy and
+ * Krylov basis for the next request on the same grid.
+ */
+HH_API hh_status hh_set_params(hh_problem* p, const double* k, const double* delta, const double* delta_hat);
+
+/*
+ * Capture the preconditioner graph (and allocate the multigrid buffers) now instead of
+ * at the first solve, so that a caller can keep allocations and captures out of the way
+ * of work it runs concurrently.  Blocking.
+ */
+HH_API hh_status hh_prepare(hh_problem* p);
+
 /* Nodes (n_l + 1)^dim of level l, or 0 if l is out of range. */
 HH_API long long hh_level_nodes(const hh_problem* p, int level);
 
@@ -257,6 +279,60 @@ HH_API hh_status hh_dot(hh_problem* p, const void* x, const void* y, double* out
  */
 HH_API hh_status hh_multidot_noalloc(const void* V, long long ld, int nvec, const void* w, long long n,
                                      void* out, void* cuda_stream);
+
+/*
+ * ---- continuous-batching solve server (a service of this library; the paper has none) ----
+ * A request loop on the current device: requests of any grid, wavenumber and shifts are
+ * queued, admitted in arrival order as worker slots and device memory free up, and solved
+ * concurrently, each on its own CUDA stream, so that their kernels overlap on the GPU.
+ * Each admitted solve keeps its hierarchy and Krylov basis on the device; finished
+ * problems stay pooled and are retargeted (hh_set_params) for later requests on the same
+ * grid, and idle problems of other grids are destroyed, least recently used first, when a
+ * new request needs their memory.  Every request's result is the one a lone
+ * hh_solve_host of the same problem would give.
+ */
+typedef struct hh_server hh_server;
+
+typedef struct {
+    hh_grid grid;           /* unit square / cube, n cells per axis                       */
+    double k, delta, delta_hat;
+    int bc[6];              /* boundary tags as in hh_create_problem                      */
+    double tol;             /* relative residual target of the outer FGMRES               */
+    int rhs_kind;           /* 0: rhs is the load vector b; 1: nodal source f, b = M f    */
+} hh_request;
+
+typedef struct {
+    long long submitted, completed, failed, queued;
+    int running;            /* solves on the device now                                   */
+    int max_concurrent;     /* most solves on the device at once so far                   */
+    size_t budget;          /* device bytes the server may hold in problems               */
+    size_t held_bytes;      /* bytes held now (running and pooled problems)               */
+    size_t peak_bytes;      /* most bytes held at once so far (never above budget)        */
+    long long problems_created, problems_reused, problems_evicted;
+} hh_server_stats;
+
+/* Start a server with `slots` worker threads (1..64: at most that many solves run at
+ * once) that holds at most device_budget bytes of problems (hh_footprint_bytes of each),
+ * all built with *opts.  Returns HH_ERR_INVALID for bad arguments. */
+HH_API hh_status hh_server_create(int slots, size_t device_budget, const hh_options* opts, hh_server** out);
+
+/* Queue one solve: rhs_host (load vector or nodal source, complex128, (n+1)^dim entries; see
+ * rhs_kind) and u_host (the
+ * solution, same size) are host arrays that the caller keeps valid until hh_server_wait
+ * returns for *ticket.  HH_ERR_INVALID if the request is invalid or its footprint exceeds
+ * the budget (it could never be admitted). */
+HH_API hh_status hh_server_submit(hh_server* s, const hh_request* req, const void* rhs_host, void* u_host,
+                                  long long* ticket);
+
+/* Wait for a request: returns its solve status and fills info (may be NULL), the time
+ * from submission to completion and the time it spent queued (seconds; may be NULL).  A
+ * ticket can be waited for once. */
+HH_API hh_status hh_server_wait(hh_server* s, long long ticket, hh_info* info, double* latency_s, double* queue_s);
+
+HH_API hh_status hh_server_get_stats(hh_server* s, hh_server_stats* out);
+
+/* Finish every queued and running request, then free all problems and stop the workers. */
+HH_API void hh_server_destroy(hh_server* s);
 
 HH_API const char* hh_status_string(hh_status s);
 HH_API const char* hh_last_error(void);

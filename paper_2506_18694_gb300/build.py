@@ -55,7 +55,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     if failed:
         raise RuntimeError("nvcc failed for: " + ", ".join(failed))
     tmp = LIB + ".tmp"
-    link = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
+    link = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lpthread"]
     if verbose:
         print(" ".join(link), flush=True)
     subprocess.run(link, check=True)

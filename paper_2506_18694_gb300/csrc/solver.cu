@@ -227,7 +227,7 @@ hh_status build_tables(hh_problem* p, Hier& H) {
             for (int b = 0; b < nb; ++b) tab[((size_t)role * L + l) * nb + b] = make_pcoef<T>(p, role, p->lv[l], b);
     const size_t bytes = tab.size() * sizeof(PCoef<T>);
     H.pc_host.assign((const unsigned char*)tab.data(), (const unsigned char*)tab.data() + bytes);
-    HH_TRY(dmalloc(p, &H.pc, bytes));
+    if (!H.pc) HH_TRY(dmalloc(p, &H.pc, bytes));  // kept when the parameters change
     HH_CUDA(cudaMemcpyAsync(H.pc, tab.data(), bytes, cudaMemcpyHostToDevice, p->s));
     if (p->grid.dim == 3) {
         const size_t per = (size_t)hh::kClass3 * hh::kClass3Len;
@@ -238,7 +238,7 @@ hh_status build_tables(hh_problem* p, Hier& H) {
                     const size_t e = ((size_t)role * L + l) * nb + b;
                     hh::boundary_weights3<T>(w3.data() + e * per, tab[e], p->lv[l], p->o.omega);
                 }
-        HH_TRY(dmalloc(p, &H.bw3, w3.size() * sizeof(Cx<T>)));
+        if (!H.bw3) HH_TRY(dmalloc(p, &H.bw3, w3.size() * sizeof(Cx<T>)));
         HH_CUDA(cudaMemcpyAsync(H.bw3, w3.data(), w3.size() * sizeof(Cx<T>), cudaMemcpyHostToDevice, p->s));
     }
     HH_CUDA(cudaStreamSynchronize(p->s));
@@ -1184,6 +1184,40 @@ hh_status hh_create_batch(const hh_grid* grid, int nb, const double* k, const do
     return HH_OK;
 }
 
+hh_status hh_set_params(hh_problem* p, const double* k, const double* delta, const double* delta_hat) {
+    if (!p) return fail(HH_ERR_INVALID, "null problem");
+    HH_TRY(check_args(&p->grid, p->nb, k, delta, delta_hat, p->bc, &p->o));
+    HH_CUDA(cudaStreamSynchronize(p->s));
+    p->k.assign(k, k + p->nb);
+    p->delta.assign(delta, delta + p->nb);
+    p->dh.assign(delta_hat, delta_hat + p->nb);
+    p->max_nhss = 0;
+    for (int b = 0; b < p->nb; ++b) {
+        p->nhss[b] = n_hss(k[b], p->o.theta);
+        p->max_nhss = std::max(p->max_nhss, p->nhss[b]);
+    }
+    HH_CUDA(cudaMemcpyAsync(p->d_nhss, p->nhss.data(), sizeof(int) * p->nb, cudaMemcpyHostToDevice, p->s));
+    HH_TRY(build_tables<float>(p, p->hier[HH_C64]));
+    HH_TRY(build_tables<double>(p, p->hier[HH_C128]));
+    // the preconditioner graphs hold the old coefficients and HSS lengths
+    for (int q = 0; q < 2; ++q)
+        if (p->hier[q].graph) {
+            cudaGraphExecDestroy(p->hier[q].graph);
+            p->hier[q].graph = nullptr;
+        }
+    return HH_OK;
+}
+
+hh_status hh_prepare(hh_problem* p) {
+    if (!p) return fail(HH_ERR_INVALID, "null problem");
+    HH_TRY(join_in(p));
+    HH_CUDA(cudaMemsetAsync(p->r, 0, (size_t)p->nb * p->N * 16, p->s));
+    HH_TRY(precondition_async(p, p->r, p->Z));
+    HH_TRY(join_out(p));
+    HH_CUDA(cudaStreamSynchronize(p->s));
+    return HH_OK;
+}
+
 hh_status hh_create_problem(const hh_grid* grid, double k, double delta, double delta_hat, const int* bc,
                             const hh_options* opts, void* cuda_stream, hh_problem** out) {
     return hh_create_batch(grid, 1, &k, &delta, &delta_hat, bc, opts, cuda_stream, out);
@@ -1241,7 +1275,8 @@ hh_status hh_solve(hh_problem* p, const void* rhs, double tol, void* u, const vo
     return st;
 }
 
-hh_status hh_solve_host(hh_problem* p, const void* rhs_host, double tol, void* u_host, hh_info* info) {
+static hh_status solve_host_impl(hh_problem* p, const void* rhs_host, bool nodal, double tol, void* u_host,
+                                 hh_info* info) {
     if (!p || !rhs_host || !u_host) return fail(HH_ERR_INVALID, "null argument");
     if (!(tol > 0)) return fail(HH_ERR_INVALID, "tol must be > 0");
     std::vector<hh_info> local(p->nb);
@@ -1253,9 +1288,13 @@ hh_status hh_solve_host(hh_problem* p, const void* rhs_host, double tol, void* u
     const size_t bytes = (size_t)p->nb * p->N * 16;
     auto t0 = std::chrono::steady_clock::now();
     HH_TRY(join_in(p));
-    // stage the right side through r, then mask into bvec
+    // stage the right side through r, then mask into bvec (nodal source: bvec = M f)
     HH_CUDA(cudaMemcpyAsync(p->r, rhs_host, bytes, cudaMemcpyHostToDevice, p->s));
-    HH_LAUNCH(hh::launch_mask_copy(p->lv[0], p->r, p->bvec, p->nb, p->s));
+    if (nodal) {
+        HH_TRY(op_axpby<double>(p, 0, R_M, p->r, nullptr, p->bvec, Cx<double>{1, 0}, Cx<double>{0, 0}, p->s));
+    } else {
+        HH_LAUNCH(hh::launch_mask_copy(p->lv[0], p->r, p->bvec, p->nb, p->s));
+    }
     HH_CUDA(cudaMemsetAsync(p->x, 0, bytes, p->s));
     hh_status st = solve_core(p, tol, inf);
     if (st == HH_OK || st == HH_NOT_CONVERGED) {
@@ -1269,6 +1308,14 @@ hh_status hh_solve_host(hh_problem* p, const void* rhs_host, double tol, void* u
     const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     for (int b = 0; b < p->nb; ++b) inf[b].seconds = sec;
     return st;
+}
+
+hh_status hh_solve_host(hh_problem* p, const void* rhs_host, double tol, void* u_host, hh_info* info) {
+    return solve_host_impl(p, rhs_host, false, tol, u_host, info);
+}
+
+hh_status hh_solve_host_nodal(hh_problem* p, const void* f_host, double tol, void* u_host, hh_info* info) {
+    return solve_host_impl(p, f_host, true, tol, u_host, info);
 }
 
 // ---------------------------------------------------------------- building blocks

@@ -23,10 +23,11 @@ OP = {"K": 0, "M": 1, "MGAMMA": 2, "AL": 3, "AR": 4, "B": 5, "BHAT": 6}
 
 EXPORTED = (
     "hh_options_default", "hh_footprint_bytes", "hh_footprint_batch_bytes", "hh_create_problem",
-    "hh_create_batch", "hh_batch_size", "hh_autotune", "hh_destroy", "hh_solve",
-    "hh_solve_host", "hh_level_nodes", "hh_apply", "hh_jacobi", "hh_residual_restrict",
+    "hh_create_batch", "hh_batch_size", "hh_autotune", "hh_set_params", "hh_prepare", "hh_destroy", "hh_solve",
+    "hh_solve_host", "hh_solve_host_nodal", "hh_level_nodes", "hh_apply", "hh_jacobi", "hh_residual_restrict",
     "hh_prolong_correct", "hh_vcycle", "hh_hss_rhs", "hh_precondition", "hh_load_vector", "hh_dot",
-    "hh_multidot_noalloc", "hh_status_string", "hh_last_error",
+    "hh_multidot_noalloc", "hh_server_create", "hh_server_submit", "hh_server_wait", "hh_server_get_stats",
+    "hh_server_destroy", "hh_status_string", "hh_last_error",
 )
 
 
@@ -49,6 +50,24 @@ class Info(ctypes.Structure):
         ("outer_its", ctypes.c_int), ("hss_its", ctypes.c_longlong), ("vcycles", ctypes.c_longlong),
         ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
         ("kernel_launches", ctypes.c_longlong),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("grid", Grid), ("k", ctypes.c_double), ("delta", ctypes.c_double), ("delta_hat", ctypes.c_double),
+                ("bc", ctypes.c_int * 6), ("tol", ctypes.c_double), ("rhs_kind", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+        ("queued", ctypes.c_longlong), ("running", ctypes.c_int), ("max_concurrent", ctypes.c_int),
+        ("budget", ctypes.c_size_t), ("held_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
+        ("problems_created", ctypes.c_longlong), ("problems_reused", ctypes.c_longlong),
+        ("problems_evicted", ctypes.c_longlong),
     ]
 
     def as_dict(self):
@@ -83,9 +102,17 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Options), P, ctypes.POINTER(P)]),
         "hh_batch_size": (I, [P]),
         "hh_autotune": (I, [P, I, ctypes.POINTER(ctypes.c_int)]),
+        "hh_set_params": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "hh_prepare": (I, [P]),
+        "hh_server_create": (I, [I, ctypes.c_size_t, ctypes.POINTER(Options), ctypes.POINTER(P)]),
+        "hh_server_submit": (I, [P, ctypes.POINTER(Request), P, P, ctypes.POINTER(ctypes.c_longlong)]),
+        "hh_server_wait": (I, [P, ctypes.c_longlong, ctypes.POINTER(Info), ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "hh_server_get_stats": (I, [P, ctypes.POINTER(ServerStats)]),
+        "hh_server_destroy": (V, [P]),
         "hh_destroy": (V, [P]),
         "hh_solve": (I, [P, P, D, P, P, ctypes.POINTER(Info)]),
         "hh_solve_host": (I, [P, P, D, P, ctypes.POINTER(Info)]),
+        "hh_solve_host_nodal": (I, [P, P, D, P, ctypes.POINTER(Info)]),
         "hh_level_nodes": (ctypes.c_longlong, [P, I]),
         "hh_apply": (I, [P, I, I, I, P, P]),
         "hh_jacobi": (I, [P, I, I, P, P, P]),
@@ -202,6 +229,17 @@ class Problem:
     def __exit__(self, *a):
         self.close()
 
+    def set_params(self, k, delta, delta_hat):
+        """New k, delta, delta_hat for every problem (same grid and options); buffers kept."""
+        ks, ds, dhs = (np.ascontiguousarray(_vec(v, self.nb)) for v in (k, delta, delta_hat))
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(self._lib.hh_set_params(self._p, ks.ctypes.data_as(dp), ds.ctypes.data_as(dp), dhs.ctypes.data_as(dp)))
+        self.k = ks if self.batched else float(ks[0])
+
+    def prepare(self):
+        """Allocate the multigrid buffers and capture the preconditioner graph now."""
+        _check(self._lib.hh_prepare(self._p))
+
     MODES = ("apply", "axpby", "jacobi", "hss_first", "jacobi2_zero", "prolong_jacobi", "resid_restrict")
 
     def autotune(self, precision=None):
@@ -237,15 +275,16 @@ class Problem:
         _check(st, allow_not_converged=True)
         return u, self._info(infos)
 
-    def solve_host(self, rhs: np.ndarray, tol=1e-8, out: np.ndarray | None = None):
+    def solve_host(self, rhs: np.ndarray, tol=1e-8, out: np.ndarray | None = None, nodal=False):
+        """Solve from host arrays (copies included); nodal=True: rhs is the nodal source f."""
         rhs = np.ascontiguousarray(rhs, dtype=np.complex128)
         out = np.empty_like(rhs) if out is None else out
         if rhs.size != self.size(0) or out.size != rhs.size or out.dtype != np.complex128 \
                 or not out.flags.c_contiguous:
             raise ValueError("host vectors must be contiguous complex128 of nb x nodes entries")
         infos = (Info * self.nb)()
-        st = self._lib.hh_solve_host(self._p, rhs.ctypes.data_as(ctypes.c_void_p), float(tol),
-                                     out.ctypes.data_as(ctypes.c_void_p), infos)
+        fn = self._lib.hh_solve_host_nodal if nodal else self._lib.hh_solve_host
+        st = fn(self._p, rhs.ctypes.data_as(ctypes.c_void_p), float(tol), out.ctypes.data_as(ctypes.c_void_p), infos)
         _check(st, allow_not_converged=True)
         return out, self._info(infos)
 
@@ -304,3 +343,65 @@ class Problem:
         _check(self._lib.hh_dot(self._p, _ptr(x, n0), _ptr(y, n0), out))
         vals = [complex(out[2 * b], out[2 * b + 1]) for b in range(self.nb)]
         return vals if self.batched else vals[0]
+
+
+class Server:
+    """Continuous-batching solve server (hh_server_*): submit host right sides of any grid
+    and wavenumber, wait for the solutions.  Solves run concurrently on the device, admitted
+    as worker slots and the device budget allow."""
+
+    def __init__(self, slots=4, budget_bytes=8 << 30, options: Options | None = None):
+        self._lib = load_library()
+        self.options = options or default_options()
+        out = ctypes.c_void_p()
+        _check(self._lib.hh_server_create(int(slots), int(budget_bytes), ctypes.byref(self.options),
+                                          ctypes.byref(out)))
+        self._s = out
+        self._pending = {}
+
+    def submit(self, dim, n, k, delta, delta_hat, bc, rhs: np.ndarray, tol=1e-8, nodal=False) -> int:
+        """Queue a solve of B u = rhs (complex128 load vector, or with nodal=True the nodal
+        source f and b = M f; (n+1)^dim entries); returns a ticket."""
+        rhs = np.ascontiguousarray(rhs, dtype=np.complex128)
+        if rhs.size != (n + 1) ** dim:
+            raise ValueError("right side has the wrong number of entries")
+        u = np.empty_like(rhs)
+        bcs = list(bc) + [0] * (6 - len(bc))
+        req = Request(Grid(dim, n), float(k), float(delta), float(delta_hat), (ctypes.c_int * 6)(*bcs), float(tol),
+                      1 if nodal else 0)
+        t = ctypes.c_longlong()
+        _check(self._lib.hh_server_submit(self._s, ctypes.byref(req), rhs.ctypes.data_as(ctypes.c_void_p),
+                                          u.ctypes.data_as(ctypes.c_void_p), ctypes.byref(t)))
+        self._pending[t.value] = (rhs, u)  # keep the host arrays alive until waited for
+        return t.value
+
+    def wait(self, ticket):
+        """(u, info, latency_s, queue_s) of a submitted request."""
+        info = Info()
+        lat, qs = ctypes.c_double(), ctypes.c_double()
+        st = self._lib.hh_server_wait(self._s, ticket, ctypes.byref(info), ctypes.byref(lat), ctypes.byref(qs))
+        _, u = self._pending.pop(ticket, (None, None))
+        _check(st, allow_not_converged=True)
+        return u, info, lat.value, qs.value
+
+    def stats(self) -> dict:
+        out = ServerStats()
+        _check(self._lib.hh_server_get_stats(self._s, ctypes.byref(out)))
+        return out.as_dict()
+
+    def close(self):
+        if getattr(self, "_s", None):
+            self._lib.hh_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

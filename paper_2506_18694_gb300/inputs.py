@@ -131,3 +131,49 @@ def batch_workload(name: str = "2d_batch64_n256", delta_hat: str | float = "k") 
     dhs = ks if delta_hat == "k" else tuple(float(delta_hat) for _ in ks)
     return BatchWorkload(name, 2, 256, ks, tuple(s[1] for s in src), tuple(s[2] for s in src), 0.0, dhs,
                          (SOMMERFELD,) * 4)
+
+
+@dataclass(frozen=True)
+class ServeRequest:
+    """One request of the serving workload: its grid, wavenumber, source and arrival time."""
+
+    dim: int
+    n: int
+    k: float
+    delta: float
+    delta_hat: float
+    bc: tuple
+    centre: tuple
+    amplitude: complex
+    arrival: float = 0.0
+    sigma: float = 0.05
+
+    @property
+    def nodes(self) -> int:
+        return (self.n + 1) ** self.dim
+
+    def source(self) -> np.ndarray:
+        return gaussian_source(self.dim, self.n, self.centre, self.sigma, self.amplitude)
+
+
+def serving_requests(count: int = 1000, seed: int = 5, rate: float = 1.0, delta_hat: str | float = "k"):
+    """Requests of the serving workload: half 2D with n log-uniform in [64, 1024], half 3D
+    with n log-uniform in [32, 96], n rounded to a multiple of 8; k uniform in [10, 160]
+    capped at 2 pi n / 10 (at least 10 points per wavelength); Gaussian sources (sigma
+    0.05) at uniform centres with complex normal amplitudes; Poisson arrivals at `rate`
+    per second.  2D: Sommerfeld on all sides; 3D: u = 0 on z = 0, Sommerfeld elsewhere."""
+    rng = np.random.default_rng(seed)
+    out, t = [], 0.0
+    for _ in range(count):
+        dim = 2 if rng.uniform() < 0.5 else 3
+        lo, hi = (64, 1024) if dim == 2 else (32, 96)
+        n = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi))) / 8.0)) * 8
+        n = min(max(n, lo), hi)
+        k = float(min(rng.uniform(10.0, 160.0), 2.0 * np.pi * n / 10.0))
+        bc = (SOMMERFELD,) * 4 if dim == 2 else (SOMMERFELD,) * 4 + (DIRICHLET, SOMMERFELD)
+        centre = tuple(float(v) for v in rng.uniform(0.0, 1.0, size=dim))
+        amp = complex(rng.standard_normal(), rng.standard_normal())
+        t += rng.exponential(1.0 / rate)
+        dh = k if delta_hat == "k" else float(delta_hat)
+        out.append(ServeRequest(dim, n, k, 0.0, dh, bc, centre, amp, t))
+    return out

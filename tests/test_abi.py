@@ -97,3 +97,14 @@ def test_invalid_batches_rejected_on_host(libhh, dim, n, ks, ds, dhs, nb):
 def test_status_strings(libhh):
     for s in (0, 1, -1, -2, -3, -4, -5):
         assert libhh.hh_status_string(s)
+
+
+def test_server_validation_on_host(libhh):
+    """Argument checks of the solve server that run before any device work."""
+    o = hh.default_options()
+    out = ctypes.c_void_p(1234)
+    assert libhh.hh_server_create(0, 1 << 30, ctypes.byref(o), ctypes.byref(out)) == -1 and not out.value
+    assert libhh.hh_server_create(2, 0, ctypes.byref(o), ctypes.byref(out)) == -1 and not out.value
+    bad = hh.default_options(levels=20)
+    assert libhh.hh_server_create(2, 1 << 30, ctypes.byref(bad), ctypes.byref(out)) == -1
+    assert libhh.hh_last_error()
