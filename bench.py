@@ -450,13 +450,13 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
 
 def measure_serving(hh, inputs, torch, count, slots=4, load=0.8):
     """The serving workload (mixed 2D/3D grids and wavenumbers, nodal Gaussian sources,
-    delta_hat = k, tol 1e-8, FGMRES restart 60) through the solve server.  Pass 1 runs the
+    delta_hat = k, tol 1e-8, FGMRES restart 60, at most 3000 iterations) through the solve server.  Pass 1 runs the
     requests one at a time (1 slot) and gives the sequential service capacity; pass 2
     replays them with Poisson arrivals at `load` times that capacity into a server with
     `slots` slots (latency); pass 3 queues them all at once (throughput with overlap)."""
     reqs = inputs.serving_requests(count)
     srcs = [r.source() for r in reqs]
-    opts = hh.default_options(precision=hh.HH_C64, restart=60)
+    opts = hh.default_options(precision=hh.HH_C64, restart=60, max_outer=3000)
     budget = int(torch.cuda.mem_get_info()[0] * 0.6)
 
     def run(slots, arrivals):
