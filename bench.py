@@ -385,11 +385,11 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
     big.close()
     ach = 24 * Nb / t_b / 1e9
     if w.dim == 2:
-        kname, prof, src = ("k_march2<float, JACOBI, 8> (scaled-Jacobi sweep)", "jacobi_2d_4097sq_c64.md",
+        kname, prof, src = ("k_march2p<float, JACOBI, 8> (scaled-Jacobi sweep, persistent)", "jacobi_2d_4097sq_c64.md",
                             "paper_2506_18694_gb300/csrc/march2.cu")
         size = "4097^2 nodes (3 x 134 MB vectors > L2)"
     else:
-        kname, prof, src = ("k_march3<float, JACOBI, 8> (scaled-Jacobi sweep)", "jacobi_3d_257cube_c64.md",
+        kname, prof, src = ("k_march3<float, JACOBI, 4> (scaled-Jacobi sweep)", "jacobi_3d_257cube_c64.md",
                             "paper_2506_18694_gb300/csrc/march3.cu")
         size = "257^3 nodes (3 x 136 MB vectors > L2)"
     out["roofline"] = {"bound": "hbm", "kernel": kname,
@@ -450,8 +450,9 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
 
 def measure_serving(hh, inputs, torch, count, slots=4, load=0.8):
     """The serving workload (mixed 2D/3D grids and wavenumbers, nodal Gaussian sources,
-    delta_hat = k, tol 1e-8, FGMRES restart 60, at most 3000 iterations) through the solve server.  Pass 1 runs the
-    requests one at a time (1 slot) and gives the sequential service capacity; pass 2
+    delta_hat = k, tol 1e-8, FGMRES restart 60, at most 3000 iterations) through the
+    solve server.  Pass 1 runs the requests one at a time (1 slot) and gives the
+    sequential service capacity; pass 2
     replays them with Poisson arrivals at `load` times that capacity into a server with
     `slots` slots (latency); pass 3 queues them all at once (throughput with overlap)."""
     reqs = inputs.serving_requests(count)
