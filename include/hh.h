@@ -111,6 +111,11 @@ typedef struct {
     int tile_rows;       /* rows (2D) / z-planes (3D) per warp tile of the stencil kernels:   */
                          /* 2, 4 or 8; 0 = chosen from the grid size                          */
     int autotune;        /* 1: run hh_autotune for `precision` when the problem is created    */
+    int fuse_sweeps;     /* 1: in 2D, on levels of at most 600000 nodes (all problems of a     */
+                         /* batch together), two consecutive Jacobi sweeps of the cycle (the  */
+                         /* HSS right side with the first two pre-sweeps, the prolongation    */
+                         /* with the first two post-sweeps) run as one kernel; same result    */
+                         /* bit for bit as 0 (one kernel per sweep)                           */
 } hh_options;
 
 typedef struct {
@@ -127,7 +132,8 @@ typedef struct hh_problem hh_problem;
 
 /* Defaults: theta 1, 4 levels, V(2,2), 8 coarse sweeps, omega automatic, restart 30,
  * max_outer 1000, complex FP32 V-cycles, graphs and programmatic launch on,
- * coarse_cluster_nodes 100000, tile shapes from the grid size (no autotuning). */
+ * coarse_cluster_nodes 100000, tile shapes from the grid size (no autotuning), fused
+ * two-sweep kernels. */
 HH_API void hh_options_default(hh_options* opts);
 
 /* Device bytes a problem with this grid and these options allocates for its solves

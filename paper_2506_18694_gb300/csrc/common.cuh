@@ -39,8 +39,10 @@ template <typename T> __device__ __forceinline__ void st(vec2<T>* p, long long i
 template <typename T> __device__ __forceinline__ Cx<T> operator+(Cx<T> a, Cx<T> b) { return {a.re + b.re, a.im + b.im}; }
 template <typename T> __device__ __forceinline__ Cx<T> operator-(Cx<T> a, Cx<T> b) { return {a.re - b.re, a.im - b.im}; }
 template <typename T> __device__ __forceinline__ Cx<T> operator*(T s, Cx<T> a) { return {s * a.re, s * a.im}; }
+// Complex product with the fused multiply-adds written out, so that the rounding does not
+// depend on how the compiler contracts the expression in a given kernel.
 template <typename T> __device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
-    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+    return {fma(a.re, b.re, -(a.im * b.im)), fma(a.re, b.im, a.im * b.re)};
 }
 // a + s * b with real s
 template <typename T> __device__ __forceinline__ Cx<T> fma_r(T s, Cx<T> b, Cx<T> a) {
@@ -51,7 +53,7 @@ template <typename T> __device__ __forceinline__ Cx<T> fma_c(Cx<T> c, Cx<T> b, C
     return {fma(c.re, b.re, fma(-c.im, b.im, a.re)), fma(c.re, b.im, fma(c.im, b.re, a.im))};
 }
 template <typename T> __device__ __forceinline__ Cx<T> cinv(Cx<T> a) {
-    T d = a.re * a.re + a.im * a.im;
+    T d = fma(a.re, a.re, a.im * a.im);
     T s = T(1) / d;
     return {a.re * s, -a.im * s};
 }

@@ -94,7 +94,11 @@ enum MarchMode {
     M_JACOBI2_ZERO = 4,   // two sweeps from x = 0 reading only z:  x1 = omega D^{-1} z,
                           // y = x1 + omega D^{-1} (z - op x1)
     M_PROLONG_JACOBI = 5, // x~ = x + P ec;  y = x~ + omega D^{-1} (z - op x~)
-    M_RESID_RESTRICT = 6  // y (coarse) = P^T (z - op x)
+    M_RESID_RESTRICT = 6, // y (coarse) = P^T (z - op x)
+    // two sweeps in one pass (2D): the second sweep's operator is pc2 / c02 (A_L)
+    M_PROLONG_JACOBI2 = 7,  // x~ = x + P ec;  x1 = x~ + omega D^{-1} (z - op x~);  y = x1 + omega D^{-1} (z - op x1)
+    M_HSS_FIRST2 = 8        // rhs = alpha (op x) + beta z;  x1 = omega D^{-1} rhs;  y = rhs,
+                            // y2 = x1 + omega D^{-1} (rhs - A_L x1)
 };
 
 // Coefficients of one operator on one level for one problem of a batch (a device table
@@ -136,6 +140,8 @@ template <typename T> struct MArgs {
     const PCoef<T>* pc;  // device coefficient table of this operator and level (nullptr: c0)
     PCoef<T> c0;         // the coefficients of a batch of one, passed by value
     const Cx<T>* bw3;    // 3D: device boundary-class weights, problem b at b * kClass3 * kClass3Len
+    const PCoef<T>* pc2; // second operator of the fused two-sweep modes (nullptr: c02)
+    PCoef<T> c02;
     const vec2<T>* x;    // stencil input (ignored for M_JACOBI2_ZERO; nullptr = 0 when xzero)
     const vec2<T>* z;    // right side / second vector
     const vec2<T>* ec;   // coarse correction (M_PROLONG_JACOBI)

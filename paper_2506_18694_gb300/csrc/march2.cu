@@ -31,30 +31,53 @@ __device__ __forceinline__ int bclass2(int tx, int ty) {
     return c - (c > 4);
 }
 
-// x + P e_c at node (ic, rc) inside the grid and not on a Dirichlet side: bilinear
-// interpolation of the coarse correction (coarse Dirichlet nodes carry no basis function).
+// Whether node (i, r) of the tile holds no unknown: outside the grid or on a Dirichlet side.
 template <typename T>
-__device__ __forceinline__ Cx<T> prolonged2(const MArgs<T>& a, const VPtrs<T>& v, int ic, int rc, long long p) {
-    const int nc = a.g.n >> 1, nnc = nc + 1;
-    const int I0 = ic >> 1, J0 = rc >> 1;
-    const bool oi = ic & 1, oj = rc & 1;
-    Cx<T> e = cx<T>(0, 0);
+__device__ __forceinline__ bool col_void(const MArgs<T>& a, int i) {
+    return i < 0 || i > a.g.n || (i == 0 && a.g.dir[0]) || (i == a.g.n && a.g.dir[1]);
+}
+template <typename T>
+__device__ __forceinline__ bool row_void(const MArgs<T>& a, int r) {
+    return r < 0 || r > a.g.n || (r == 0 && a.g.dir[2]) || (r == a.g.n && a.g.dir[3]);
+}
+
+// x + P e_c on the NR fine rows rfirst, rfirst + 1, ... of this lane's column ic (P = parity
+// of rfirst), zero where no unknown lives.  Each coarse row the tile touches is read once
+// per lane: the lane at an even fine column takes its coarse value, a lane at an odd column
+// the mean of its own and its right neighbour's (by shuffle; lane 31 reads its second value
+// itself); odd fine rows then average two interpolated coarse rows.  Coarse nodes on a
+// Dirichlet side carry no basis function and count as zero.
+template <typename T, int NR, int P>
+__device__ __forceinline__ void prolong_rows(const MArgs<T>& a, const VPtrs<T>& v, int ic, int rfirst, bool cvoid,
+                                             Cx<T>* out) {
+    const int n = a.g.n, nc = n >> 1, nnc = nc + 1;
+    const int lane = threadIdx.x & 31;
+    const int I = ic >> 1;
+    const int I1 = I + 1 <= nc ? I + 1 : nc;
+    const bool odd = ic & 1;
+    const bool v0 = (I == 0 && a.g.dir[0]) || (I == nc && a.g.dir[1]);
+    const bool v1 = (I1 == 0 && a.g.dir[0]) || (I1 == nc && a.g.dir[1]);
+    constexpr int NCR = ((P + NR) >> 1) + 1;
+    const int J0 = rfirst >> 1;  // floor(rfirst / 2)
+    Cx<T> ex[NCR];
 #pragma unroll
-    for (int bj = 0; bj < 2; ++bj) {
-        if (bj == 1 && !oj) break;
-        const int J = J0 + bj;
-        if ((J == 0 && a.g.dir[2]) || (J == nc && a.g.dir[3])) continue;
-        const T wj = oj ? T(0.5) : T(1);
-#pragma unroll
-        for (int ai = 0; ai < 2; ++ai) {
-            if (ai == 1 && !oi) break;
-            const int I = I0 + ai;
-            if ((I == 0 && a.g.dir[0]) || (I == nc && a.g.dir[1])) continue;
-            const T w = oi ? T(0.5) * wj : wj;
-            e = fma_r(w, ld<T>(v.ec, (long long)J * nnc + I), e);
-        }
+    for (int q = 0; q < NCR; ++q) {
+        const int J = J0 + q;
+        const bool jv = J < 0 || J > nc || (J == 0 && a.g.dir[2]) || (J == nc && a.g.dir[3]);
+        const long long row = (long long)clampi(J, 0, nc) * nnc;
+        const Cx<T> c0 = (jv || v0) ? cx<T>(0, 0) : ld<T>(v.ec, row + I);
+        Cx<T> c1 = shfl_dn(c0);
+        if (lane == 31) c1 = (jv || v1) ? cx<T>(0, 0) : ld<T>(v.ec, row + I1);
+        ex[q] = odd ? T(0.5) * (c0 + c1) : c0;
     }
-    return ld<T>(v.x, p) + e;
+#pragma unroll
+    for (int t = 0; t < NR; ++t) {
+        const int r = rfirst + t;
+        const long long p = (long long)clampi(r, 0, n) * a.g.nn + ic;
+        const int lq = (P + t) >> 1;
+        const Cx<T> e = ((P + t) & 1) == 0 ? ex[lq] : T(0.5) * (ex[lq] + ex[lq + 1]);
+        out[t] = (cvoid || row_void(a, r)) ? cx<T>(0, 0) : ld<T>(v.x, p) + e;
+    }
 }
 
 // One warp tile: a strip of 30 output columns (lanes 1..30; lanes 0 and 31 are the halo)
@@ -75,16 +98,6 @@ template <typename T, int MODE, int ROWS> struct Tile2 {
     Cx<T> zv[NZ];  // right side / second vector on the output rows
 };
 
-// Whether node (i, r) of the tile holds no unknown: outside the grid or on a Dirichlet side.
-template <typename T>
-__device__ __forceinline__ bool col_void(const MArgs<T>& a, int i) {
-    return i < 0 || i > a.g.n || (i == 0 && a.g.dir[0]) || (i == a.g.n && a.g.dir[1]);
-}
-template <typename T>
-__device__ __forceinline__ bool row_void(const MArgs<T>& a, int r) {
-    return r < 0 || r > a.g.n || (r == 0 && a.g.dir[2]) || (r == a.g.n && a.g.dir[3]);
-}
-
 template <typename T, int MODE, int ROWS>
 __device__ __forceinline__ void tile_load(const MArgs<T>& a, const VPtrs<T>& v, int strip, int cy,
                                           Tile2<T, MODE, ROWS>& tl) {
@@ -96,6 +109,8 @@ __device__ __forceinline__ void tile_load(const MArgs<T>& a, const VPtrs<T>& v, 
     const int rfirst = TL::RR ? 2 * base - 2 : base - 1;
     const int ic = clampi(i, 0, n);
     const bool cvoid = col_void(a, i);
+    // (ROWS is even, so the first stencil row base - 1 is odd)
+    if (MODE == M_PROLONG_JACOBI) prolong_rows<T, TL::NR, 1>(a, v, ic, rfirst, cvoid, tl.fv);
 #pragma unroll
     for (int t = 0; t < TL::NR; ++t) {
         const int r = rfirst + t;
@@ -104,9 +119,7 @@ __device__ __forceinline__ void tile_load(const MArgs<T>& a, const VPtrs<T>& v, 
         const bool vd = cvoid || row_void(a, r);
         if (MODE == M_JACOBI2_ZERO) {
             tl.bv[t] = ld<T>(v.z, p);
-        } else if (MODE == M_PROLONG_JACOBI) {
-            tl.fv[t] = vd ? cx<T>(0, 0) : prolonged2(a, v, ic, rc, p);
-        } else {
+        } else if (MODE != M_PROLONG_JACOBI) {
             tl.fv[t] = (a.xzero || vd) ? cx<T>(0, 0) : ld<T>(v.x, p);
         }
     }
@@ -224,6 +237,175 @@ __device__ __forceinline__ void tile_compute(const MArgs<T>& a, const PCoef<T>& 
             st<T>(v.y, p, fma_c(dinv_w, b - ax, fv[t]));
         }
     }
+}
+
+// ---- two sweeps in one pass ----
+// Tile of the fused modes: 28 output columns (lanes 2..29) and ROWS output rows.  The field
+// is loaded on ROWS + 4 rows; the first stage (a sweep, or the HSS right side and its
+// pointwise first sweep) is formed on the ROWS + 2 rows and lanes 1..30 around the outputs,
+// the second sweep on the outputs.  Every node's arithmetic is that of the one-sweep modes,
+// so the result equals the two separate passes bit for bit.
+template <typename T, int ROWS> struct TileF {
+    static constexpr int NR = ROWS + 4;
+    Cx<T> fv[NR];      // field: x + P ec (PROLONG_JACOBI2) or u (HSS_FIRST2)
+    Cx<T> zv[NR - 2];  // b (PROLONG_JACOBI2) or r (HSS_FIRST2) on rows 1..NR-2
+};
+
+template <typename T, int MODE, int ROWS>
+__device__ __forceinline__ void tilef_load(const MArgs<T>& a, const VPtrs<T>& v, int strip, int cy,
+                                           TileF<T, ROWS>& tl) {
+    constexpr int NR = TileF<T, ROWS>::NR;
+    const int lane = threadIdx.x & 31;
+    const int n = a.g.n;
+    const int i = strip * 28 + lane - 2;
+    const int rfirst = cy * ROWS - 2;
+    const int ic = clampi(i, 0, n);
+    const bool cvoid = col_void(a, i);
+    if (MODE == M_PROLONG_JACOBI2) {
+        prolong_rows<T, NR, 0>(a, v, ic, rfirst, cvoid, tl.fv);  // (first row cy * ROWS - 2 is even)
+    } else {
+#pragma unroll
+        for (int t = 0; t < NR; ++t) {
+            const int r = rfirst + t;
+            const long long p = (long long)clampi(r, 0, n) * a.g.nn + ic;
+            tl.fv[t] = (a.xzero || cvoid || row_void(a, r)) ? cx<T>(0, 0) : ld<T>(v.x, p);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NR - 2; ++t) tl.zv[t] = ld<T>(v.z, (long long)clampi(rfirst + 1 + t, 0, n) * a.g.nn + ic);
+}
+
+// op f at row t of a tile column (interior weights or the node's boundary class), with
+// omega D^{-1} of the record's opd.
+template <typename T>
+__device__ __forceinline__ void stencil_node2(const PCoef<T>& c, Cx<T> fm, Cx<T> f0, Cx<T> fp, Cx<T> lm, Cx<T> l0,
+                                              Cx<T> lp, Cx<T> rm, Cx<T> r0, Cx<T> rp, bool fast, int tx, int ty,
+                                              Cx<T>& ax, Cx<T>& dinv_w) {
+    if (fast) {
+        const Cx<T> edge = (l0 + r0) + (fm + fp);
+        const Cx<T> diag = (lm + rm) + (lp + rp);
+        ax = fma_c(c.iw[2], diag, fma_c(c.iw[1], edge, cmul(c.iw[0], f0)));
+        dinv_w = c.wdinv;
+    } else {
+        const int q = bclass2(tx, ty);
+        const Cx<T> hx = l0 + r0;
+        const Cx<T> vy = fm + fp;
+        const Cx<T> dg = (lm + rm) + (lp + rp);
+        ax = fma_c(c.bw[q][3], dg, fma_c(c.bw[q][2], vy, fma_c(c.bw[q][1], hx, cmul(c.bw[q][0], f0))));
+        dinv_w = c.bdinv[q];
+    }
+}
+
+template <typename T, int MODE, int ROWS>
+__device__ __forceinline__ void tilef_compute(const MArgs<T>& a, const PCoef<T>& c, const PCoef<T>& cl,
+                                              const VPtrs<T>& v, int strip, int cy, TileF<T, ROWS>& tl) {
+    constexpr int NR = TileF<T, ROWS>::NR;
+    const int lane = threadIdx.x & 31;
+    const int n = a.g.n;
+    const int i = strip * 28 + lane - 2;
+    const int rfirst = cy * ROWS - 2;
+    const int ic = clampi(i, 0, n);
+    const bool col_in = (i >= 0 && i <= n);
+    const bool col_inner = (i >= 1 && i <= n - 1);
+    const bool cvoid = col_void(a, i);
+    const int tx = ic == 0 ? 0 : (ic == n ? 2 : 1);
+    const Cx<T>* fv = tl.fv;
+    Cx<T> lf[NR], rg[NR];
+#pragma unroll
+    for (int t = 0; t < NR; ++t) {
+        lf[t] = shfl_up(fv[t]);
+        rg[t] = shfl_dn(fv[t]);
+    }
+    // first stage on rows 1..NR-2: x1, and the right side of the second sweep
+    Cx<T> x1[NR], b2[NR];
+    x1[0] = x1[NR - 1] = b2[0] = b2[NR - 1] = cx<T>(0, 0);
+    const Cx<T> alpha = a.use_pc_ab ? c.alpha : a.alpha, beta = a.use_pc_ab ? c.beta : a.beta;
+#pragma unroll
+    for (int t = 1; t < NR - 1; ++t) {
+        const int j = rfirst + t;
+        const int jc = clampi(j, 0, n);
+        const bool fast = col_inner && j >= 1 && j <= n - 1;
+        const int ty = jc == 0 ? 0 : (jc == n ? 2 : 1);
+        Cx<T> ax, dinv_w;
+        stencil_node2(c, fv[t - 1], fv[t], fv[t + 1], lf[t - 1], lf[t], lf[t + 1], rg[t - 1], rg[t], rg[t + 1], fast,
+                      tx, ty, ax, dinv_w);
+        const bool vd = cvoid || row_void(a, j);
+        if (MODE == M_PROLONG_JACOBI2) {
+            b2[t] = tl.zv[t - 1];
+            x1[t] = vd ? cx<T>(0, 0) : fma_c(dinv_w, tl.zv[t - 1] - ax, fv[t]);
+        } else {
+            const Cx<T> rhs = fma_c(alpha, ax, cmul(beta, tl.zv[t - 1]));
+            b2[t] = vd ? cx<T>(0, 0) : rhs;
+            x1[t] = vd ? cx<T>(0, 0) : cmul(dinv_w, rhs);
+        }
+    }
+    // second sweep (operator cl) on the output rows 2..NR-3
+#pragma unroll
+    for (int t = 0; t < NR; ++t) {
+        lf[t] = shfl_up(x1[t]);
+        rg[t] = shfl_dn(x1[t]);
+    }
+#pragma unroll
+    for (int t = 2; t < NR - 2; ++t) {
+        const int j = rfirst + t;
+        const bool row_in = (j >= 0 && j <= n);
+        const int jc = clampi(j, 0, n);
+        const bool fast = col_inner && j >= 1 && j <= n - 1;
+        const int ty = jc == 0 ? 0 : (jc == n ? 2 : 1);
+        Cx<T> ax, dinv_w;
+        stencil_node2(cl, x1[t - 1], x1[t], x1[t + 1], lf[t - 1], lf[t], lf[t + 1], rg[t - 1], rg[t], rg[t + 1], fast,
+                      tx, ty, ax, dinv_w);
+        if (!(lane >= 2 && lane <= 29 && col_in && row_in)) continue;
+        const long long p = (long long)jc * a.g.nn + ic;
+        const bool masked = !fast && (cvoid || row_void(a, j));
+        if (masked) {
+            st<T>(v.y, p, cx<T>(0, 0));
+            if (MODE == M_HSS_FIRST2) st<T>(v.y2, p, cx<T>(0, 0));
+            continue;
+        }
+        const Cx<T> x2 = fma_c(dinv_w, b2[t] - ax, x1[t]);
+        if (MODE == M_PROLONG_JACOBI2) {
+            st<T>(v.y, p, x2);
+        } else {
+            st<T>(v.y, p, b2[t]);
+            st<T>(v.y2, p, x2);
+        }
+    }
+}
+
+// grid (strips of 28 columns, ceil(chunks / 4), problems)
+template <typename T, int MODE, int ROWS, bool BATCH>
+__global__ void __launch_bounds__(128) k_march2f(const __grid_constant__ MArgs<T> a, int chunks) {
+    pdl_entry();
+    const int b = BATCH ? (int)blockIdx.z : 0;
+    const int cy = blockIdx.y * 4 + (threadIdx.x >> 5);
+    if (cy >= chunks) return;
+    if (BATCH && problem_skipped(a, b)) return;
+    const PCoef<T>& c = BATCH ? a.pc[b] : a.c0;
+    const PCoef<T>& cl = BATCH ? a.pc2[b] : a.c02;
+    const VPtrs<T> v = problem_ptrs(a, b, false);
+    TileF<T, ROWS> tl;
+    tilef_load<T, MODE, ROWS>(a, v, blockIdx.x, cy, tl);
+    tilef_compute<T, MODE, ROWS>(a, c, cl, v, blockIdx.x, cy, tl);
+}
+
+template <typename T, int MODE>
+static cudaError_t gof(MArgs<T> a, cudaStream_t s) {
+    a.h = T(a.g.h);
+    a.ih = T(1.0 / a.g.h);
+    if (a.pc && !a.pc2) return cudaErrorInvalidValue;
+    const int strips = (a.g.nn + 27) / 28;
+    int rows = ((long long)strips * ((a.g.nn + 3) / 4) * a.nb >= 152LL * 24) ? 4 : 2;
+    if (a.tile_rows == 2 || a.tile_rows == 4) rows = a.tile_rows;
+    const int chunks = (a.g.nn + rows - 1) / rows;
+    const dim3 grd((unsigned)strips, (unsigned)((chunks + 3) / 4), (unsigned)a.nb);
+    if (a.pc) {
+        if (rows == 4) return klaunch(k_march2f<T, MODE, 4, true>, grd, dim3(128), 0, s, 1, a, chunks);
+        return klaunch(k_march2f<T, MODE, 2, true>, grd, dim3(128), 0, s, 1, a, chunks);
+    }
+    if (a.nb != 1) return cudaErrorInvalidValue;
+    if (rows == 4) return klaunch(k_march2f<T, MODE, 4, false>, grd, dim3(128), 0, s, 1, a, chunks);
+    return klaunch(k_march2f<T, MODE, 2, false>, grd, dim3(128), 0, s, 1, a, chunks);
 }
 
 // One tile per warp; grid (strips, ceil(chunks / 4), problems).  BATCH = false: a batch of
@@ -435,6 +617,8 @@ cudaError_t launch_march2(int mode, const MArgs<T>& a, cudaStream_t s) {
         case M_JACOBI2_ZERO: return go2<T, M_JACOBI2_ZERO>(a, s);
         case M_PROLONG_JACOBI: return go2<T, M_PROLONG_JACOBI>(a, s);
         case M_RESID_RESTRICT: return go2<T, M_RESID_RESTRICT>(a, s);
+        case M_PROLONG_JACOBI2: return gof<T, M_PROLONG_JACOBI2>(a, s);
+        case M_HSS_FIRST2: return gof<T, M_HSS_FIRST2>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -375,6 +375,23 @@ struct MG {
         return a;
     }
 
+    // arguments of the fused two-sweep modes: role for the first stage, A_L for the second
+    hh::MArgs<T> margs2(int l, int role) const {
+        hh::MArgs<T> a = margs(l, role);
+        if (p->nb == 1) {
+            std::memcpy(&a.c02, H->pc_host.data() + ((size_t)R_AL * p->o.levels + l) * sizeof(PCoef<T>),
+                        sizeof(PCoef<T>));
+        } else {
+            a.pc2 = table(R_AL, l);
+        }
+        return a;
+    }
+
+    // two consecutive sweeps of level l run as one pass (2D): it removes a launch and a trip
+    // through memory but computes the first sweep on a wider halo, which pays while the
+    // level is latency-bound (measured: faster up to 513^2 nodes, slower from 1025^2)
+    bool fused2(int l) const { return d2() && p->o.fuse_sweeps && Nl(l) * p->nb <= 600000; }
+
     hh::Batch batch(int l) const {
         return hh::Batch{p->nb, Nl(l), l + 1 < p->o.levels ? Nl(l + 1) : 0, p->nb == 1 ? -1 : hss_it, p->d_nhss,
                          active_flags(p)};
@@ -387,7 +404,7 @@ struct MG {
         const auto& tab = p->tune[prec];
         int l = 0;
         while ((p->grid.n >> l) != a.g.n) ++l;
-        if (l < (int)tab.size() && tab[l][mode][0] != 0) {
+        if (mode < kModes && l < (int)tab.size() && tab[l][mode][0] != 0) {
             t.tile_rows = tab[l][mode][0];
             t.tile_form = tab[l][mode][1];
         }
@@ -438,6 +455,28 @@ struct MG {
         a.z = b;
         a.y = xout;
         HH_LAUNCH(march(hh::M_PROLONG_JACOBI, a));
+        return HH_OK;
+    }
+    // xout = two sweeps from x~ = x + P ec, in one pass
+    hh_status prolong_jacobi2(int l, V2* x, const V2* ec, const V2* b, V2* xout) {
+        hh::MArgs<T> a = margs2(l, R_AL);
+        a.x = x;
+        a.ec = ec;
+        a.z = b;
+        a.y = xout;
+        HH_LAUNCH(march(hh::M_PROLONG_JACOBI2, a));
+        return HH_OK;
+    }
+    // rhs = c1 A_R u + c2 r and two Jacobi sweeps from 0 on A_L x = rhs, in one pass
+    hh_status hss_first2(const V2* u, const V2* r, V2* rhs, V2* x2) {
+        hh::MArgs<T> a = margs2(0, R_AR);
+        a.x = u;
+        a.xzero = u == nullptr;
+        a.z = r;
+        a.y = rhs;
+        a.y2 = x2;
+        a.use_pc_ab = 1;
+        HH_LAUNCH(march(hh::M_HSS_FIRST2, a));
         return HH_OK;
     }
     // rhs = c1 A_R u + c2 r and the first Jacobi sweep x1 = omega D^{-1} rhs (u == nullptr: u = 0)
@@ -493,14 +532,14 @@ struct MG {
     }
 
     // One V-cycle on level l for right side b from x = 0; result buffer in *out.
-    // xstart: the first pre-smoothing sweep was already done and sits in xstart.
-    hh_status vcycle(int l, const V2* b, V2* xstart, V2** out) {
+    // xstart: the first `done` pre-smoothing sweeps were already done and sit in xstart.
+    hh_status vcycle(int l, const V2* b, V2* xstart, V2** out, int done = 1) {
         const int L = p->o.levels;
         if (l == L - 1) {
             V2* x = (V2*)H->xa[l];
             if (xstart) {
                 x = xstart;
-                HH_TRY(smooth(l, b, p->o.nu_coarse - 1, &x));
+                HH_TRY(smooth(l, b, p->o.nu_coarse - done, &x));
             } else if (p->o.nu_coarse >= 1 && Nl(l) <= p->o.coarse_cluster_nodes && hh::coarse_fits<T>(p->lv[l])) {
                 hh::MArgs<T> a = margs(l, R_AL);
                 a.z = b;
@@ -515,7 +554,7 @@ struct MG {
         V2* x;
         if (xstart) {
             x = xstart;
-            HH_TRY(smooth(l, b, p->o.nu_pre - 1, &x));
+            HH_TRY(smooth(l, b, p->o.nu_pre - done, &x));
         } else {
             HH_TRY(smooth_from_zero(l, b, p->o.nu_pre, &x));
         }
@@ -524,6 +563,11 @@ struct MG {
         HH_TRY(vcycle(l + 1, (const V2*)H->b[l + 1], nullptr, &ec));
         if (p->o.nu_post == 0) {
             HH_LAUNCH(hh::launch_prolong<T>(p->lv[l], ec, x, batch(l), s));
+        } else if (p->o.nu_post >= 2 && fused2(l)) {
+            V2* oth = other(l, x);
+            HH_TRY(prolong_jacobi2(l, x, ec, b, oth));
+            x = oth;
+            HH_TRY(smooth(l, b, p->o.nu_post - 2, &x));
         } else {
             V2* oth = other(l, x);
             HH_TRY(prolong_jacobi(l, x, ec, b, oth));
@@ -534,10 +578,10 @@ struct MG {
         return HH_OK;
     }
 
-    // cycles_per_hss V-cycles for A_L x = b; the first may start from xstart.
-    hh_status mg_solve(const V2* b, V2* xstart, V2** out) {
+    // cycles_per_hss V-cycles for A_L x = b; the first may start from xstart (`done` sweeps).
+    hh_status mg_solve(const V2* b, V2* xstart, V2** out, int done = 1) {
         V2* x;
-        HH_TRY(vcycle(0, b, xstart, &x));
+        HH_TRY(vcycle(0, b, xstart, &x, done));
         const long long N = Nl(0);
         for (int c = 1; c < p->o.cycles_per_hss; ++c) {
             // keep x outside the level-0 ping-pong buffers the next cycle overwrites
@@ -563,6 +607,7 @@ struct MG {
     // buffer that holds problem b's result (its loop may end before the others').
     hh_status hss_loop(std::vector<V2*>* src) {
         const bool fuse = p->o.nu_pre >= 1 && !(p->o.levels == 1 && p->o.nu_coarse == 0);
+        const bool two = fuse && fused2(0) && (p->o.levels > 1 ? p->o.nu_pre : p->o.nu_coarse) >= 2;
         std::vector<V2*> after(p->max_nhss, nullptr);
         V2* u = nullptr;
         for (int it = 0; it < p->max_nhss; ++it) {
@@ -570,8 +615,13 @@ struct MG {
             if (fuse) {
                 // the first pre-smoothing sweep of the fine level is fused with the right side
                 V2* x1 = (u == (V2*)H->xa[0]) ? (V2*)H->xb[0] : (V2*)H->xa[0];
-                HH_TRY(hss_first(u, (const V2*)H->r_lo, (V2*)H->rhs, x1));
-                HH_TRY(mg_solve((const V2*)H->rhs, x1, &u));
+                if (two) {
+                    HH_TRY(hss_first2(u, (const V2*)H->r_lo, (V2*)H->rhs, x1));
+                    HH_TRY(mg_solve((const V2*)H->rhs, x1, &u, 2));
+                } else {
+                    HH_TRY(hss_first(u, (const V2*)H->r_lo, (V2*)H->rhs, x1));
+                    HH_TRY(mg_solve((const V2*)H->rhs, x1, &u));
+                }
             } else {
                 HH_TRY(hss_rhs(u, (const V2*)H->r_lo, (V2*)H->rhs));
                 HH_TRY(mg_solve((const V2*)H->rhs, nullptr, &u));
@@ -1040,6 +1090,7 @@ hh_status check_args(const hh_grid* grid, int nb, const double* k, const double*
     if (o->tile_rows != 0 && o->tile_rows != 2 && o->tile_rows != 4 && o->tile_rows != 8)
         return fail(HH_ERR_INVALID, "tile_rows must be 0, 2, 4 or 8");
     if (o->autotune != 0 && o->autotune != 1) return fail(HH_ERR_INVALID, "autotune must be 0 or 1");
+    if (o->fuse_sweeps != 0 && o->fuse_sweeps != 1) return fail(HH_ERR_INVALID, "fuse_sweeps must be 0 or 1");
     if (!bc) return fail(HH_ERR_INVALID, "null bc");
     for (int s = 0; s < 2 * grid->dim; ++s)
         if (bc[s] != HH_BC_SOMMERFELD && bc[s] != HH_BC_DIRICHLET) return fail(HH_ERR_INVALID, "bad boundary tag");
@@ -1090,6 +1141,7 @@ void hh_options_default(hh_options* o) {
     o->coarse_cluster_nodes = 100000;
     o->tile_rows = 0;
     o->autotune = 0;
+    o->fuse_sweeps = 1;
 }
 
 size_t hh_footprint_batch_bytes(const hh_grid* grid, const hh_options* o, int nb) {
