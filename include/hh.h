@@ -174,15 +174,17 @@ HH_API int hh_batch_size(const hh_problem* p);
 /*
  * Tile-shape autotuner (a service of this library; the paper has none).  Times every
  * candidate tile shape (rows or planes per warp tile, one tile per warp or persistent
- * warps) of each stencil kernel the solver runs on each level in `precision`, and of the
- * FP64 outer operator, on the problem's own scratch buffers, and keeps the fastest for
- * this problem; later solves use them (the preconditioner graph is captured again).
+ * warps) of each stencil kernel the solver runs on each level in `precision`, every
+ * cluster size of the coarsest-level solve, and the FP64 outer operator, on the problem's
+ * own scratch buffers, and keeps the fastest for this problem; later solves use them (the
+ * preconditioner graph is captured again).
  * Every shape gives the same result bit for bit.  Choices are remembered per process for
  * (device, dim, level size, batch size, precision, kernel), so problems of the same shape
- * reuse them without timing.  Blocking.  shapes, if not NULL, receives levels x 7 x 2 ints:
- * for level l and kernel mode m (y = op x, axpby, Jacobi, HSS first step, two Jacobi
- * sweeps from 0, prolongation + Jacobi, residual + restriction), {rows, form} at
- * [(l * 7 + m) * 2], 0 where nothing was tuned.
+ * reuse them without timing.  Blocking.  shapes, if not NULL, receives levels x 10 x 2 ints:
+ * for level l and kernel m (0 y = op x, 1 axpby, 2 Jacobi, 3 HSS first step, 4 two Jacobi
+ * sweeps from 0, 5 prolongation + Jacobi, 6 residual + restriction, 7 prolongation + two
+ * sweeps, 8 HSS first step + two sweeps, 9 coarsest-level solve), {rows, form} (for 9:
+ * {cluster size, 0}) at [(l * 10 + m) * 2], 0 where nothing was tuned.
  */
 HH_API hh_status hh_autotune(hh_problem* p, int precision, int* shapes);
 

@@ -29,8 +29,10 @@ static SlabPlan slab_plan(const GridDesc& g, int cs) {
     SlabPlan sp;
     sp.per = (g.nn + cs - 1) / cs;
     sp.S = g.dim == 3 ? (long long)g.nn * g.nn : g.nn;
-    // two iterate buffers with a halo slab on each side
-    sp.smem = (size_t)(2 * (sp.per + 2)) * sp.S * sizeof(vec2<T>);
+    // two iterate buffers with a halo slab on each side (2D: rows padded by a zero column
+    // on both sides)
+    const long long width = g.dim == 3 ? sp.S : sp.S + 2;
+    sp.smem = (size_t)(2 * (sp.per + 2)) * width * sizeof(vec2<T>);
     return sp;
 }
 
@@ -163,12 +165,110 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem(const __grid_co
     for (int q = threadIdx.x; q < own; q += blockDim.x) xout[(long long)r0 * S + q] = xs[cur][q + S];
 }
 
+// ---- 2D: padded slabs and boundary classes ----
+// The 2D form keeps each slab row with a zero column on both sides and the halo rows above
+// and below, so that every node reads its 8 neighbours unconditionally (Dirichlet nodes and
+// nodes outside the grid stay 0); inner nodes use the interior weights and side nodes the
+// weights of their boundary class, exactly as the 2D stencil kernels do, so the result
+// equals nsweeps separate sweeps bit for bit.
+template <typename T>
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem2(const __grid_constant__ MArgs<T> a, int nsweeps,
+                                                                  int per) {
+    pdl_entry();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int prob = blockIdx.x / (int)cl.num_blocks();
+    if (problem_skipped(a, prob)) return;  // uniform over the cluster: no barrier is left waiting
+    const PCoef<T>& c = coef_of(a, prob);
+    const vec2<T>* __restrict__ b = a.z + (long long)prob * a.bs;
+    vec2<T>* __restrict__ xout = a.y + (long long)prob * a.bs;
+    const int nn = a.g.nn, n = a.g.n, W = nn + 2;
+    const int r0 = min(rank * per, nn);
+    const int r1 = min(r0 + per, nn);
+    const int own = (r1 - r0) * nn;  // owned nodes (at most kCoarseNodesPerThread per thread)
+    const int buf = (per + 2) * W;   // one padded iterate buffer, halo rows included
+    vec2<T>* xs[2] = {reinterpret_cast<vec2<T>*>(smem_raw), reinterpret_cast<vec2<T>*>(smem_raw) + buf};
+    for (int q = threadIdx.x; q < 2 * buf; q += blockDim.x) st<T>(xs[0], q, cx<T>(0, 0));
+
+    // per owned node, once: padded index, kind (-1 none, 8 inner, 0..7 boundary class), b and
+    // the padded indices of its copies in the neighbours' halo rows (-1 if none)
+    constexpr int K = kCoarseNodesPerThread2;
+    int pidx[K], kind[K], hm[K], hp[K];
+    Cx<T> bq[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int q = threadIdx.x + k * blockDim.x;
+        pidx[k] = 0;
+        kind[k] = hm[k] = hp[k] = -1;
+        bq[k] = cx<T>(0, 0);
+        if (q >= own) continue;
+        const int rl = q / nn, i = q - rl * nn, j = r0 + rl;
+        const bool vd = (i == 0 && a.g.dir[0]) || (i == n && a.g.dir[1]) || (j == 0 && a.g.dir[2]) ||
+                        (j == n && a.g.dir[3]);
+        if (vd) continue;
+        pidx[k] = (rl + 1) * W + (i + 1);
+        const int tx = i == 0 ? 0 : (i == n ? 2 : 1), ty = j == 0 ? 0 : (j == n ? 2 : 1);
+        const int cls = ty * 3 + tx;
+        kind[k] = cls == 4 ? 8 : cls - (cls > 4);
+        bq[k] = ld<T>(b, (long long)j * nn + i);
+        if (rl == 0 && rank > 0) hm[k] = (per + 1) * W + (i + 1);
+        if (j == r1 - 1 && r1 < nn) hp[k] = i + 1;
+    }
+    cl.sync();  // every CTA's buffers are zero before any halo row arrives
+    int cur = 0;
+    for (int s = 0; s < nsweeps; ++s) {
+        const vec2<T>* __restrict__ xc = xs[cur];
+        vec2<T>* xn = xs[cur ^ 1];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (kind[k] < 0) continue;
+            const int pi = pidx[k];
+            const bool inner = kind[k] == 8;
+            const Cx<T> dinv = inner ? c.wdinv : c.bdinv[kind[k]];
+            Cx<T> xv;
+            if (s == 0) {
+                xv = cmul(dinv, bq[k]);  // first sweep from x = 0
+            } else {
+                const Cx<T> f0 = ld<T>(xc, pi), fm = ld<T>(xc, pi - W), fp = ld<T>(xc, pi + W);
+                const Cx<T> l0 = ld<T>(xc, pi - 1), r0v = ld<T>(xc, pi + 1);
+                const Cx<T> lm = ld<T>(xc, pi - W - 1), rm = ld<T>(xc, pi - W + 1);
+                const Cx<T> lp = ld<T>(xc, pi + W - 1), rp = ld<T>(xc, pi + W + 1);
+                Cx<T> ax;
+                if (inner) {
+                    const Cx<T> edge = (l0 + r0v) + (fm + fp);
+                    const Cx<T> diag = (lm + rm) + (lp + rp);
+                    ax = fma_c(c.iw[2], diag, fma_c(c.iw[1], edge, cmul(c.iw[0], f0)));
+                } else {
+                    const int qc = kind[k];
+                    const Cx<T> hx = l0 + r0v;
+                    const Cx<T> vy = fm + fp;
+                    const Cx<T> dg = (lm + rm) + (lp + rp);
+                    ax = fma_c(c.bw[qc][3], dg, fma_c(c.bw[qc][2], vy, fma_c(c.bw[qc][1], hx, cmul(c.bw[qc][0], f0))));
+                }
+                xv = fma_c(dinv, bq[k] - ax, f0);
+            }
+            st<T>(xn, pi, xv);
+            if (hm[k] >= 0) st<T>(cl.map_shared_rank(xn, rank - 1), hm[k], xv);
+            if (hp[k] >= 0) st<T>(cl.map_shared_rank(xn, rank + 1), hp[k], xv);
+        }
+        cl.sync();
+        cur ^= 1;
+    }
+    for (int q = threadIdx.x; q < own; q += blockDim.x) {
+        const int rl = q / nn, i = q - rl * nn;
+        xout[(long long)(r0 + rl) * nn + i] = xs[cur][(rl + 1) * W + (i + 1)];
+    }
+}
+
 static int g_cluster_size = 0;
 
 int coarse_cluster_size() {
     if (g_cluster_size) return g_cluster_size;
     cudaFuncSetAttribute(k_coarse_dsmem<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute(k_coarse_dsmem<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_coarse_dsmem2<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_coarse_dsmem2<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaGetLastError();
     for (int cs : {16, 8}) {
     cudaLaunchConfig_t cfg = {};
@@ -193,16 +293,29 @@ int coarse_cluster_size() {
     return 1;
 }
 
+// Nodes one CTA can own: the 2D kernel keeps 4 per thread, the 3D kernel 2.
+static long long cta_capacity(const GridDesc& g) {
+    return (long long)(g.dim == 2 ? kCoarseNodesPerThread2 : kCoarseNodesPerThread) * kCoarseThreads;
+}
+
+template <typename T>
+bool coarse_cluster_ok(const GridDesc& g, int cs) {
+    if (cs < 1 || cs > coarse_cluster_size()) return false;
+    const SlabPlan sp = slab_plan<T>(g, cs);
+    return sp.smem <= kCoarseSmemMax && (long long)sp.per * sp.S <= cta_capacity(g);
+}
+
 template <typename T>
 bool coarse_fits(const GridDesc& g) {
-    const SlabPlan sp = slab_plan<T>(g, coarse_cluster_size());
-    return sp.smem <= kCoarseSmemMax && (long long)sp.per * sp.S <= (long long)kCoarseNodesPerThread * kCoarseThreads;
+    return coarse_cluster_ok<T>(g, coarse_cluster_size());
 }
 
 template <typename T>
 cudaError_t prepare_coarse() {
     cudaError_t e = cudaFuncSetAttribute(k_coarse_dsmem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kCoarseSmemMax);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_coarse_dsmem2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemMax);
     if (e != cudaSuccess) return e;
     coarse_cluster_size();
     return cudaSuccess;
@@ -214,26 +327,26 @@ cudaError_t prepare_coarse() {
 template <typename T>
 static int batch_cluster_size(const GridDesc& g, int nb) {
     int cs = coarse_cluster_size();
-    while (cs > 1 && (long long)nb * cs > 2LL * 152) {
-        const SlabPlan sp = slab_plan<T>(g, cs / 2);
-        if (sp.smem > kCoarseSmemMax || (long long)sp.per * sp.S > (long long)kCoarseNodesPerThread * kCoarseThreads)
-            break;
-        cs /= 2;
-    }
+    while (cs > 1 && (long long)nb * cs > 2LL * 152 && coarse_cluster_ok<T>(g, cs / 2)) cs /= 2;
     return cs;
 }
 
 template <typename T>
 cudaError_t launch_coarse_solve(const MArgs<T>& a, int nsweeps, cudaStream_t s) {
-    const int cs = batch_cluster_size<T>(a.g, a.nb);
+    if (nsweeps < 1) return cudaErrorInvalidValue;
+    // a tuned cluster size arrives in tile_rows
+    const int cs = coarse_cluster_ok<T>(a.g, a.tile_rows) ? a.tile_rows : batch_cluster_size<T>(a.g, a.nb);
+    if (!coarse_cluster_ok<T>(a.g, cs)) return cudaErrorInvalidValue;
     const SlabPlan sp = slab_plan<T>(a.g, cs);
-    if (sp.smem > kCoarseSmemMax || nsweeps < 1) return cudaErrorInvalidValue;
-    if ((long long)sp.per * sp.S > (long long)kCoarseNodesPerThread * kCoarseThreads) return cudaErrorInvalidValue;
+    if (a.g.dim == 2)
+        return klaunch(k_coarse_dsmem2<T>, dim3(cs * a.nb), dim3(kCoarseThreads), sp.smem, s, cs, a, nsweeps, sp.per);
     return klaunch(k_coarse_dsmem<T>, dim3(cs * a.nb), dim3(kCoarseThreads), sp.smem, s, cs, a, nsweeps, sp.per);
 }
 
 template bool coarse_fits<float>(const GridDesc&);
 template bool coarse_fits<double>(const GridDesc&);
+template bool coarse_cluster_ok<float>(const GridDesc&, int);
+template bool coarse_cluster_ok<double>(const GridDesc&, int);
 template cudaError_t prepare_coarse<float>();
 template cudaError_t prepare_coarse<double>();
 template cudaError_t launch_coarse_solve<float>(const MArgs<float>&, int, cudaStream_t);

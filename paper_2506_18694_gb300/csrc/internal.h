@@ -208,7 +208,8 @@ cudaError_t launch_march3(int mode, const MArgs<T>& a, cudaStream_t s);
 // ---- coarsest level inside one thread-block cluster per problem, in distributed shared
 //      memory (coarse.cu) ----
 constexpr int kCoarseThreads = 512;
-constexpr int kCoarseNodesPerThread = 2;
+constexpr int kCoarseNodesPerThread = 2;   // 3D kernel
+constexpr int kCoarseNodesPerThread2 = 4;  // 2D kernel
 constexpr size_t kCoarseSmemMax = 200 * 1024;
 
 // CTAs per cluster (16 or 8 when the device can co-schedule them, else 1)
@@ -216,11 +217,14 @@ int coarse_cluster_size();
 // whether a grid's slabs fit the shared memory of the cluster's CTAs
 template <typename T>
 bool coarse_fits(const GridDesc& g);
+// whether clusters of cs CTAs can hold the grid (cs up to the device's cluster size)
+template <typename T>
+bool coarse_cluster_ok(const GridDesc& g, int cs);
 // one-time set-up (shared-memory limit, cluster query); call before any stream capture
 template <typename T>
 cudaError_t prepare_coarse();
 // a.nb problems: nsweeps scaled-Jacobi sweeps on op x = z from x = 0 into y (coefficients
-// from a.pc), one cluster per problem
+// from a.pc), one cluster per problem; a.tile_rows, if a valid cluster size, picks it
 template <typename T>
 cudaError_t launch_coarse_solve(const MArgs<T>& a, int nsweeps, cudaStream_t s);
 

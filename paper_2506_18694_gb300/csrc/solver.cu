@@ -88,7 +88,8 @@ int n_hss(double k, double theta) {
     return (int)std::ceil(v);
 }
 
-constexpr int kModes = 7;  // hh::MarchMode values
+constexpr int kModes = 10;      // hh::MarchMode values 0..8 and the coarsest-level solve
+constexpr int kCoarseMode = 9;
 
 // Operators with a coefficient table (per problem and level).
 enum Role { R_K = 0, R_M, R_MG, R_AL, R_AR, R_B, R_BHAT, R_COUNT };
@@ -544,6 +545,8 @@ struct MG {
                 hh::MArgs<T> a = margs(l, R_AL);
                 a.z = b;
                 a.y = x;
+                const auto& tab = p->tune[sizeof(T) == 4 ? HH_C64 : HH_C128];
+                a.tile_rows = l < (int)tab.size() ? tab[l][kCoarseMode][0] : 0;
                 HH_LAUNCH(hh::launch_coarse_solve<T>(a, p->o.nu_coarse, s));
             } else {
                 HH_TRY(smooth_from_zero(l, b, p->o.nu_coarse, &x));
@@ -759,9 +762,22 @@ hh_status residual_B(hh_problem* p, const double2* x, double2* r) {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int, int>, std::array<int, 2>> g_tune_cache;
 
-// Candidate {rows, form} of a stencil kernel (form: 1 one tile per warp, 2 persistent).
-std::vector<std::array<int, 2>> tile_candidates(int dim, int prec, int mode) {
+// Candidate {rows, form} of a stencil kernel (form: 1 one tile per warp, 2 persistent); for
+// the coarsest-level solve, {cluster size, 0}.
+std::vector<std::array<int, 2>> tile_candidates(const GridDesc& g, int prec, int mode) {
+    const int dim = g.dim;
     std::vector<std::array<int, 2>> c;
+    if (mode == kCoarseMode) {
+        for (int cs : {16, 8, 4, 2, 1}) {
+            const bool ok = prec == HH_C64 ? hh::coarse_cluster_ok<float>(g, cs) : hh::coarse_cluster_ok<double>(g, cs);
+            if (ok) c.push_back({cs, 0});
+        }
+        return c;
+    }
+    if (mode == hh::M_PROLONG_JACOBI2 || mode == hh::M_HSS_FIRST2) {
+        if (dim == 2) c = {{2, 1}, {4, 1}};
+        return c;
+    }
     if (dim == 2) {
         std::vector<int> rows = {2, 4};
         if (prec == HH_C64 && mode != hh::M_RESID_RESTRICT) rows.push_back(8);
@@ -784,8 +800,8 @@ hh_status time_shape(hh_problem* p, int l, int mode, const std::array<int, 2>& c
     MG<T> m = make_mg<T>(p, prec, p->s);
     const bool fgm = prec == HH_C128 && l == 0 && (mode == hh::M_APPLY || mode == hh::M_AXPBY) &&
                      !p->hier[HH_C128].ready;
-    const int role = mode == hh::M_HSS_FIRST ? R_AR : (mode == hh::M_APPLY ? R_B : R_AL);
-    hh::MArgs<T> a = m.margs(l, role);
+    const int role = (mode == hh::M_HSS_FIRST || mode == hh::M_HSS_FIRST2) ? R_AR : (mode == hh::M_APPLY ? R_B : R_AL);
+    hh::MArgs<T> a = (mode == hh::M_PROLONG_JACOBI2 || mode == hh::M_HSS_FIRST2) ? m.margs2(l, role) : m.margs(l, role);
     if (fgm) {
         // the FP64 outer operator: Krylov buffers stand in for the hierarchy
         a.x = (const V2*)p->V;
@@ -800,12 +816,16 @@ hh_status time_shape(hh_problem* p, int l, int mode, const std::array<int, 2>& c
         if (l + 1 < p->o.levels) a.ec = (const V2*)H.xa[l + 1];
         if (mode == hh::M_RESID_RESTRICT) a.y = (V2*)H.t[l + 1];
     }
-    a.use_pc_ab = mode == hh::M_HSS_FIRST;
+    a.use_pc_ab = mode == hh::M_HSS_FIRST || mode == hh::M_HSS_FIRST2;
     a.alpha = Cx<T>{-1, 0};
     a.beta = Cx<T>{1, 0};
     a.tile_rows = cand[0];
     a.tile_form = cand[1];
-    auto launch = [&]() { return m.d2() ? hh::launch_march2<T>(mode, a, p->s) : hh::launch_march3<T>(mode, a, p->s); };
+    if (mode == kCoarseMode) a.y = (V2*)p->hier[prec].xa[l];
+    auto launch = [&]() {
+        if (mode == kCoarseMode) return hh::launch_coarse_solve<T>(a, p->o.nu_coarse, p->s);
+        return m.d2() ? hh::launch_march2<T>(mode, a, p->s) : hh::launch_march3<T>(mode, a, p->s);
+    };
     cudaEvent_t e0, e1;
     HH_CUDA(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -838,9 +858,17 @@ hh_status autotune(hh_problem* p, int prec) {
     std::vector<std::tuple<int, int, int>> work;  // (precision, level, mode)
     for (int l = 0; l < L; ++l)
         for (int mode = 0; mode < kModes; ++mode) {
-            if ((mode == hh::M_PROLONG_JACOBI || mode == hh::M_RESID_RESTRICT) && l == L - 1) continue;
-            if (mode == hh::M_RESID_RESTRICT && p->grid.dim == 3) continue;
-            if (mode == hh::M_HSS_FIRST && l != 0) continue;
+            const bool coarse_cluster = p->o.nu_coarse >= 1 && p->lv[l].N <= p->o.coarse_cluster_nodes &&
+                                        (prec == HH_C64 ? hh::coarse_fits<float>(p->lv[l])
+                                                        : hh::coarse_fits<double>(p->lv[l]));
+            if (mode == kCoarseMode && (l != L - 1 || !coarse_cluster)) continue;
+            if ((mode == hh::M_PROLONG_JACOBI || mode == hh::M_RESID_RESTRICT || mode == hh::M_PROLONG_JACOBI2) &&
+                l == L - 1)
+                continue;
+            if ((mode == hh::M_RESID_RESTRICT || mode == hh::M_PROLONG_JACOBI2 || mode == hh::M_HSS_FIRST2) &&
+                p->grid.dim == 3)
+                continue;
+            if ((mode == hh::M_HSS_FIRST || mode == hh::M_HSS_FIRST2) && l != 0) continue;
             work.emplace_back(prec, l, mode);
         }
     if (prec == HH_C64) {
@@ -857,7 +885,7 @@ hh_status autotune(hh_problem* p, int prec) {
             if (it != g_tune_cache.end()) best = it->second;
         }
         if (best[0] == 0) {
-            const auto cands = tile_candidates(p->grid.dim, q, mode);
+            const auto cands = tile_candidates(p->lv[l], q, mode);
             if (cands.size() < 2) continue;
             float tbest = 0.f;
             for (const auto& c : cands) {

@@ -241,17 +241,19 @@ class Problem:
         """Allocate the multigrid buffers and capture the preconditioner graph now."""
         _check(self._lib.hh_prepare(self._p))
 
-    MODES = ("apply", "axpby", "jacobi", "hss_first", "jacobi2_zero", "prolong_jacobi", "resid_restrict")
+    MODES = ("apply", "axpby", "jacobi", "hss_first", "jacobi2_zero", "prolong_jacobi", "resid_restrict",
+             "prolong_jacobi2", "hss_first2", "coarse")
 
     def autotune(self, precision=None):
         """Time the tile shapes of every stencil kernel and keep the fastest; returns
         {(level, mode): (rows, form)} for the tuned kernels."""
         prec = self.options.precision if precision is None else precision
         L = self.options.levels
-        out = (ctypes.c_int * (L * 7 * 2))()
+        M = len(self.MODES)
+        out = (ctypes.c_int * (L * M * 2))()
         _check(self._lib.hh_autotune(self._p, prec, out))
-        return {(l, m): (out[(l * 7 + i) * 2], out[(l * 7 + i) * 2 + 1])
-                for l in range(L) for i, m in enumerate(self.MODES) if out[(l * 7 + i) * 2]}
+        return {(l, m): (out[(l * M + i) * 2], out[(l * M + i) * 2 + 1])
+                for l in range(L) for i, m in enumerate(self.MODES) if out[(l * M + i) * 2]}
 
     def nodes(self, level=0) -> int:
         """Nodes of one problem's level-`level` vector."""

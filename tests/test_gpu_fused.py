@@ -51,3 +51,21 @@ def test_fused_batch_equals_unfused(libhh):
             u, infos = p.solve(f, 1e-9)
             res[fuse] = (u.cpu(), [i.outer_its for i in infos])
     assert torch.equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
+
+
+@pytest.mark.parametrize("prec", [hh.HH_C64, hh.HH_C128])
+@pytest.mark.parametrize("n,levels,bc", [(72, 4, (S, D, S, S)), (128, 3, (S, S, S, S)), (256, 3, (D, S, S, D))])
+def test_coarse_cluster_equals_separate_sweeps(libhh, prec, n, levels, bc):
+    """The coarsest level solved in one thread-block cluster equals the same sweeps run as
+    separate kernels, bit for bit."""
+    g = O.Grid(2, n, bc)
+    r = torch.from_numpy(inputs.random_complex(g.N, 1500 + n) * g.free()).cuda()
+    out = {}
+    for cc in (0, 100000):
+        opts = hh.default_options(levels=levels, precision=prec, coarse_cluster_nodes=cc)
+        with hh.Problem(2, n, 12.0, 0.0, 12.0, bc, opts) as p:
+            z = p.precondition(r)
+            u, info = p.solve(r, 1e-9)
+            out[cc] = (z.cpu(), u.cpu(), info.outer_its)
+    assert torch.equal(out[0][0], out[100000][0])
+    assert torch.equal(out[0][1], out[100000][1]) and out[0][2] == out[100000][2]
