@@ -29,10 +29,14 @@ static SlabPlan slab_plan(const GridDesc& g, int cs) {
     SlabPlan sp;
     sp.per = (g.nn + cs - 1) / cs;
     sp.S = g.dim == 3 ? (long long)g.nn * g.nn : g.nn;
-    // two iterate buffers with a halo slab on each side (2D: rows padded by a zero column
-    // on both sides)
-    const long long width = g.dim == 3 ? sp.S : sp.S + 2;
-    sp.smem = (size_t)(2 * (sp.per + 2)) * width * sizeof(vec2<T>);
+    if (g.dim == 3) {
+        // two iterate buffers with a halo slab on each side
+        sp.smem = (size_t)(2 * (sp.per + 2)) * sp.S * sizeof(vec2<T>);
+    } else {
+        // three padded buffers (rows padded by a zero column on both sides) with two halo
+        // rows on each side
+        sp.smem = (size_t)(3 * (sp.per + 4)) * (sp.S + 2) * sizeof(vec2<T>);
+    }
     return sp;
 }
 
@@ -165,12 +169,40 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem(const __grid_co
     for (int q = threadIdx.x; q < own; q += blockDim.x) xout[(long long)r0 * S + q] = xs[cur][q + S];
 }
 
-// ---- 2D: padded slabs and boundary classes ----
-// The 2D form keeps each slab row with a zero column on both sides and the halo rows above
+// ---- 2D: padded slabs, boundary classes, two sweeps per cluster barrier ----
+// The 2D form keeps each slab row with a zero column on both sides and two halo rows above
 // and below, so that every node reads its 8 neighbours unconditionally (Dirichlet nodes and
-// nodes outside the grid stay 0); inner nodes use the interior weights and side nodes the
-// weights of their boundary class, exactly as the 2D stencil kernels do, so the result
-// equals nsweeps separate sweeps bit for bit.
+// nodes outside the grid stay 0).  Sweeps run in pairs: a CTA computes the first sweep of
+// a pair on its own rows and on the nearest row of each neighbour (recomputed, so no
+// exchange is needed in between), then the second sweep on its own rows, and only then
+// writes its two top and two bottom rows into the neighbours' halo rows: one cluster
+// barrier per two sweeps.  The first sweep (from x = 0) is pointwise and needs no halo.
+// Inner nodes use the interior weights and side nodes the weights of their boundary class,
+// exactly as the 2D stencil kernels do, so the result equals nsweeps separate sweeps bit
+// for bit.  Slabs of one row (tiny grids) exchange after every sweep.
+template <typename T>
+__device__ __forceinline__ Cx<T> coarse_update2(const PCoef<T>& c, const vec2<T>* __restrict__ xc, int pi, int W,
+                                               int kind, Cx<T> bq) {
+    const bool inner = kind == 8;
+    const Cx<T> dinv = inner ? c.wdinv : c.bdinv[kind];
+    const Cx<T> f0 = ld<T>(xc, pi), fm = ld<T>(xc, pi - W), fp = ld<T>(xc, pi + W);
+    const Cx<T> l0 = ld<T>(xc, pi - 1), r0v = ld<T>(xc, pi + 1);
+    const Cx<T> lm = ld<T>(xc, pi - W - 1), rm = ld<T>(xc, pi - W + 1);
+    const Cx<T> lp = ld<T>(xc, pi + W - 1), rp = ld<T>(xc, pi + W + 1);
+    Cx<T> ax;
+    if (inner) {
+        const Cx<T> edge = (l0 + r0v) + (fm + fp);
+        const Cx<T> diag = (lm + rm) + (lp + rp);
+        ax = fma_c(c.iw[2], diag, fma_c(c.iw[1], edge, cmul(c.iw[0], f0)));
+    } else {
+        const Cx<T> hx = l0 + r0v;
+        const Cx<T> vy = fm + fp;
+        const Cx<T> dg = (lm + rm) + (lp + rp);
+        ax = fma_c(c.bw[kind][3], dg, fma_c(c.bw[kind][2], vy, fma_c(c.bw[kind][1], hx, cmul(c.bw[kind][0], f0))));
+    }
+    return fma_c(dinv, bq - ax, f0);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem2(const __grid_constant__ MArgs<T> a, int nsweeps,
                                                                   int per) {
@@ -186,78 +218,86 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem2(const __grid_c
     const int nn = a.g.nn, n = a.g.n, W = nn + 2;
     const int r0 = min(rank * per, nn);
     const int r1 = min(r0 + per, nn);
-    const int own = (r1 - r0) * nn;  // owned nodes (at most kCoarseNodesPerThread per thread)
-    const int buf = (per + 2) * W;   // one padded iterate buffer, halo rows included
-    vec2<T>* xs[2] = {reinterpret_cast<vec2<T>*>(smem_raw), reinterpret_cast<vec2<T>*>(smem_raw) + buf};
-    for (int q = threadIdx.x; q < 2 * buf; q += blockDim.x) st<T>(xs[0], q, cx<T>(0, 0));
+    const int rows = r1 - r0;
+    const bool paired = per >= 2;
+    const int buf = (per + 4) * W;  // one padded buffer: rows -2 .. per + 1 of the slab
+    vec2<T>* xs[3];
+    for (int q = 0; q < 3; ++q) xs[q] = reinterpret_cast<vec2<T>*>(smem_raw) + (long long)q * buf;
+    for (int q = threadIdx.x; q < 3 * buf; q += blockDim.x) st<T>(xs[0], q, cx<T>(0, 0));
 
-    // per owned node, once: padded index, kind (-1 none, 8 inner, 0..7 boundary class), b and
-    // the padded indices of its copies in the neighbours' halo rows (-1 if none)
+    // entries: the slab's rows and, for pairs, the nearest row of each neighbour (rl = -1,
+    // rl = rows).  Per entry: padded index, kind (-1 none, 8 inner, 0..7 boundary class), b,
+    // whether it is an own node, and where its value goes in the neighbours' halo rows.
     constexpr int K = kCoarseNodesPerThread2;
     int pidx[K], kind[K], hm[K], hp[K];
+    bool mine[K];
     Cx<T> bq[K];
+    const int first = paired ? -1 : 0, last = paired ? rows : rows - 1;  // entry rows
+    const int ents = (last - first + 1) * nn;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const int q = threadIdx.x + k * blockDim.x;
+        const int e = threadIdx.x + k * blockDim.x;
         pidx[k] = 0;
         kind[k] = hm[k] = hp[k] = -1;
+        mine[k] = false;
         bq[k] = cx<T>(0, 0);
-        if (q >= own) continue;
-        const int rl = q / nn, i = q - rl * nn, j = r0 + rl;
+        if (e >= ents || rows <= 0) continue;
+        const int rl = first + e / nn, i = e % nn, j = r0 + rl;
+        if (j < 0 || j >= nn) continue;
         const bool vd = (i == 0 && a.g.dir[0]) || (i == n && a.g.dir[1]) || (j == 0 && a.g.dir[2]) ||
                         (j == n && a.g.dir[3]);
         if (vd) continue;
-        pidx[k] = (rl + 1) * W + (i + 1);
+        pidx[k] = (rl + 2) * W + (i + 1);
         const int tx = i == 0 ? 0 : (i == n ? 2 : 1), ty = j == 0 ? 0 : (j == n ? 2 : 1);
         const int cls = ty * 3 + tx;
         kind[k] = cls == 4 ? 8 : cls - (cls > 4);
         bq[k] = ld<T>(b, (long long)j * nn + i);
-        if (rl == 0 && rank > 0) hm[k] = (per + 1) * W + (i + 1);
-        if (j == r1 - 1 && r1 < nn) hp[k] = i + 1;
+        mine[k] = rl >= 0 && rl < rows;
+        if (!mine[k]) continue;
+        // upper neighbour: its halo rows per + 2 (our row 0), per + 3 (our row 1)
+        if (rank > 0 && rl < (paired ? 2 : 1)) hm[k] = (per + 2 + rl) * W + (i + 1);
+        // lower neighbour: its halo rows 0 (our row rows - 2), 1 (our row rows - 1)
+        if (r1 < nn && rl >= rows - (paired ? 2 : 1)) hp[k] = (rl - rows + 2) * W + (i + 1);
     }
     cl.sync();  // every CTA's buffers are zero before any halo row arrives
-    int cur = 0;
-    for (int s = 0; s < nsweeps; ++s) {
-        const vec2<T>* __restrict__ xc = xs[cur];
-        vec2<T>* xn = xs[cur ^ 1];
+    int in = 0;  // buffer holding the current iterate (own rows and valid halo rows)
+    int s = 0;
+    while (s < nsweeps) {
+        const int tmp = (in + 1) % 3, out = (in + 2) % 3;
+        const bool pair = paired && s + 1 < nsweeps;
+        // first sweep of the pair (or the single sweep): own rows, and the neighbours'
+        // nearest rows when paired
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            if (kind[k] < 0) continue;
-            const int pi = pidx[k];
-            const bool inner = kind[k] == 8;
-            const Cx<T> dinv = inner ? c.wdinv : c.bdinv[kind[k]];
-            Cx<T> xv;
-            if (s == 0) {
-                xv = cmul(dinv, bq[k]);  // first sweep from x = 0
-            } else {
-                const Cx<T> f0 = ld<T>(xc, pi), fm = ld<T>(xc, pi - W), fp = ld<T>(xc, pi + W);
-                const Cx<T> l0 = ld<T>(xc, pi - 1), r0v = ld<T>(xc, pi + 1);
-                const Cx<T> lm = ld<T>(xc, pi - W - 1), rm = ld<T>(xc, pi - W + 1);
-                const Cx<T> lp = ld<T>(xc, pi + W - 1), rp = ld<T>(xc, pi + W + 1);
-                Cx<T> ax;
-                if (inner) {
-                    const Cx<T> edge = (l0 + r0v) + (fm + fp);
-                    const Cx<T> diag = (lm + rm) + (lp + rp);
-                    ax = fma_c(c.iw[2], diag, fma_c(c.iw[1], edge, cmul(c.iw[0], f0)));
-                } else {
-                    const int qc = kind[k];
-                    const Cx<T> hx = l0 + r0v;
-                    const Cx<T> vy = fm + fp;
-                    const Cx<T> dg = (lm + rm) + (lp + rp);
-                    ax = fma_c(c.bw[qc][3], dg, fma_c(c.bw[qc][2], vy, fma_c(c.bw[qc][1], hx, cmul(c.bw[qc][0], f0))));
-                }
-                xv = fma_c(dinv, bq[k] - ax, f0);
+            if (kind[k] < 0 || (!pair && !mine[k])) continue;
+            const Cx<T> xv = s == 0 ? cmul(kind[k] == 8 ? c.wdinv : c.bdinv[kind[k]], bq[k])
+                                    : coarse_update2(c, xs[in], pidx[k], W, kind[k], bq[k]);
+            st<T>(pair ? xs[tmp] : xs[out], pidx[k], xv);
+        }
+        if (pair) {
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if (kind[k] < 0 || !mine[k]) continue;
+                st<T>(xs[out], pidx[k], coarse_update2(c, xs[tmp], pidx[k], W, kind[k], bq[k]));
             }
-            st<T>(xn, pi, xv);
-            if (hm[k] >= 0) st<T>(cl.map_shared_rank(xn, rank - 1), hm[k], xv);
-            if (hp[k] >= 0) st<T>(cl.map_shared_rank(xn, rank + 1), hp[k], xv);
+            __syncthreads();
+        }
+        // own boundary rows of the new iterate into the neighbours' halo rows
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (kind[k] < 0 || !mine[k] || (hm[k] < 0 && hp[k] < 0)) continue;
+            const Cx<T> xv = ld<T>(xs[out], pidx[k]);
+            if (hm[k] >= 0) st<T>(cl.map_shared_rank(xs[out], rank - 1), hm[k], xv);
+            if (hp[k] >= 0) st<T>(cl.map_shared_rank(xs[out], rank + 1), hp[k], xv);
         }
         cl.sync();
-        cur ^= 1;
+        in = out;
+        s += pair ? 2 : 1;
     }
-    for (int q = threadIdx.x; q < own; q += blockDim.x) {
+    for (int q = threadIdx.x; q < rows * nn; q += blockDim.x) {
         const int rl = q / nn, i = q - rl * nn;
-        xout[(long long)(r0 + rl) * nn + i] = xs[cur][(rl + 1) * W + (i + 1)];
+        xout[(long long)(r0 + rl) * nn + i] = xs[in][(rl + 2) * W + (i + 1)];
     }
 }
 
@@ -302,7 +342,9 @@ template <typename T>
 bool coarse_cluster_ok(const GridDesc& g, int cs) {
     if (cs < 1 || cs > coarse_cluster_size()) return false;
     const SlabPlan sp = slab_plan<T>(g, cs);
-    return sp.smem <= kCoarseSmemMax && (long long)sp.per * sp.S <= cta_capacity(g);
+    // 2D CTAs also hold the nearest row of each neighbour
+    const long long rows = g.dim == 2 ? sp.per + 2 : sp.per;
+    return sp.smem <= kCoarseSmemMax && rows * sp.S <= cta_capacity(g);
 }
 
 template <typename T>

@@ -54,15 +54,17 @@ def test_fused_batch_equals_unfused(libhh):
 
 
 @pytest.mark.parametrize("prec", [hh.HH_C64, hh.HH_C128])
-@pytest.mark.parametrize("n,levels,bc", [(72, 4, (S, D, S, S)), (128, 3, (S, S, S, S)), (256, 3, (D, S, S, D))])
-def test_coarse_cluster_equals_separate_sweeps(libhh, prec, n, levels, bc):
-    """The coarsest level solved in one thread-block cluster equals the same sweeps run as
-    separate kernels, bit for bit."""
+@pytest.mark.parametrize("n,levels,bc,nc", [(72, 4, (S, D, S, S), 8), (128, 3, (S, S, S, S), 8),
+                                            (256, 3, (D, S, S, D), 8), (128, 3, (S, S, D, S), 7),
+                                            (64, 2, (S, D, S, S), 1), (256, 3, (S, S, S, S), 2)])
+def test_coarse_cluster_equals_separate_sweeps(libhh, prec, n, levels, bc, nc):
+    """The coarsest level solved in one thread-block cluster (sweeps in pairs, one-row slabs
+    and odd counts included) equals the same sweeps run as separate kernels, bit for bit."""
     g = O.Grid(2, n, bc)
     r = torch.from_numpy(inputs.random_complex(g.N, 1500 + n) * g.free()).cuda()
     out = {}
     for cc in (0, 100000):
-        opts = hh.default_options(levels=levels, precision=prec, coarse_cluster_nodes=cc)
+        opts = hh.default_options(levels=levels, precision=prec, coarse_cluster_nodes=cc, nu_coarse=nc)
         with hh.Problem(2, n, 12.0, 0.0, 12.0, bc, opts) as p:
             z = p.precondition(r)
             u, info = p.solve(r, 1e-9)
