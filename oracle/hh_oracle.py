@@ -559,6 +559,38 @@ def solve(prob: Problem, b, tol, x0=None, inner=None):
                   restart=prob.opts.restart, max_it=prob.opts.max_outer, x0=x0)
 
 
+def richardson(apply_A, b, prec, tol, max_it=200, x0=None):
+    """Preconditioned Richardson (stationary) iteration u^{n+1} = u^n + P(b - A u^n), the
+    iteration that the text after Def. 4.1 defines with P the shifted-HSS preconditioner.
+
+    Stops when the true relative residual ||b - A u|| / ||b|| (computed every step) is
+    <= tol.  Returns (x, iterations, relative residual, history of residuals).
+    """
+    b = np.asarray(b, dtype=complex)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=complex)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return np.zeros_like(b), 0, 0.0, []
+    r = b - apply_A(x)
+    rel = np.linalg.norm(r) / bnorm
+    hist = [rel]
+    its = 0
+    while rel > tol and its < max_it:
+        x = x + prec(r)
+        r = b - apply_A(x)
+        rel = np.linalg.norm(r) / bnorm
+        hist.append(rel)
+        its += 1
+    return x, its, rel, hist
+
+
+def solve_richardson(prob: Problem, b, tol, x0=None, inner=None):
+    """Outer preconditioned Richardson on B_delta u = b with the shifted-HSS operator."""
+    A = prob.B
+    return richardson(lambda v: A @ v, b, lambda v: prob.prec(v, inner=inner), tol,
+                      max_it=prob.opts.max_outer, x0=x0)
+
+
 def load_vector_nodal(grid, f_nodal):
     """b = M f for a nodal interpolant f (the right side G[v] of Sec. 2 with f in Q1)."""
     _, M, _ = assemble(grid)

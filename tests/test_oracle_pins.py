@@ -15,6 +15,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 
 from oracle import hh_oracle as O
+from paper_2506_18694_gb300 import inputs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 S, D = O.SOMMERFELD, O.DIRICHLET
@@ -495,3 +496,42 @@ def test_diag_elementwise_equals_assembled(dim, n, bc):
     for coeff in (O.coeff_AL(7.0, 2.0), (1.0, 0.0, 0.0), (0.0, 1.0, 0.5)):
         ref = O.combine(O.assemble(g), coeff).diagonal()
         assert np.abs(O.diag_elementwise(g, coeff) - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_richardson_exact_preconditioner_one_step():
+    """With P = A^{-1} the stationary iteration lands on the solution in one step."""
+    rng = np.random.default_rng(41)
+    A = rng.standard_normal((12, 12)) + 1j * rng.standard_normal((12, 12)) + 8 * np.eye(12)
+    b = rng.standard_normal(12) + 1j * rng.standard_normal(12)
+    Ainv = np.linalg.inv(A)
+    x, its, rel, hist = O.richardson(lambda v: A @ v, b, lambda r: Ainv @ r, 1e-12)
+    assert its == 1 and rel <= 1e-13
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=0, atol=1e-12)
+
+
+def test_richardson_matches_neumann_series():
+    """With a Jacobi preconditioner D^{-1}, step n equals sum_{m<n} (I - D^{-1}A)^m D^{-1} b."""
+    rng = np.random.default_rng(42)
+    n = 10
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + 12 * np.eye(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    Dinv = np.diag(1.0 / np.diag(A))
+    x3, its, _, _ = O.richardson(lambda v: A @ v, b, lambda r: Dinv @ r, 0.0, max_it=3)
+    G = np.eye(n) - Dinv @ A
+    ref = sum(np.linalg.matrix_power(G, m) @ Dinv @ b for m in range(3))
+    assert its == 3 and np.allclose(x3, ref, rtol=0, atol=1e-12)
+
+
+def test_richardson_hss_converges_to_lu():
+    """The HSS-preconditioned Richardson iteration (delta_hat = 2, each HSS step solved
+    directly as in the paper's Richardson tables) converges monotonically to the LU solution
+    (the contraction of Prop. 3.2 / Cor. 3.3 at work)."""
+    g = O.Grid(2, 16, (O.SOMMERFELD,) * 4)
+    f = inputs.gaussian_source(2, 16, (0.4, 0.6), 0.05)
+    b = O.load_vector_nodal(g, f)
+    prob = O.Problem(g, 6.0, 0.0, 2.0, O.Options(levels=2, max_outer=200))
+    x, its, rel, hist = O.solve_richardson(prob, b, 1e-10, inner=prob.lu("AL"))
+    ref = prob.lu("B")(b)
+    assert rel <= 1e-10 and its < 200
+    assert np.linalg.norm(x - ref) <= 1e-7 * np.linalg.norm(ref)
+    assert all(h1 < h0 for h0, h1 in zip(hist, hist[1:]))
