@@ -425,6 +425,22 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
     out["delta_hat_2"] = {"cycles_per_hss": 2, "solve_ms": 1e3 * t2, "outer_its": i2.outer_its, "vcycles": i2.vcycles,
                           "rel_residual": i2.rel_residual, "value": prob.nodes() * i2.vcycles / t2}
 
+    # the paper's preconditioned Richardson outer iteration on the same grid and source
+    # (delta_hat = 2, two cycles per HSS step)
+    try:
+        with hh.Problem(w2.dim, w2.n, w2.k, w2.delta, w2.delta_hat, w2.bc,
+                        hh.default_options(cycles_per_hss=2, outer=hh.HH_OUTER_RICHARDSON, max_outer=400)) as pr:
+            pr.solve(b, w.tol)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, ir = pr.solve(b, w.tol)
+            tr = time.perf_counter() - t0
+        out["richardson_delta_hat_2"] = {"cycles_per_hss": 2, "solve_ms": 1e3 * tr, "outer_its": ir.outer_its,
+                                         "vcycles": ir.vcycles, "rel_residual": ir.rel_residual,
+                                         "value": prob.nodes() * ir.vcycles / tr}
+    except Exception as e:
+        out["richardson_delta_hat_2"] = {"failed": str(e)}
+
     # serving: Poisson arrivals of mixed 2D/3D requests through the solve server
     try:
         out["serving"] = measure_serving(hh, inputs, torch, SERVE_REQUESTS[0])

@@ -75,6 +75,12 @@ typedef enum { HH_BC_SOMMERFELD = 0, HH_BC_DIRICHLET = 1 } hh_bc;
 /* Arithmetic of the multigrid V-cycles (the outer FGMRES is always FP64). */
 typedef enum { HH_C128 = 0, HH_C64 = 1 } hh_precision;
 
+/* Outer iteration on B_delta u = b, preconditioned by the shifted-HSS operator: flexible
+ * GMRES (Sec. 5.1), or the preconditioned Richardson iteration u += P (b - B_delta u) that
+ * the text after Def. 4.1 defines (the stationary iteration of the paper's Richardson
+ * tables, Sec. 5.2); restart is ignored for the latter. */
+typedef enum { HH_OUTER_FGMRES = 0, HH_OUTER_RICHARDSON = 1 } hh_outer;
+
 /* Operators that hh_apply can apply (coefficient triples of the weak forms). */
 typedef enum {
     HH_OP_K = 0,        /* stiffness                                     (Sec. 2) */
@@ -116,10 +122,11 @@ typedef struct {
                          /* HSS right side with the first two pre-sweeps, the prolongation    */
                          /* with the first two post-sweeps) run as one kernel; same result    */
                          /* bit for bit as 0 (one kernel per sweep)                           */
+    int outer;           /* hh_outer: HH_OUTER_FGMRES (default) or HH_OUTER_RICHARDSON      */
 } hh_options;
 
 typedef struct {
-    int outer_its;          /* FGMRES iterations                                 */
+    int outer_its;          /* outer (FGMRES or Richardson) iterations          */
     long long hss_its;      /* inner HSS iterations                              */
     long long vcycles;      /* V-cycles on the finest level                      */
     double rel_residual;    /* ||b - B_delta u||_2 / ||b||_2 recomputed in FP64   */

@@ -1075,6 +1075,61 @@ hh_status fgmres(hh_problem* p, double tol, hh_info* info) {
     return all ? HH_OK : HH_NOT_CONVERGED;
 }
 
+// Preconditioned Richardson (the stationary iteration after Def. 4.1): u += P (b - B u)
+// with the FP64 residual recomputed every step, the nb problems in lockstep; a problem
+// leaves the launches when it converges or reaches max_outer.
+hh_status richardson(hh_problem* p, double tol, hh_info* info) {
+    const int nb = p->nb, hs = hstride(p), nrm = 2 * (p->o.restart + 1);
+    const long long N = p->N;
+    std::vector<char> solving(nb, 1);
+    std::vector<double> bnorm(nb), rel(nb);
+    HH_TRY(set_active(p, nullptr));
+    HH_TRY(norm2_dev(p, p->bvec, nrm));
+    HH_TRY(fetch(p));
+    for (int b = 0; b < nb; ++b) {
+        bnorm[b] = std::sqrt(p->h_host[(size_t)b * hs + nrm].x);
+        if (!finite(bnorm[b])) return fail(HH_ERR_NONFINITE, "right-hand side " + std::to_string(b) + " is not finite");
+    }
+    HH_TRY(residual_B(p, p->x, p->r));
+    HH_TRY(norm2_dev(p, p->r, nrm));
+    HH_TRY(fetch(p));
+    for (int b = 0; b < nb; ++b) {
+        const double beta = std::sqrt(p->h_host[(size_t)b * hs + nrm].x);
+        if (!finite(beta)) return fail(HH_ERR_NONFINITE, "initial residual is not finite");
+        rel[b] = bnorm[b] > 0 ? beta / bnorm[b] : 0.0;
+        info[b].outer_its = 0;
+        if (bnorm[b] == 0.0 || rel[b] <= tol || p->o.max_outer == 0) solving[b] = 0;
+    }
+    for (int b = 0; b < nb; ++b)
+        if (bnorm[b] == 0.0) HH_CUDA(cudaMemsetAsync(p->x + (long long)b * N, 0, (size_t)N * 16, p->s));
+    const hh::Batch all{nb, N, 0, -1, nullptr, active_flags(p)};
+    while (std::any_of(solving.begin(), solving.end(), [](char c) { return c != 0; })) {
+        HH_TRY(set_active(p, &solving));
+        HH_TRY(precondition_async(p, p->r, p->Z));
+        HH_LAUNCH(hh::launch_add<double>(p->x, p->Z, N, all, p->s));
+        HH_TRY(residual_B(p, p->x, p->r));
+        HH_TRY(norm2_dev(p, p->r, nrm));
+        HH_TRY(fetch(p));
+        for (int b = 0; b < nb; ++b) {
+            if (!solving[b]) continue;
+            info[b].outer_its += 1;
+            info[b].hss_its += p->nhss[b];
+            info[b].vcycles += (long long)p->nhss[b] * p->o.cycles_per_hss;
+            const double beta = std::sqrt(p->h_host[(size_t)b * hs + nrm].x);
+            if (!finite(beta)) return fail(HH_ERR_NONFINITE, "Richardson residual is not finite");
+            rel[b] = beta / bnorm[b];
+            if (rel[b] <= tol || info[b].outer_its >= p->o.max_outer) solving[b] = 0;
+        }
+    }
+    HH_TRY(set_active(p, nullptr));
+    bool ok = true;
+    for (int b = 0; b < nb; ++b) {
+        info[b].rel_residual = rel[b];
+        ok = ok && rel[b] <= tol;
+    }
+    return ok ? HH_OK : HH_NOT_CONVERGED;
+}
+
 }  // namespace
 
 namespace {
@@ -1119,6 +1174,8 @@ hh_status check_args(const hh_grid* grid, int nb, const double* k, const double*
         return fail(HH_ERR_INVALID, "tile_rows must be 0, 2, 4 or 8");
     if (o->autotune != 0 && o->autotune != 1) return fail(HH_ERR_INVALID, "autotune must be 0 or 1");
     if (o->fuse_sweeps != 0 && o->fuse_sweeps != 1) return fail(HH_ERR_INVALID, "fuse_sweeps must be 0 or 1");
+    if (o->outer != HH_OUTER_FGMRES && o->outer != HH_OUTER_RICHARDSON)
+        return fail(HH_ERR_INVALID, "outer must be HH_OUTER_FGMRES or HH_OUTER_RICHARDSON");
     if (!bc) return fail(HH_ERR_INVALID, "null bc");
     for (int s = 0; s < 2 * grid->dim; ++s)
         if (bc[s] != HH_BC_SOMMERFELD && bc[s] != HH_BC_DIRICHLET) return fail(HH_ERR_INVALID, "bad boundary tag");
@@ -1127,7 +1184,7 @@ hh_status check_args(const hh_grid* grid, int nb, const double* k, const double*
 
 hh_status solve_core(hh_problem* p, double tol, hh_info* info) {
     const long long k0 = hh::g_kernel_launches;
-    hh_status st = fgmres(p, tol, info);
+    hh_status st = p->o.outer == HH_OUTER_RICHARDSON ? richardson(p, tol, info) : fgmres(p, tol, info);
     for (int b = 0; b < p->nb; ++b) info[b].device_bytes = p->bytes;
     info[0].kernel_launches += hh::g_kernel_launches - k0;
     return st;
@@ -1170,6 +1227,7 @@ void hh_options_default(hh_options* o) {
     o->tile_rows = 0;
     o->autotune = 0;
     o->fuse_sweeps = 1;
+    o->outer = HH_OUTER_FGMRES;
 }
 
 size_t hh_footprint_batch_bytes(const hh_grid* grid, const hh_options* o, int nb) {

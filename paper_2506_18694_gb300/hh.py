@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libhh.so")
 
 HH_OK, HH_NOT_CONVERGED = 0, 1
 HH_C128, HH_C64 = 0, 1
+HH_OUTER_FGMRES, HH_OUTER_RICHARDSON = 0, 1
 SOMMERFELD, DIRICHLET = 0, 1
 OP = {"K": 0, "M": 1, "MGAMMA": 2, "AL": 3, "AR": 4, "B": 5, "BHAT": 6}
 
@@ -42,7 +43,7 @@ class Options(ctypes.Structure):
         ("omega", ctypes.c_double), ("restart", ctypes.c_int), ("max_outer", ctypes.c_int),
         ("precision", ctypes.c_int), ("use_graphs", ctypes.c_int), ("use_pdl", ctypes.c_int),
         ("coarse_cluster_nodes", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
-        ("fuse_sweeps", ctypes.c_int),
+        ("fuse_sweeps", ctypes.c_int), ("outer", ctypes.c_int),
     ]
 
 

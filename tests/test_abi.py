@@ -31,7 +31,7 @@ def test_options_default(libhh):
     assert o.cycles_per_hss == 1 and o.omega == 0.0
     assert o.restart == 30 and o.precision == hh.HH_C64 and o.use_graphs == 1
     assert o.use_pdl == 1 and o.coarse_cluster_nodes == 100000 and o.tile_rows == 0 and o.autotune == 0
-    assert o.fuse_sweeps == 1
+    assert o.fuse_sweeps == 1 and o.outer == hh.HH_OUTER_FGMRES
 
 
 def test_footprint_bytes(libhh):
