@@ -545,8 +545,9 @@ template void interior_weights<double>(PCoef<double>&, const GridDesc&, double);
 template <typename T, int MODE, int ROWS, bool BATCH>
 static cudaError_t run2b(const MArgs<T>& a, int strips, int chunks, cudaStream_t s) {
     const long long tiles = (long long)strips * chunks * a.nb;
-    // residual-restriction and prolongation tiles carry more rows; they run one tile per warp
-    if constexpr (MODE != M_PROLONG_JACOBI && MODE != M_RESID_RESTRICT) {
+    // prolongation tiles run one tile per warp; residual-restriction tiles (more rows) only
+    // when tuned to the persistent form
+    if constexpr (MODE != M_PROLONG_JACOBI) {
         static int per_sm = 0;
         if (!per_sm) {
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march2p<T, MODE, ROWS, BATCH>, 128, 0) !=
@@ -558,7 +559,8 @@ static cudaError_t run2b(const MArgs<T>& a, int strips, int chunks, cudaStream_t
         }
         const long long resident_blocks = 152LL * per_sm;
         // automatic: persistent once there are several tiles per resident warp
-        const bool persist = a.tile_form == 2 || (a.tile_form == 0 && tiles >= 16 * resident_blocks);
+        const bool persist =
+            a.tile_form == 2 || (a.tile_form == 0 && MODE != M_RESID_RESTRICT && tiles >= 16 * resident_blocks);
         if (persist && tiles < (1LL << 31)) {
             const long long blocks = std::min(resident_blocks, (tiles + 3) / 4);
             return klaunch(k_march2p<T, MODE, ROWS, BATCH>, dim3((unsigned)blocks), dim3(128), 0, s, 1, a, strips,

@@ -781,7 +781,7 @@ std::vector<std::array<int, 2>> tile_candidates(const GridDesc& g, int prec, int
     if (dim == 2) {
         std::vector<int> rows = {2, 4};
         if (prec == HH_C64 && mode != hh::M_RESID_RESTRICT) rows.push_back(8);
-        const bool persist_ok = mode != hh::M_PROLONG_JACOBI && mode != hh::M_RESID_RESTRICT;
+        const bool persist_ok = mode != hh::M_PROLONG_JACOBI;
         for (int r : rows) {
             c.push_back({r, 1});
             if (persist_ok) c.push_back({r, 2});
