@@ -382,6 +382,7 @@ class Options:
     nu_coarse: int = 8
     omega: float = 0.0          # Jacobi damping; 0 = 0.6 in 2D, 0.5 in 3D
     cycles_per_hss: int = 1
+    gamma: int = 1              # cycle index: 1 V-cycle, 2 W-cycle (Sec. 5.3 uses a W-cycle)
     restart: int = 30
     max_outer: int = 200
 
@@ -428,7 +429,9 @@ class Problem:
         return x + self.opts.omega * self.Dinv[l] * (b - self.AL[l] @ x)
 
     def vcycle(self, l, b):
-        """One V-cycle on A_L of level l from the zero initial guess (returns x)."""
+        """One multigrid cycle on A_L of level l from the zero initial guess (returns x):
+        a V-cycle for gamma = 1; for gamma = 2 (W-cycle) the coarse correction is two cycles
+        on the coarse problem, the second on the residual the first leaves."""
         o = self.opts
         x = np.zeros_like(b)
         if l == len(self.AL) - 1:
@@ -439,6 +442,8 @@ class Problem:
             x = self.jacobi(l, b, x)
         rc = self.P[l].T @ (b - self.AL[l] @ x)
         ec = self.vcycle(l + 1, rc)
+        for _ in range(o.gamma - 1):
+            ec = ec + self.vcycle(l + 1, rc - self.AL[l + 1] @ ec)
         x = x + self.P[l] @ ec
         for _ in range(o.nu_post):
             x = self.jacobi(l, b, x)

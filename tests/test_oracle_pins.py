@@ -258,6 +258,11 @@ def _dense_vcycle_operator(prob, l):
             Si = Sm @ Si
         return B
     Bc = _dense_vcycle_operator(prob, l + 1)
+    if o.gamma > 1:
+        # gamma cycles on the coarse problem: sum_{m < gamma} (I - Bc Ac)^m Bc
+        Ac = prob.AL[l + 1].toarray()
+        G = np.eye(Ac.shape[0]) - Bc @ Ac
+        Bc = sum(np.linalg.matrix_power(G, m) @ Bc for m in range(o.gamma))
     P = prob.P[l].toarray()
     E = np.linalg.matrix_power(Sm, o.nu_post) @ (np.eye(A.shape[0]) - P @ Bc @ P.T @ A) \
         @ np.linalg.matrix_power(Sm, o.nu_pre)
@@ -269,10 +274,11 @@ def _dense_vcycle_operator(prob, l):
     return B
 
 
+@pytest.mark.parametrize("gamma", [1, 2])
 @pytest.mark.parametrize("bc", [(S, S, S, S), (D, S, S, D)])
-def test_vcycle_matches_error_propagation_formula(bc):
+def test_vcycle_matches_error_propagation_formula(bc, gamma):
     g = O.Grid(2, 8, bc)
-    prob = O.Problem(g, 5.0, 0.0, 2.0, O.Options(levels=3, nu_pre=1, nu_post=2, nu_coarse=3))
+    prob = O.Problem(g, 5.0, 0.0, 2.0, O.Options(levels=3, nu_pre=1, nu_post=2, nu_coarse=3, gamma=gamma))
     B = _dense_vcycle_operator(prob, 0)
     rng = np.random.default_rng(5)
     b = (rng.standard_normal(g.N) + 1j * rng.standard_normal(g.N)) * g.free()
