@@ -441,6 +441,20 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
     except Exception as e:
         out["richardson_delta_hat_2"] = {"failed": str(e)}
 
+    # the paper's cycle type: W-cycles, one per HSS step, delta_hat = 2
+    try:
+        with hh.Problem(w2.dim, w2.n, w2.k, w2.delta, w2.delta_hat, w2.bc,
+                        hh.default_options(cycle_gamma=2, max_outer=400)) as pw:
+            pw.solve(b, w.tol)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, iw = pw.solve(b, w.tol)
+            tw = time.perf_counter() - t0
+        out["w_cycle_delta_hat_2"] = {"cycle": "W(2,2)", "solve_ms": 1e3 * tw, "outer_its": iw.outer_its,
+                                      "cycles": iw.vcycles, "rel_residual": iw.rel_residual}
+    except Exception as e:
+        out["w_cycle_delta_hat_2"] = {"failed": str(e)}
+
     # serving: Poisson arrivals of mixed 2D/3D requests through the solve server
     try:
         out["serving"] = measure_serving(hh, inputs, torch, SERVE_REQUESTS[0])

@@ -123,6 +123,9 @@ typedef struct {
                          /* with the first two post-sweeps) run as one kernel; same result    */
                          /* bit for bit as 0 (one kernel per sweep)                           */
     int outer;           /* hh_outer: HH_OUTER_FGMRES (default) or HH_OUTER_RICHARDSON      */
+    int cycle_gamma;     /* multigrid cycle index 1..4: 1 V-cycle (default), 2 W-cycle (the    */
+                         /* paper's cycle type, Sec. 5.3): each coarse correction is gamma    */
+                         /* cycles on the coarse problem, each on the residual left so far    */
 } hh_options;
 
 typedef struct {
@@ -257,7 +260,8 @@ HH_API hh_status hh_residual_restrict(hh_problem* p, int level, int precision, c
 /* x += P ec: prolongation of a level-(l+1) correction onto level l. */
 HH_API hh_status hh_prolong_correct(hh_problem* p, int level, int precision, const void* ec, void* x);
 
-/* x = one V-cycle on A_L of level 0 from the zero initial guess (cycles_per_hss ignored). */
+/* x = one multigrid cycle (V or W, cycle_gamma) on A_L of level 0 from the zero initial guess
+ * (cycles_per_hss ignored). */
 HH_API hh_status hh_vcycle(hh_problem* p, int precision, const void* b, void* x);
 
 /* rhs = (k-1)/(k+1) A_R u + 2k/(k+1) r on level 0 (Def. 4.1); u == NULL means u = 0. */

@@ -99,6 +99,7 @@ struct Hier {
     bool ready = false;
     size_t elem = 0;                  // bytes per complex entry
     std::vector<void*> xa, xb, b, t;  // per level: ping-pong iterates, right side, residual scratch
+    std::vector<void*> wk, wr;        // W-cycles (levels >= 1): kept correction, its residual
     void* r_lo = nullptr;             // level-0 copy of the preconditioner input
     void* rhs = nullptr;              // level-0 HSS right side
     void* ca = nullptr;               // extra level-0 buffers for cycles_per_hss > 1
@@ -248,13 +249,14 @@ hh_status build_tables(hh_problem* p, Hier& H) {
 
 // Device bytes of one precision's multigrid buffers for nb problems plus the coefficient
 // tables (matches ensure_hier and ensure_tables).
-size_t hier_bytes(const hh_grid* grid, int levels, int prec, int nb) {
+size_t hier_bytes(const hh_grid* grid, int levels, int prec, int nb, int gamma) {
     const size_t elem = prec == HH_C64 ? 8 : 16, B = (size_t)nb;
     size_t tot = 0;
     for (int l = 0; l < levels; ++l) {
         long long nn = (grid->n >> l) + 1;
         long long N = nn * nn * (grid->dim == 3 ? nn : 1);
         tot += 4 * (size_t)N * elem * B;  // xa, xb, b, t
+        if (gamma > 1 && l >= 1) tot += 2 * (size_t)N * elem * B;  // W-cycle correction and residual
         if (l == 0) tot += 5 * (size_t)N * elem * B;  // r_lo, rhs, ca, cb, cres
     }
     tot += sizeof(void*) * B;  // usrc
@@ -284,8 +286,14 @@ hh_status ensure_hier(hh_problem* p, int prec) {
     H.xb.assign(L, nullptr);
     H.b.assign(L, nullptr);
     H.t.assign(L, nullptr);
+    H.wk.assign(L, nullptr);
+    H.wr.assign(L, nullptr);
     for (int l = 0; l < L; ++l) {
         const size_t nbytes = (size_t)p->lv[l].N * p->nb * H.elem;
+        if (p->o.cycle_gamma > 1 && l >= 1) {
+            HH_TRY(dmalloc(p, &H.wk[l], nbytes));
+            HH_TRY(dmalloc(p, &H.wr[l], nbytes));
+        }
         HH_TRY(dmalloc(p, &H.xa[l], nbytes));
         HH_TRY(dmalloc(p, &H.xb[l], nbytes));
         HH_TRY(dmalloc(p, &H.b[l], nbytes));
@@ -564,6 +572,26 @@ struct MG {
         HH_TRY(resid_restrict(l, b, x, (V2*)H->b[l + 1]));
         V2* ec;
         HH_TRY(vcycle(l + 1, (const V2*)H->b[l + 1], nullptr, &ec));
+        if (p->o.cycle_gamma > 1) {
+            // W-cycle: further cycles on the coarse problem, each on the residual that the
+            // correction so far leaves, kept outside the coarse ping-pong buffers
+            const int c = l + 1;
+            V2* keep = (V2*)H->wk[c];
+            HH_LAUNCH(hh::launch_copy<T>(keep, ec, Nl(c), batch(c), s));
+            for (int g = 1; g < p->o.cycle_gamma; ++g) {
+                hh::MArgs<T> a = margs(c, R_AL);
+                a.x = keep;
+                a.z = (const V2*)H->b[c];
+                a.y = (V2*)H->wr[c];
+                a.alpha = Cx<T>{-1, 0};
+                a.beta = Cx<T>{1, 0};
+                HH_LAUNCH(march(hh::M_AXPBY, a));
+                V2* corr;
+                HH_TRY(vcycle(c, (const V2*)H->wr[c], nullptr, &corr));
+                HH_LAUNCH(hh::launch_add<T>(keep, corr, Nl(c), batch(c), s));
+            }
+            ec = keep;
+        }
         if (p->o.nu_post == 0) {
             HH_LAUNCH(hh::launch_prolong<T>(p->lv[l], ec, x, batch(l), s));
         } else if (p->o.nu_post >= 2 && fused2(l)) {
@@ -1174,6 +1202,7 @@ hh_status check_args(const hh_grid* grid, int nb, const double* k, const double*
         return fail(HH_ERR_INVALID, "tile_rows must be 0, 2, 4 or 8");
     if (o->autotune != 0 && o->autotune != 1) return fail(HH_ERR_INVALID, "autotune must be 0 or 1");
     if (o->fuse_sweeps != 0 && o->fuse_sweeps != 1) return fail(HH_ERR_INVALID, "fuse_sweeps must be 0 or 1");
+    if (o->cycle_gamma < 1 || o->cycle_gamma > 4) return fail(HH_ERR_INVALID, "cycle_gamma must be in 1..4");
     if (o->outer != HH_OUTER_FGMRES && o->outer != HH_OUTER_RICHARDSON)
         return fail(HH_ERR_INVALID, "outer must be HH_OUTER_FGMRES or HH_OUTER_RICHARDSON");
     if (!bc) return fail(HH_ERR_INVALID, "null bc");
@@ -1228,6 +1257,7 @@ void hh_options_default(hh_options* o) {
     o->autotune = 0;
     o->fuse_sweeps = 1;
     o->outer = HH_OUTER_FGMRES;
+    o->cycle_gamma = 1;
 }
 
 size_t hh_footprint_batch_bytes(const hh_grid* grid, const hh_options* o, int nb) {
@@ -1235,7 +1265,7 @@ size_t hh_footprint_batch_bytes(const hh_grid* grid, const hh_options* o, int nb
     const int bc0[6] = {0, 0, 0, 0, 0, 0};
     std::vector<double> one(nb, 1.0), zero(nb, 0.0);
     if (check_args(grid, nb, one.data(), zero.data(), one.data(), bc0, o) != HH_OK) return 0;
-    return hier_bytes(grid, o->levels, o->precision, nb) + krylov_bytes(grid, o->restart, nb);
+    return hier_bytes(grid, o->levels, o->precision, nb, o->cycle_gamma) + krylov_bytes(grid, o->restart, nb);
 }
 
 size_t hh_footprint_bytes(const hh_grid* grid, const hh_options* o) { return hh_footprint_batch_bytes(grid, o, 1); }

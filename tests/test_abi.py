@@ -31,7 +31,7 @@ def test_options_default(libhh):
     assert o.cycles_per_hss == 1 and o.omega == 0.0
     assert o.restart == 30 and o.precision == hh.HH_C64 and o.use_graphs == 1
     assert o.use_pdl == 1 and o.coarse_cluster_nodes == 100000 and o.tile_rows == 0 and o.autotune == 0
-    assert o.fuse_sweeps == 1 and o.outer == hh.HH_OUTER_FGMRES
+    assert o.fuse_sweeps == 1 and o.outer == hh.HH_OUTER_FGMRES and o.cycle_gamma == 1
 
 
 def test_footprint_bytes(libhh):
@@ -60,6 +60,13 @@ def test_invalid_arguments_rejected_on_host(libhh, dim, n, k, delta, dh, bc):
                                  ctypes.byref(out))
     assert st == -1 and not out.value
     assert libhh.hh_last_error()
+
+
+def test_footprint_counts_w_cycle_buffers(libhh):
+    v = hh.footprint_bytes(2, 256, hh.default_options(levels=4))
+    w = hh.footprint_bytes(2, 256, hh.default_options(levels=4, cycle_gamma=2))
+    # two complex64 vectors on each of levels 1..3
+    assert w - v == 2 * 8 * (129 ** 2 + 65 ** 2 + 33 ** 2)
 
 
 def test_footprint_is_linear_in_batch(libhh):
