@@ -118,10 +118,10 @@ typedef struct {
                          /* 2, 4 or 8; 0 = chosen from the grid size                          */
     int autotune;        /* 1: run hh_autotune for `precision` when the problem is created    */
     int fuse_sweeps;     /* 1: in 2D, on levels of at most 600000 nodes (all problems of a     */
-                         /* batch together), two consecutive Jacobi sweeps of the cycle (the  */
-                         /* HSS right side with the first two pre-sweeps, the prolongation    */
-                         /* with the first two post-sweeps) run as one kernel; same result    */
-                         /* bit for bit as 0 (one kernel per sweep)                           */
+                         /* batch together), consecutive steps of the cycle run as one kernel */
+                         /* (with V(2,*): the two pre-sweeps, or the HSS right side and them, */
+                         /* with the residual restriction; the prolongation with the first    */
+                         /* two post-sweeps); same result bit for bit as 0 (one kernel each)  */
     int outer;           /* hh_outer: HH_OUTER_FGMRES (default) or HH_OUTER_RICHARDSON      */
     int cycle_gamma;     /* multigrid cycle index 1..4: 1 V-cycle (default), 2 W-cycle (the    */
                          /* paper's cycle type, Sec. 5.3): each coarse correction is gamma    */
@@ -190,11 +190,13 @@ HH_API int hh_batch_size(const hh_problem* p);
  * preconditioner graph is captured again).
  * Every shape gives the same result bit for bit.  Choices are remembered per process for
  * (device, dim, level size, batch size, precision, kernel), so problems of the same shape
- * reuse them without timing.  Blocking.  shapes, if not NULL, receives levels x 10 x 2 ints:
+ * reuse them without timing.  Blocking.  shapes, if not NULL, receives levels x 12 x 2 ints:
  * for level l and kernel m (0 y = op x, 1 axpby, 2 Jacobi, 3 HSS first step, 4 two Jacobi
  * sweeps from 0, 5 prolongation + Jacobi, 6 residual + restriction, 7 prolongation + two
- * sweeps, 8 HSS first step + two sweeps, 9 coarsest-level solve), {rows, form} (for 9:
- * {cluster size, 0}) at [(l * 10 + m) * 2], 0 where nothing was tuned.
+ * sweeps, 8 HSS first step + two sweeps, 9 two sweeps from 0 + residual restriction, 10 HSS
+ * first step + two sweeps + residual restriction, 11 coarsest-level solve), {rows, form}
+ * (for 9, 10: {coarse rows per tile, 1}; for 11: {cluster size, 0}) at [(l * 12 + m) * 2],
+ * 0 where nothing was tuned.
  */
 HH_API hh_status hh_autotune(hh_problem* p, int precision, int* shapes);
 

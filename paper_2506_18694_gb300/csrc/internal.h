@@ -97,8 +97,11 @@ enum MarchMode {
     M_RESID_RESTRICT = 6, // y (coarse) = P^T (z - op x)
     // two sweeps in one pass (2D): the second sweep's operator is pc2 / c02 (A_L)
     M_PROLONG_JACOBI2 = 7,  // x~ = x + P ec;  x1 = x~ + omega D^{-1} (z - op x~);  y = x1 + omega D^{-1} (z - op x1)
-    M_HSS_FIRST2 = 8        // rhs = alpha (op x) + beta z;  x1 = omega D^{-1} rhs;  y = rhs,
+    M_HSS_FIRST2 = 8,       // rhs = alpha (op x) + beta z;  x1 = omega D^{-1} rhs;  y = rhs,
                             // y2 = x1 + omega D^{-1} (rhs - A_L x1)
+    // two pre-sweeps and the residual restriction in one pass (2D, march2rr.cu)
+    M_JACOBI2_ZERO_RR = 9,  // y = two sweeps on A_L x = z from 0;  yc (coarse) = P^T (z - A_L y)
+    M_HSS_FIRST2_RR = 10    // as M_HSS_FIRST2 (y = rhs, y2 = x2), and yc = P^T (rhs - A_L x2)
 };
 
 // Coefficients of one operator on one level for one problem of a batch (a device table
@@ -142,6 +145,7 @@ template <typename T> struct MArgs {
     const Cx<T>* bw3;    // 3D: device boundary-class weights, problem b at b * kClass3 * kClass3Len
     const PCoef<T>* pc2; // second operator of the fused two-sweep modes (nullptr: c02)
     PCoef<T> c02;
+    vec2<T>* yc;         // coarse output of the *_RR modes (problem b at b * bsc)
     const vec2<T>* x;    // stencil input (ignored for M_JACOBI2_ZERO; nullptr = 0 when xzero)
     const vec2<T>* z;    // right side / second vector
     const vec2<T>* ec;   // coarse correction (M_PROLONG_JACOBI)
@@ -200,6 +204,9 @@ __device__ __forceinline__ bool problem_skipped(const MArgs<T>& a, int b) {
 
 template <typename T>
 cudaError_t launch_march2(int mode, const MArgs<T>& a, cudaStream_t s);
+// the pre-smoothing + residual-restriction passes (M_JACOBI2_ZERO_RR, M_HSS_FIRST2_RR)
+template <typename T>
+cudaError_t launch_march2rr(int mode, const MArgs<T>& a, cudaStream_t s);
 
 // ---- fused 3D tile kernels (march3.cu): modes as above except M_RESID_RESTRICT ----
 template <typename T>

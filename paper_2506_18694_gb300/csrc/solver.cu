@@ -88,8 +88,8 @@ int n_hss(double k, double theta) {
     return (int)std::ceil(v);
 }
 
-constexpr int kModes = 10;      // hh::MarchMode values 0..8 and the coarsest-level solve
-constexpr int kCoarseMode = 9;
+constexpr int kModes = 12;      // hh::MarchMode values 0..10 and the coarsest-level solve
+constexpr int kCoarseMode = 11;
 
 // Operators with a coefficient table (per problem and level).
 enum Role { R_K = 0, R_M, R_MG, R_AL, R_AR, R_B, R_BHAT, R_COUNT };
@@ -417,6 +417,7 @@ struct MG {
             t.tile_rows = tab[l][mode][0];
             t.tile_form = tab[l][mode][1];
         }
+        if (mode == hh::M_JACOBI2_ZERO_RR || mode == hh::M_HSS_FIRST2_RR) return hh::launch_march2rr<T>(mode, t, s);
         return d2() ? hh::launch_march2<T>(mode, t, s) : hh::launch_march3<T>(mode, t, s);
     }
 
@@ -474,6 +475,30 @@ struct MG {
         a.z = b;
         a.y = xout;
         HH_LAUNCH(march(hh::M_PROLONG_JACOBI2, a));
+        return HH_OK;
+    }
+    // pre-smoothing passes that also restrict the residual (2D levels where fused2 holds)
+    bool fused_rr(int l) const { return fused2(l) && p->o.nu_pre == 2 && l + 1 < p->o.levels; }
+    // xout = two sweeps from 0 on A_L x = b, rc = P^T (b - A_L xout), in one pass
+    hh_status jacobi2_zero_rr(int l, const V2* b, V2* xout, V2* rc) {
+        hh::MArgs<T> a = margs2(l, R_AL);
+        a.z = b;
+        a.y = xout;
+        a.yc = rc;
+        HH_LAUNCH(march(hh::M_JACOBI2_ZERO_RR, a));
+        return HH_OK;
+    }
+    // the HSS right side, two sweeps and the restricted residual, in one pass
+    hh_status hss_first2_rr(const V2* u, const V2* r, V2* rhs, V2* x2, V2* rc) {
+        hh::MArgs<T> a = margs2(0, R_AR);
+        a.x = u;
+        a.xzero = u == nullptr;
+        a.z = r;
+        a.y = rhs;
+        a.y2 = x2;
+        a.yc = rc;
+        a.use_pc_ab = 1;
+        HH_LAUNCH(march(hh::M_HSS_FIRST2_RR, a));
         return HH_OK;
     }
     // rhs = c1 A_R u + c2 r and two Jacobi sweeps from 0 on A_L x = rhs, in one pass
@@ -541,8 +566,9 @@ struct MG {
     }
 
     // One V-cycle on level l for right side b from x = 0; result buffer in *out.
-    // xstart: the first `done` pre-smoothing sweeps were already done and sit in xstart.
-    hh_status vcycle(int l, const V2* b, V2* xstart, V2** out, int done = 1) {
+    // xstart: the first `done` pre-smoothing sweeps were already done and sit in xstart;
+    // restricted: all pre-sweeps are done and the coarse residual already sits in H->b[l + 1].
+    hh_status vcycle(int l, const V2* b, V2* xstart, V2** out, int done = 1, bool restricted = false) {
         const int L = p->o.levels;
         if (l == L - 1) {
             V2* x = (V2*)H->xa[l];
@@ -563,13 +589,19 @@ struct MG {
             return HH_OK;
         }
         V2* x;
-        if (xstart) {
+        if (restricted) {
+            x = xstart;
+        } else if (xstart) {
             x = xstart;
             HH_TRY(smooth(l, b, p->o.nu_pre - done, &x));
+        } else if (fused_rr(l)) {
+            x = (V2*)H->xa[l];
+            HH_TRY(jacobi2_zero_rr(l, b, x, (V2*)H->b[l + 1]));
+            restricted = true;
         } else {
             HH_TRY(smooth_from_zero(l, b, p->o.nu_pre, &x));
         }
-        HH_TRY(resid_restrict(l, b, x, (V2*)H->b[l + 1]));
+        if (!restricted) HH_TRY(resid_restrict(l, b, x, (V2*)H->b[l + 1]));
         V2* ec;
         HH_TRY(vcycle(l + 1, (const V2*)H->b[l + 1], nullptr, &ec));
         if (p->o.cycle_gamma > 1) {
@@ -609,10 +641,11 @@ struct MG {
         return HH_OK;
     }
 
-    // cycles_per_hss V-cycles for A_L x = b; the first may start from xstart (`done` sweeps).
-    hh_status mg_solve(const V2* b, V2* xstart, V2** out, int done = 1) {
+    // cycles_per_hss V-cycles for A_L x = b; the first may start from xstart (`done` sweeps,
+    // `restricted` as in vcycle).
+    hh_status mg_solve(const V2* b, V2* xstart, V2** out, int done = 1, bool restricted = false) {
         V2* x;
-        HH_TRY(vcycle(0, b, xstart, &x, done));
+        HH_TRY(vcycle(0, b, xstart, &x, done, restricted));
         const long long N = Nl(0);
         for (int c = 1; c < p->o.cycles_per_hss; ++c) {
             // keep x outside the level-0 ping-pong buffers the next cycle overwrites
@@ -646,7 +679,10 @@ struct MG {
             if (fuse) {
                 // the first pre-smoothing sweep of the fine level is fused with the right side
                 V2* x1 = (u == (V2*)H->xa[0]) ? (V2*)H->xb[0] : (V2*)H->xa[0];
-                if (two) {
+                if (two && fused_rr(0)) {
+                    HH_TRY(hss_first2_rr(u, (const V2*)H->r_lo, (V2*)H->rhs, x1, (V2*)H->b[1]));
+                    HH_TRY(mg_solve((const V2*)H->rhs, x1, &u, 2, true));
+                } else if (two) {
                     HH_TRY(hss_first2(u, (const V2*)H->r_lo, (V2*)H->rhs, x1));
                     HH_TRY(mg_solve((const V2*)H->rhs, x1, &u, 2));
                 } else {
@@ -806,6 +842,10 @@ std::vector<std::array<int, 2>> tile_candidates(const GridDesc& g, int prec, int
         if (dim == 2) c = {{2, 1}, {4, 1}};
         return c;
     }
+    if (mode == hh::M_JACOBI2_ZERO_RR || mode == hh::M_HSS_FIRST2_RR) {
+        if (dim == 2) c = {{1, 1}, {2, 1}};  // coarse rows per tile
+        return c;
+    }
     if (dim == 2) {
         std::vector<int> rows = {2, 4};
         if (prec == HH_C64 && mode != hh::M_RESID_RESTRICT) rows.push_back(8);
@@ -828,8 +868,11 @@ hh_status time_shape(hh_problem* p, int l, int mode, const std::array<int, 2>& c
     MG<T> m = make_mg<T>(p, prec, p->s);
     const bool fgm = prec == HH_C128 && l == 0 && (mode == hh::M_APPLY || mode == hh::M_AXPBY) &&
                      !p->hier[HH_C128].ready;
-    const int role = (mode == hh::M_HSS_FIRST || mode == hh::M_HSS_FIRST2) ? R_AR : (mode == hh::M_APPLY ? R_B : R_AL);
-    hh::MArgs<T> a = (mode == hh::M_PROLONG_JACOBI2 || mode == hh::M_HSS_FIRST2) ? m.margs2(l, role) : m.margs(l, role);
+    const bool hssm = mode == hh::M_HSS_FIRST || mode == hh::M_HSS_FIRST2 || mode == hh::M_HSS_FIRST2_RR;
+    const int role = hssm ? R_AR : (mode == hh::M_APPLY ? R_B : R_AL);
+    const bool two = mode == hh::M_PROLONG_JACOBI2 || mode == hh::M_HSS_FIRST2 || mode == hh::M_JACOBI2_ZERO_RR ||
+                     mode == hh::M_HSS_FIRST2_RR;
+    hh::MArgs<T> a = two ? m.margs2(l, role) : m.margs(l, role);
     if (fgm) {
         // the FP64 outer operator: Krylov buffers stand in for the hierarchy
         a.x = (const V2*)p->V;
@@ -843,8 +886,9 @@ hh_status time_shape(hh_problem* p, int l, int mode, const std::array<int, 2>& c
         a.y2 = (V2*)H.t[l];
         if (l + 1 < p->o.levels) a.ec = (const V2*)H.xa[l + 1];
         if (mode == hh::M_RESID_RESTRICT) a.y = (V2*)H.t[l + 1];
+        if (mode == hh::M_JACOBI2_ZERO_RR || mode == hh::M_HSS_FIRST2_RR) a.yc = (V2*)H.t[l + 1];
     }
-    a.use_pc_ab = mode == hh::M_HSS_FIRST || mode == hh::M_HSS_FIRST2;
+    a.use_pc_ab = hssm;
     a.alpha = Cx<T>{-1, 0};
     a.beta = Cx<T>{1, 0};
     a.tile_rows = cand[0];
@@ -852,6 +896,7 @@ hh_status time_shape(hh_problem* p, int l, int mode, const std::array<int, 2>& c
     if (mode == kCoarseMode) a.y = (V2*)p->hier[prec].xa[l];
     auto launch = [&]() {
         if (mode == kCoarseMode) return hh::launch_coarse_solve<T>(a, p->o.nu_coarse, p->s);
+        if (mode == hh::M_JACOBI2_ZERO_RR || mode == hh::M_HSS_FIRST2_RR) return hh::launch_march2rr<T>(mode, a, p->s);
         return m.d2() ? hh::launch_march2<T>(mode, a, p->s) : hh::launch_march3<T>(mode, a, p->s);
     };
     cudaEvent_t e0, e1;
@@ -890,13 +935,15 @@ hh_status autotune(hh_problem* p, int prec) {
                                         (prec == HH_C64 ? hh::coarse_fits<float>(p->lv[l])
                                                         : hh::coarse_fits<double>(p->lv[l]));
             if (mode == kCoarseMode && (l != L - 1 || !coarse_cluster)) continue;
-            if ((mode == hh::M_PROLONG_JACOBI || mode == hh::M_RESID_RESTRICT || mode == hh::M_PROLONG_JACOBI2) &&
-                l == L - 1)
-                continue;
-            if ((mode == hh::M_RESID_RESTRICT || mode == hh::M_PROLONG_JACOBI2 || mode == hh::M_HSS_FIRST2) &&
+            const bool needs_coarser = mode == hh::M_PROLONG_JACOBI || mode == hh::M_RESID_RESTRICT ||
+                                       mode == hh::M_PROLONG_JACOBI2 || mode == hh::M_JACOBI2_ZERO_RR ||
+                                       mode == hh::M_HSS_FIRST2_RR;
+            if (needs_coarser && l == L - 1) continue;
+            if ((mode == hh::M_RESID_RESTRICT || mode == hh::M_PROLONG_JACOBI2 || mode == hh::M_HSS_FIRST2 ||
+                 mode == hh::M_JACOBI2_ZERO_RR || mode == hh::M_HSS_FIRST2_RR) &&
                 p->grid.dim == 3)
                 continue;
-            if ((mode == hh::M_HSS_FIRST || mode == hh::M_HSS_FIRST2) && l != 0) continue;
+            if ((mode == hh::M_HSS_FIRST || mode == hh::M_HSS_FIRST2 || mode == hh::M_HSS_FIRST2_RR) && l != 0) continue;
             work.emplace_back(prec, l, mode);
         }
     if (prec == HH_C64) {

@@ -243,7 +243,7 @@ class Problem:
         _check(self._lib.hh_prepare(self._p))
 
     MODES = ("apply", "axpby", "jacobi", "hss_first", "jacobi2_zero", "prolong_jacobi", "resid_restrict",
-             "prolong_jacobi2", "hss_first2", "coarse")
+             "prolong_jacobi2", "hss_first2", "jacobi2_zero_rr", "hss_first2_rr", "coarse")
 
     def autotune(self, precision=None):
         """Time the tile shapes of every stencil kernel and keep the fastest; returns

@@ -44,6 +44,9 @@ def test_tuned_solve_equals_untuned(libhh, dim, n, bc, batch, prec):
         if mode == "coarse":
             assert rows in (1, 2, 4, 8, 16) and form == 0 and l == 2
             continue
+        if mode.endswith("_rr"):
+            assert rows in (1, 2) and form == 1
+            continue
         assert rows in (2, 4, 8) and form in (0, 1, 2)
         assert mode != "resid_restrict" or dim == 2
     assert torch.equal(u0, u1)
