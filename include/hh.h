@@ -126,6 +126,10 @@ typedef struct {
     int cycle_gamma;     /* multigrid cycle index 1..4: 1 V-cycle (default), 2 W-cycle (the    */
                          /* paper's cycle type, Sec. 5.3): each coarse correction is gamma    */
                          /* cycles on the coarse problem, each on the residual left so far    */
+    int tile_form;       /* 2D stencil kernels: 0 = chosen from the grid size, 1 = one tile  */
+                         /* per warp, 2 = persistent warps walking the tiles (each loads its  */
+                         /* next tile while computing the current one); same result bit for  */
+                         /* bit; the autotuner's choices override it; ignored in 3D           */
 } hh_options;
 
 typedef struct {

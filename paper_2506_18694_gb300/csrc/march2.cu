@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(128) k_march2p(const __grid_constant__ MArgs<T
     if (t >= tiles) return;
     if constexpr (!BATCH) {
         const PCoef<T>& c = a.c0;
-        const VPtrs<T> v = problem_ptrs(a, 0, false);
+        const VPtrs<T> v = problem_ptrs(a, 0, MODE == M_RESID_RESTRICT);
         Tile2<T, MODE, ROWS> cur;
         tile_load<T, MODE, ROWS>(a, v, t % strips, t / strips, cur);
         for (; t < tiles; t += W) {
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(128) k_march2p(const __grid_constant__ MArgs<T
         split(t, &b, &strip, &cy);
         Tile2<T, MODE, ROWS> cur;
         bool have = !problem_skipped(a, b);
-        if (have) tile_load<T, MODE, ROWS>(a, problem_ptrs(a, b, false), strip, cy, cur);
+        if (have) tile_load<T, MODE, ROWS>(a, problem_ptrs(a, b, MODE == M_RESID_RESTRICT), strip, cy, cur);
         for (; t < tiles; t += W) {
             Tile2<T, MODE, ROWS> nxt;
             const int tn = t + W;
@@ -419,9 +419,9 @@ __global__ void __launch_bounds__(128) k_march2p(const __grid_constant__ MArgs<T
             if (tn < tiles) {
                 split(tn, &bn, &sn, &cn);
                 next = !problem_skipped(a, bn);
-                if (next) tile_load<T, MODE, ROWS>(a, problem_ptrs(a, bn, false), sn, cn, nxt);
+                if (next) tile_load<T, MODE, ROWS>(a, problem_ptrs(a, bn, MODE == M_RESID_RESTRICT), sn, cn, nxt);
             }
-            if (have) tile_compute<T, MODE, ROWS>(a, a.pc[b], problem_ptrs(a, b, false), strip, cy, cur);
+            if (have) tile_compute<T, MODE, ROWS>(a, a.pc[b], problem_ptrs(a, b, MODE == M_RESID_RESTRICT), strip, cy, cur);
             cur = nxt;
             have = next;
             b = bn;

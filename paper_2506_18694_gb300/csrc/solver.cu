@@ -378,6 +378,7 @@ struct MG {
         a.bsc = l + 1 < p->o.levels ? Nl(l + 1) : 0;
         a.omega = omega;
         a.tile_rows = p->o.tile_rows;
+        a.tile_form = p->o.tile_form;
         a.hss_it = p->nb == 1 ? -1 : hss_it;
         a.nhss = p->d_nhss;
         a.active = active_flags(p);
@@ -1247,6 +1248,7 @@ hh_status check_args(const hh_grid* grid, int nb, const double* k, const double*
     if (o->coarse_cluster_nodes < 0) return fail(HH_ERR_INVALID, "coarse_cluster_nodes < 0");
     if (o->tile_rows != 0 && o->tile_rows != 2 && o->tile_rows != 4 && o->tile_rows != 8)
         return fail(HH_ERR_INVALID, "tile_rows must be 0, 2, 4 or 8");
+    if (o->tile_form < 0 || o->tile_form > 2) return fail(HH_ERR_INVALID, "tile_form must be 0, 1 or 2");
     if (o->autotune != 0 && o->autotune != 1) return fail(HH_ERR_INVALID, "autotune must be 0 or 1");
     if (o->fuse_sweeps != 0 && o->fuse_sweeps != 1) return fail(HH_ERR_INVALID, "fuse_sweeps must be 0 or 1");
     if (o->cycle_gamma < 1 || o->cycle_gamma > 4) return fail(HH_ERR_INVALID, "cycle_gamma must be in 1..4");
@@ -1305,6 +1307,7 @@ void hh_options_default(hh_options* o) {
     o->fuse_sweeps = 1;
     o->outer = HH_OUTER_FGMRES;
     o->cycle_gamma = 1;
+    o->tile_form = 0;
 }
 
 size_t hh_footprint_batch_bytes(const hh_grid* grid, const hh_options* o, int nb) {

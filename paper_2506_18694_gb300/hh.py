@@ -44,6 +44,7 @@ class Options(ctypes.Structure):
         ("precision", ctypes.c_int), ("use_graphs", ctypes.c_int), ("use_pdl", ctypes.c_int),
         ("coarse_cluster_nodes", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
         ("fuse_sweeps", ctypes.c_int), ("outer", ctypes.c_int), ("cycle_gamma", ctypes.c_int),
+        ("tile_form", ctypes.c_int),
     ]
 
 

@@ -85,8 +85,14 @@ def test_batched_host_solve_and_zero_member(libhh):
 
 
 @pytest.mark.parametrize("prec", [hh.HH_C128, hh.HH_C64])
-@pytest.mark.parametrize("dim,n,bc", [(2, 72, (S, S, D, S)), (3, 12, (S, S, S, S, S, D))])
-def test_batched_building_blocks_equal_solo(libhh, prec, dim, n, bc):
+@pytest.mark.parametrize("dim,n,bc,form", [
+    (2, 72, (S, S, D, S), 0), (2, 72, (S, S, D, S), 1), (2, 72, (S, S, D, S), 2), (3, 12, (S, S, S, S, S, D), 0),
+], ids=["2d", "2d-tile", "2d-persistent", "3d"])
+def test_batched_building_blocks_equal_solo(libhh, prec, dim, n, bc, form):
+    """Batched kernels against batches of one; the batch runs the tile form `form`
+    (persistent warps walk every problem's tiles), the problems of one the automatic form.
+    The coarse output of the residual restriction sits in a larger buffer whose tail must
+    stay untouched."""
     dt = torch.complex128 if prec == hh.HH_C128 else torch.complex64
     g = O.Grid(dim, n, bc)
     nb = len(MIX)
@@ -96,13 +102,16 @@ def test_batched_building_blocks_equal_solo(libhh, prec, dim, n, bc):
     gc = O.Grid(dim, n // 2, bc)
     ec = np.stack([inputs.random_complex(gc.N, 950 + b) for b in range(nb)])
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a.reshape(-1))).to(dt).cuda()
-    with _batch(dim, n, bc, MIX, levels=L, precision=prec) as pb:
+    nc = nb * gc.N
+    guarded = torch.full((nc * 16,), complex(7.0, -3.0), dtype=dt).cuda()
+    with _batch(dim, n, bc, MIX, levels=L, precision=prec, tile_form=form) as pb:
         out_b = {
             "AL": pb.apply(0, "AL", dev(x)), "B": pb.apply(1, "B", dev(ec)),
             "jac": pb.jacobi(0, dev(r), dev(x)), "jac0": pb.jacobi(0, dev(r)),
-            "rr": pb.residual_restrict(0, dev(r), dev(x)), "pc": pb.prolong_correct(0, dev(ec), dev(x)),
+            "rr": pb.residual_restrict(0, dev(r), dev(x), guarded[:nc]), "pc": pb.prolong_correct(0, dev(ec), dev(x)),
             "vc": pb.vcycle(dev(r)), "hr": pb.hss_rhs(dev(x), dev(r)),
         }
+        assert bool((guarded[nc:] == complex(7.0, -3.0)).all()), "write past the coarse output"
         out_b = {k: v.cpu().numpy().reshape(nb, -1) for k, v in out_b.items()}
         xd, rd = (torch.from_numpy(a.reshape(-1)).cuda() for a in (x, r))
         dots = pb.dot(xd, rd)
