@@ -33,6 +33,7 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--rows", type=int, default=0, help="tile rows/planes (0 = automatic)")
+    ap.add_argument("--form", type=int, default=0, help="tile form (options.tile_form)")
     ap.add_argument("--batch", type=int, default=1, help="problems in the batch (vectors nb x nodes)")
     ap.add_argument("--autotune", action="store_true", help="tune tile shapes first")
     args = ap.parse_args(argv)
@@ -44,7 +45,8 @@ def main(argv=None):
     levels = 4 if args.kernel == "vcycle" else 2
     kk = k if args.batch == 1 else [k] * args.batch
     p = hh.Problem(args.dim, args.n, kk, 0.0, k, bc,
-                   hh.default_options(precision=prec, levels=levels, restart=1, tile_rows=args.rows))
+                   hh.default_options(precision=prec, levels=levels, restart=1, tile_rows=args.rows,
+                                                    tile_form=args.form))
     if args.autotune:
         p.autotune()
     N = p.size()
@@ -71,7 +73,7 @@ def main(argv=None):
     end.synchronize()
     t = start.elapsed_time(end) / args.reps / 1e3
     out = {"kernel": args.kernel, "dim": args.dim, "n": args.n, "batch": args.batch, "nodes": N, "prec": args.prec,
-           "rows": args.rows, "autotune": args.autotune, "us": t * 1e6}
+           "rows": args.rows, "form": args.form, "autotune": args.autotune, "us": t * 1e6}
     if BYTES[args.kernel] is not None:
         byt = BYTES[args.kernel](e, args.dim) * N
         out.update({"bytes": byt, "gbs": byt / t / 1e9})
