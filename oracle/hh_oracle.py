@@ -14,8 +14,9 @@ indefinite Helmholtz equation", arXiv 2506.18694):
   can serve as an independent check);
 * the gamma = k HSS iteration of Def. 3.1 (Eq. "primal-hss-system") and the
   shifted-HSS preconditioner of Def. 4.1 (Eq. "HSSpc primal"), whose inner
-  systems are approximated here by a multigrid V-cycle with scaled Jacobi
-  smoothing, prolongation by bi/trilinear interpolation and restriction R = P^T;
+  systems are approximated here by a multigrid V- or W-cycle with scaled Jacobi
+  smoothing, or GMRES with a Jacobi preconditioner as the smoother (Sec. 5.3),
+  prolongation by bi/trilinear interpolation and restriction R = P^T;
 * flexible GMRES (Saad 1993, used as the outer method in Sec. 5.1) with right
   preconditioning, modified Gram-Schmidt and Givens rotations;
 * a direct sparse LU solve of the same discrete system, which is the exact
@@ -383,6 +384,8 @@ class Options:
     omega: float = 0.0          # Jacobi damping; 0 = 0.6 in 2D, 0.5 in 3D
     cycles_per_hss: int = 1
     gamma: int = 1              # cycle index: 1 V-cycle, 2 W-cycle (Sec. 5.3 uses a W-cycle)
+    smoother: str = "jacobi"    # "jacobi": nu scaled-Jacobi sweeps; "gmres": nu iterations of
+                                # GMRES with a Jacobi preconditioner (Sec. 5.3's smoother)
     restart: int = 30
     max_outer: int = 200
 
@@ -428,6 +431,46 @@ class Problem:
         """One scaled-Jacobi sweep x <- x + omega D^{-1} (b - A_L x), D = diag(A_L)."""
         return x + self.opts.omega * self.Dinv[l] * (b - self.AL[l] @ x)
 
+    def gmres_smooth(self, l, b, x, s):
+        """s iterations of GMRES on the Jacobi-preconditioned system D^{-1} A_L x = D^{-1} b
+        of level l, started from x, without restart (the smoother of Sec. 5.3; preconditioner
+        applied on the left, D = diag(A_L)).  The result is x + V y, where the columns of V
+        are an orthonormal basis of the Krylov space K_s(D^{-1} A_L, z0), z0 = D^{-1}(b - A_L x),
+        and y minimises ||D^{-1}(b - A_L (x + V y))||_2 = ||beta e1 - H y||_2 (Arnoldi relation
+        D^{-1} A_L V_s = V_{s+1} H).  Arnoldi by modified Gram-Schmidt; the small least-squares
+        problem by numpy's lstsq.  The loop stops early at a breakdown (h_{j+1,j} = 0 up to
+        rounding: the Krylov space is invariant and the minimiser solves the system)."""
+        A, dinv = self.AL[l], self.Dinv[l]
+        z0 = dinv * (b - A @ x)
+        beta = np.linalg.norm(z0)
+        if s == 0 or beta == 0.0:
+            return x
+        V = [z0 / beta]
+        H = np.zeros((s + 1, s), dtype=complex)
+        m = s
+        for j in range(s):
+            w = dinv * (A @ V[j])
+            for i in range(j + 1):
+                H[i, j] = np.vdot(V[i], w)
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j].real <= 1e-14 * beta:
+                m = j + 1
+                break
+            V.append(w / H[j + 1, j])
+        rhs = np.zeros(m + 1, dtype=complex)
+        rhs[0] = beta
+        y = np.linalg.lstsq(H[:m + 1, :m], rhs, rcond=None)[0]
+        return x + sum(y[i] * V[i] for i in range(m))
+
+    def smooth(self, l, b, x, nu):
+        """nu smoothing steps on level l: scaled-Jacobi sweeps, or GMRES(nu) with Jacobi."""
+        if self.opts.smoother == "gmres":
+            return self.gmres_smooth(l, b, x, nu)
+        for _ in range(nu):
+            x = self.jacobi(l, b, x)
+        return x
+
     def vcycle(self, l, b):
         """One multigrid cycle on A_L of level l from the zero initial guess (returns x):
         a V-cycle for gamma = 1; for gamma = 2 (W-cycle) the coarse correction is two cycles
@@ -435,19 +478,14 @@ class Problem:
         o = self.opts
         x = np.zeros_like(b)
         if l == len(self.AL) - 1:
-            for _ in range(o.nu_coarse):
-                x = self.jacobi(l, b, x)
-            return x
-        for _ in range(o.nu_pre):
-            x = self.jacobi(l, b, x)
+            return self.smooth(l, b, x, o.nu_coarse)
+        x = self.smooth(l, b, x, o.nu_pre)
         rc = self.P[l].T @ (b - self.AL[l] @ x)
         ec = self.vcycle(l + 1, rc)
         for _ in range(o.gamma - 1):
             ec = ec + self.vcycle(l + 1, rc - self.AL[l + 1] @ ec)
         x = x + self.P[l] @ ec
-        for _ in range(o.nu_post):
-            x = self.jacobi(l, b, x)
-        return x
+        return self.smooth(l, b, x, o.nu_post)
 
     def mg_solve(self, b):
         """cycles_per_hss V-cycles for A_L x = b starting from x = 0."""

@@ -541,3 +541,87 @@ def test_richardson_hss_converges_to_lu():
     assert rel <= 1e-10 and its < 200
     assert np.linalg.norm(x - ref) <= 1e-7 * np.linalg.norm(ref)
     assert all(h1 < h0 for h0, h1 in zip(hist, hist[1:]))
+
+
+# --------------------------------------------------------------------- GMRES smoother
+def _gmres_case(n, bc, seed):
+    g = O.Grid(2, n, bc)
+    prob = O.Problem(g, 6.0, 0.0, 3.0, O.Options(levels=1, smoother="gmres"))
+    rng = np.random.default_rng(seed)
+    b = (rng.standard_normal(g.N) + 1j * rng.standard_normal(g.N)) * g.free()
+    x0 = (rng.standard_normal(g.N) + 1j * rng.standard_normal(g.N)) * g.free()
+    return g, prob, b, x0
+
+
+def test_gmres_smoother_full_krylov_space_solves():
+    """With as many iterations as free unknowns the Krylov space is the whole free space, so
+    GMRES from any starting vector returns the solution of A_L x = b (sparse LU)."""
+    g, prob, b, x0 = _gmres_case(4, (S, D, S, S), 30)
+    nf = int(g.free().sum())
+    x = prob.gmres_smooth(0, b, x0, nf)
+    ex = prob.lu("AL")(b)
+    assert np.linalg.norm(x - ex) <= 1e-8 * np.linalg.norm(ex)
+
+
+def test_gmres_smoother_one_step_closed_form():
+    """One iteration is the minimal-residual step x0 + alpha z0 with z0 = D^{-1}(b - A x0),
+    w = D^{-1} A z0 and alpha = (w^H z0) / (w^H w), the least-squares fit of z0 by w."""
+    g, prob, b, x0 = _gmres_case(8, (S, S, D, S), 31)
+    A, dinv = prob.AL[0], prob.Dinv[0]
+    z0 = dinv * (b - A @ x0)
+    w = dinv * (A @ z0)
+    alpha = np.vdot(w, z0) / np.vdot(w, w)
+    ref = x0 + alpha * z0
+    assert np.linalg.norm(prob.gmres_smooth(0, b, x0, 1) - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_gmres_smoother_minimises_over_krylov_space():
+    """After s = 3 iterations the preconditioned residual r is orthogonal to M K_3 (M = D^{-1} A,
+    K_3 spanned by z0, M z0, M^2 z0: the normal equations of the minimisation), no larger than
+    at other points of x0 + K_3 (random ones and three damped Jacobi sweeps), and it does not
+    grow with the number of iterations."""
+    g, prob, b, x0 = _gmres_case(8, (S, S, S, S), 32)
+    A, dinv = prob.AL[0], prob.Dinv[0]
+    M = lambda v: dinv * (A @ v)
+    res = lambda x: dinv * (b - A @ x)
+    z0 = res(x0)
+    K = [z0, M(z0), M(M(z0))]
+    x3 = prob.gmres_smooth(0, b, x0, 3)
+    r3 = res(x3)
+    for v in K:
+        mv = M(v)
+        assert abs(np.vdot(mv, r3)) <= 1e-10 * np.linalg.norm(mv) * np.linalg.norm(z0)
+    rng = np.random.default_rng(33)
+    for _ in range(30):
+        c = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+        c *= 0.1 * np.linalg.norm(z0) / np.linalg.norm(c[0] * K[0] + c[1] * K[1] + c[2] * K[2])
+        xc = x3 + c[0] * K[0] + c[1] * K[1] + c[2] * K[2]
+        assert np.linalg.norm(r3) <= np.linalg.norm(res(xc)) * (1 + 1e-12)
+    xj = x0
+    for _ in range(3):
+        xj = prob.jacobi(0, b, xj)
+    assert np.linalg.norm(r3) <= np.linalg.norm(res(xj))
+    norms = [np.linalg.norm(res(prob.gmres_smooth(0, b, x0, s))) for s in range(7)]
+    assert all(norms[s + 1] <= norms[s] * (1 + 1e-12) for s in range(6))
+
+
+def test_gmres_cycle_two_grid_exact_coarse_and_homogeneous():
+    """A two-level cycle with no fine smoothing and GMRES on the coarse level with as many
+    iterations as coarse unknowns is P A_c^{-1} P^T b exactly; the cycle with smoothing is
+    homogeneous (b -> c b gives x -> c x for complex c), as GMRES is."""
+    g = O.Grid(2, 8, (S, S, D, S))
+    rng = np.random.default_rng(34)
+    b = (rng.standard_normal(g.N) + 1j * rng.standard_normal(g.N)) * g.free()
+    nfc = int(g.coarse().free().sum())
+    prob = O.Problem(g, 6.0, 0.0, 3.0, O.Options(levels=2, nu_pre=0, nu_post=0, nu_coarse=nfc, smoother="gmres"))
+    Ac = prob.AL[1].toarray()
+    fc = prob.free[1]
+    ec = np.zeros(g.coarse().N, dtype=complex)
+    ec[fc] = np.linalg.solve(Ac[np.ix_(fc, fc)], (prob.P[0].T @ b)[fc])
+    ref = prob.P[0] @ ec
+    assert np.linalg.norm(prob.vcycle(0, b) - ref) <= 1e-9 * np.linalg.norm(ref)
+    prob2 = O.Problem(g, 6.0, 0.0, 3.0, O.Options(levels=2, nu_pre=3, nu_post=2, nu_coarse=4, smoother="gmres",
+                                                   gamma=2))
+    c = 0.7 - 2.1j
+    x = prob2.vcycle(0, b)
+    assert np.linalg.norm(prob2.vcycle(0, c * b) - c * x) <= 1e-12 * abs(c) * np.linalg.norm(x)
