@@ -80,6 +80,8 @@ typedef enum { HH_C128 = 0, HH_C64 = 1 } hh_precision;
  * the text after Def. 4.1 defines (the stationary iteration of the paper's Richardson
  * tables, Sec. 5.2); restart is ignored for the latter. */
 typedef enum { HH_OUTER_FGMRES = 0, HH_OUTER_RICHARDSON = 1 } hh_outer;
+/* multigrid smoother (options.smoother) */
+typedef enum { HH_SMOOTH_JACOBI = 0, HH_SMOOTH_GMRES = 1 } hh_smoother;
 
 /* Operators that hh_apply can apply (coefficient triples of the weak forms). */
 typedef enum {
@@ -130,6 +132,12 @@ typedef struct {
                          /* per warp, 2 = persistent warps walking the tiles (each loads its  */
                          /* next tile while computing the current one); same result bit for  */
                          /* bit; the autotuner's choices override it; ignored in 3D           */
+    int smoother;        /* hh_smoother: HH_SMOOTH_JACOBI (default): nu scaled-Jacobi sweeps;  */
+                         /* HH_SMOOTH_GMRES: each smoothing step (nu_pre, nu_post, and the     */
+                         /* coarsest level's nu_coarse) is nu iterations of GMRES on the       */
+                         /* Jacobi-preconditioned level system D^{-1} A_L x = D^{-1} b from    */
+                         /* the current iterate (Sec. 5.3's smoother; nu <= 8); the cycle is   */
+                         /* then not linear in its right side, which FGMRES allows            */
 } hh_options;
 
 typedef struct {

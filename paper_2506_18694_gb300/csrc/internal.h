@@ -101,7 +101,10 @@ enum MarchMode {
                             // y2 = x1 + omega D^{-1} (rhs - A_L x1)
     // two pre-sweeps and the residual restriction in one pass (2D, march2rr.cu)
     M_JACOBI2_ZERO_RR = 9,  // y = two sweeps on A_L x = z from 0;  yc (coarse) = P^T (z - A_L y)
-    M_HSS_FIRST2_RR = 10    // as M_HSS_FIRST2 (y = rhs, y2 = x2), and yc = P^T (rhs - A_L x2)
+    M_HSS_FIRST2_RR = 10,   // as M_HSS_FIRST2 (y = rhs, y2 = x2), and yc = P^T (rhs - A_L x2)
+    // (11 is the coarse solve's slot in the tuning table)
+    M_DAXPBY = 12           // y = omega D^{-1} (alpha (op x) + beta z): the Jacobi-preconditioned
+                            // residual and operator of the GMRES smoother (march2.cu, march3.cu)
 };
 
 // Coefficients of one operator on one level for one problem of a batch (a device table
@@ -235,6 +238,37 @@ cudaError_t prepare_coarse();
 template <typename T>
 cudaError_t launch_coarse_solve(const MArgs<T>& a, int nsweeps, cudaStream_t s);
 
+
+// ---- GMRES smoother with a Jacobi preconditioner (gsmooth.cu) ----
+// Level vectors of nb problems (problem b at offset b * N); the Krylov basis holds vector i
+// of problem b at V + i * ld + b * N.  Sums in FP64 over a fixed block grid (gs_blocks(N)), so
+// the results do not depend on launch history.  Problems skipped as in Batch.
+constexpr int kGsMaxIts = 8;                // iterations per smoothing step at most
+constexpr int kGsMaxVec = kGsMaxIts + 1;    // basis vectors
+constexpr int kGsThreads = 256;
+inline int gs_blocks(long long N) {
+    const long long b = (N + 4 * kGsThreads - 1) / (4 * kGsThreads);
+    return (int)(b < 1 ? 1 : (b > 304 ? 304 : b));
+}
+// part[(b * nblk + blk) * kGsMaxVec + i] = block blk's share of V_i^H w (i < nv)
+template <typename T>
+cudaError_t launch_gs_dot(const vec2<T>* V, long long ld, int nv, const vec2<T>* w, long long N, double2* part,
+                          const Batch& bt, cudaStream_t s);
+// c_i = sum over blocks of part (i < nv); w -= sum_i c_i V_i; H[b][i][col] = c_i (accumulate:
+// += c_i); part2 != nullptr: block shares of ||w||^2 into part2[(b * nblk + blk) * kGsMaxVec]
+template <typename T>
+cudaError_t launch_gs_orth(vec2<T>* w, const vec2<T>* V, long long ld, int nv, long long N, const double2* part,
+                           double2* H, int col, int accumulate, double2* part2, const Batch& bt, cudaStream_t s);
+// h = sqrt(sum over blocks of part2); out = w / h (0 when h = 0); h stored at H[b][row][col]
+// (row < 0: in beta[b])
+template <typename T>
+cudaError_t launch_gs_scale(vec2<T>* out, const vec2<T>* w, long long N, const double2* part2, double2* H, int row,
+                            int col, double* beta, const Batch& bt, cudaStream_t s);
+// y = argmin ||beta e1 - H y|| over the first m columns (Givens rotations, FP64); x += V y
+// (overwrite: x = V y)
+template <typename T>
+cudaError_t launch_gs_update(vec2<T>* x, const vec2<T>* V, long long ld, int m, long long N, const double2* H,
+                             const double* beta, int overwrite, const Batch& bt, cudaStream_t s);
 
 // ---- FP64 Krylov kernels (blas.cu) ----
 // Fixed reduction grid: results do not depend on timing or launch history.

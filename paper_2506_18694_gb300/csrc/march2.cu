@@ -200,6 +200,8 @@ __device__ __forceinline__ void tile_compute(const MArgs<T>& a, const PCoef<T>& 
             st<T>(v.y, p, ax);
         } else if (MODE == M_AXPBY) {
             st<T>(v.y, p, fma_c(alpha, ax, cmul(beta, tl.zv[t - 1])));
+        } else if (MODE == M_DAXPBY) {
+            st<T>(v.y, p, cmul(dinv_w, fma_c(alpha, ax, cmul(beta, tl.zv[t - 1]))));
         } else if (MODE == M_HSS_FIRST) {
             const Cx<T> rhs = fma_c(alpha, ax, cmul(beta, tl.zv[t - 1]));
             st<T>(v.y, p, rhs);
@@ -566,6 +568,7 @@ cudaError_t launch_march2(int mode, const MArgs<T>& a, cudaStream_t s) {
     switch (mode) {
         case M_APPLY: return go2<T, M_APPLY>(a, s);
         case M_AXPBY: return go2<T, M_AXPBY>(a, s);
+        case M_DAXPBY: return go2<T, M_DAXPBY>(a, s);
         case M_JACOBI: return go2<T, M_JACOBI>(a, s);
         case M_HSS_FIRST: return go2<T, M_HSS_FIRST>(a, s);
         case M_JACOBI2_ZERO: return go2<T, M_JACOBI2_ZERO>(a, s);

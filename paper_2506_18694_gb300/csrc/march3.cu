@@ -180,6 +180,8 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__
             st<T>(v.y, p, ax);
         } else if (MODE == M_AXPBY) {
             st<T>(v.y, p, fma_c(alpha, ax, cmul(beta, zv[t])));
+        } else if (MODE == M_DAXPBY) {
+            st<T>(v.y, p, cmul(dinv_w, fma_c(alpha, ax, cmul(beta, zv[t]))));
         } else if (MODE == M_HSS_FIRST) {
             const Cx<T> rhs = fma_c(alpha, ax, cmul(beta, zv[t]));
             st<T>(v.y, p, rhs);
@@ -281,6 +283,7 @@ cudaError_t launch_march3(int mode, const MArgs<T>& a, cudaStream_t s) {
     switch (mode) {
         case M_APPLY: return pick3<T, M_APPLY>(a, s);
         case M_AXPBY: return pick3<T, M_AXPBY>(a, s);
+        case M_DAXPBY: return pick3<T, M_DAXPBY>(a, s);
         case M_JACOBI: return pick3<T, M_JACOBI>(a, s);
         case M_HSS_FIRST: return pick3<T, M_HSS_FIRST>(a, s);
         case M_JACOBI2_ZERO: return pick3<T, M_JACOBI2_ZERO>(a, s);

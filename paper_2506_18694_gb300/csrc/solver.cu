@@ -100,6 +100,8 @@ struct Hier {
     size_t elem = 0;                  // bytes per complex entry
     std::vector<void*> xa, xb, b, t;  // per level: ping-pong iterates, right side, residual scratch
     std::vector<void*> wk, wr;        // W-cycles (levels >= 1): kept correction, its residual
+    std::vector<void*> gv, gsm;       // GMRES smoother, per level: basis and work vector; sums,
+                                      // Hessenberg matrices and norms (FP64)
     void* r_lo = nullptr;             // level-0 copy of the preconditioner input
     void* rhs = nullptr;              // level-0 HSS right side
     void* ca = nullptr;               // extra level-0 buffers for cycles_per_hss > 1
@@ -247,9 +249,21 @@ hh_status build_tables(hh_problem* p, Hier& H) {
     return HH_OK;
 }
 
+// GMRES smoother: iterations of the longest smoothing step (0 with the Jacobi smoother)
+int gs_its(const hh_options* o) {
+    return o->smoother == HH_SMOOTH_GMRES ? std::max(o->nu_pre, std::max(o->nu_post, o->nu_coarse)) : 0;
+}
+// its FP64 scratch of one level: block sums (two sets), Hessenberg matrices, norms
+size_t gs_small_bytes(long long N, int nb) {
+    return (size_t)nb * (2 * (size_t)hh::gs_blocks(N) * hh::kGsMaxVec + hh::kGsMaxVec * hh::kGsMaxIts) *
+               sizeof(double2) +
+           (size_t)nb * sizeof(double);
+}
+
 // Device bytes of one precision's multigrid buffers for nb problems plus the coefficient
 // tables (matches ensure_hier and ensure_tables).
-size_t hier_bytes(const hh_grid* grid, int levels, int prec, int nb, int gamma) {
+size_t hier_bytes(const hh_grid* grid, const hh_options* o, int prec, int nb) {
+    const int levels = o->levels, gamma = o->cycle_gamma, gs = gs_its(o);
     const size_t elem = prec == HH_C64 ? 8 : 16, B = (size_t)nb;
     size_t tot = 0;
     for (int l = 0; l < levels; ++l) {
@@ -258,6 +272,7 @@ size_t hier_bytes(const hh_grid* grid, int levels, int prec, int nb, int gamma) 
         tot += 4 * (size_t)N * elem * B;  // xa, xb, b, t
         if (gamma > 1 && l >= 1) tot += 2 * (size_t)N * elem * B;  // W-cycle correction and residual
         if (l == 0) tot += 5 * (size_t)N * elem * B;  // r_lo, rhs, ca, cb, cres
+        if (gs > 0) tot += (size_t)(gs + 2) * N * elem * B + gs_small_bytes(N, nb);  // basis, w, sums
     }
     tot += sizeof(void*) * B;  // usrc
     // coefficient tables of both precisions (and the 3D boundary-class tables)
@@ -288,8 +303,18 @@ hh_status ensure_hier(hh_problem* p, int prec) {
     H.t.assign(L, nullptr);
     H.wk.assign(L, nullptr);
     H.wr.assign(L, nullptr);
+    H.gv.assign(L, nullptr);
+    H.gsm.assign(L, nullptr);
+    const int gs = gs_its(&p->o);
     for (int l = 0; l < L; ++l) {
         const size_t nbytes = (size_t)p->lv[l].N * p->nb * H.elem;
+        if (gs > 0) {
+            const size_t sb = gs_small_bytes(p->lv[l].N, p->nb);
+            HH_TRY(dmalloc(p, &H.gv[l], (size_t)(gs + 2) * nbytes));
+            HH_TRY(dmalloc(p, &H.gsm[l], sb));
+            HH_CUDA(cudaMemsetAsync(H.gv[l], 0, (size_t)(gs + 2) * nbytes, p->s));
+            HH_CUDA(cudaMemsetAsync(H.gsm[l], 0, sb, p->s));
+        }
         if (p->o.cycle_gamma > 1 && l >= 1) {
             HH_TRY(dmalloc(p, &H.wk[l], nbytes));
             HH_TRY(dmalloc(p, &H.wr[l], nbytes));
@@ -566,11 +591,109 @@ struct MG {
         return HH_OK;
     }
 
+    bool gm() const { return p->o.smoother == HH_SMOOTH_GMRES; }
+
+    // GMRES smoother on level l: `its` iterations of GMRES on omega D^{-1} A_L x = omega D^{-1} b
+    // from x (xzero: from 0), the result written over x.  omega scales the preconditioned system
+    // and its residual alike, so the iterates are those of the plain Jacobi preconditioner.
+    hh_status gsmooth(int l, const V2* b, V2* x, bool xzero, int its) {
+        const long long N = Nl(l);
+        const hh::Batch bt = batch(l);
+        if (its == 0) {
+            if (xzero) HH_LAUNCH(hh::launch_zero<T>(x, N, bt, s));
+            return HH_OK;
+        }
+        const long long ld = N * p->nb;  // basis vector stride
+        V2* Vb = (V2*)H->gv[l];
+        V2* W = Vb + (long long)(its + 1) * ld;  // after the basis
+        const int nblk = hh::gs_blocks(N);
+        double2* part = (double2*)H->gsm[l];
+        double2* part2 = part + (size_t)p->nb * nblk * hh::kGsMaxVec;
+        double2* Hm = part2 + (size_t)p->nb * nblk * hh::kGsMaxVec;
+        double* beta = (double*)(Hm + (size_t)p->nb * hh::kGsMaxVec * hh::kGsMaxIts);
+        // z0 = omega D^{-1} (b - A_L x), beta = ||z0||, v_0 = z0 / beta
+        hh::MArgs<T> a = margs(l, R_AL);
+        a.x = xzero ? nullptr : x;
+        a.xzero = xzero;
+        a.z = b;
+        a.y = W;
+        a.alpha = Cx<T>{-1, 0};
+        a.beta = Cx<T>{1, 0};
+        HH_LAUNCH(march(hh::M_DAXPBY, a));
+        HH_LAUNCH(hh::launch_gs_dot<T>(W, ld, 1, W, N, part, bt, s));
+        HH_LAUNCH(hh::launch_gs_scale<T>(Vb, W, N, part, Hm, -1, 0, beta, bt, s));
+        for (int j = 0; j < its; ++j) {
+            V2* vj = Vb + (long long)j * ld;
+            hh::MArgs<T> m = margs(l, R_AL);
+            m.x = vj;
+            m.z = vj;  // beta = 0: read, not used
+            m.y = W;
+            m.alpha = Cx<T>{1, 0};
+            m.beta = Cx<T>{0, 0};
+            HH_LAUNCH(march(hh::M_DAXPBY, m));
+            // classical Gram-Schmidt, twice
+            HH_LAUNCH(hh::launch_gs_dot<T>(Vb, ld, j + 1, W, N, part, bt, s));
+            HH_LAUNCH(hh::launch_gs_orth<T>(W, Vb, ld, j + 1, N, part, Hm, j, 0, nullptr, bt, s));
+            HH_LAUNCH(hh::launch_gs_dot<T>(Vb, ld, j + 1, W, N, part, bt, s));
+            HH_LAUNCH(hh::launch_gs_orth<T>(W, Vb, ld, j + 1, N, part, Hm, j, 1, part2, bt, s));
+            HH_LAUNCH(hh::launch_gs_scale<T>(Vb + (long long)(j + 1) * ld, W, N, part2, Hm, j + 1, j, beta, bt, s));
+        }
+        HH_LAUNCH(hh::launch_gs_update<T>(x, Vb, ld, its, N, Hm, beta, xzero ? 1 : 0, bt, s));
+        return HH_OK;
+    }
+
+    // the coarse correction of level l (one cycle on level l + 1 for the right side in
+    // H->b[l + 1], and gamma - 1 more on what it leaves for a W-cycle); result buffer in *ec
+    hh_status coarse_correction(int l, V2** ec_out) {
+        V2* ec;
+        HH_TRY(vcycle(l + 1, (const V2*)H->b[l + 1], nullptr, &ec));
+        if (p->o.cycle_gamma > 1) {
+            // W-cycle: further cycles on the coarse problem, each on the residual that the
+            // correction so far leaves, kept outside the coarse ping-pong buffers
+            const int c = l + 1;
+            V2* keep = (V2*)H->wk[c];
+            HH_LAUNCH(hh::launch_copy<T>(keep, ec, Nl(c), batch(c), s));
+            for (int g = 1; g < p->o.cycle_gamma; ++g) {
+                hh::MArgs<T> a = margs(c, R_AL);
+                a.x = keep;
+                a.z = (const V2*)H->b[c];
+                a.y = (V2*)H->wr[c];
+                a.alpha = Cx<T>{-1, 0};
+                a.beta = Cx<T>{1, 0};
+                HH_LAUNCH(march(hh::M_AXPBY, a));
+                V2* corr;
+                HH_TRY(vcycle(c, (const V2*)H->wr[c], nullptr, &corr));
+                HH_LAUNCH(hh::launch_add<T>(keep, corr, Nl(c), batch(c), s));
+            }
+            ec = keep;
+        }
+        *ec_out = ec;
+        return HH_OK;
+    }
+
+    // One cycle with the GMRES smoother: every step in place in the level's first buffer
+    hh_status gcycle(int l, const V2* b, V2** out) {
+        V2* x = (V2*)H->xa[l];
+        if (l == p->o.levels - 1) {
+            HH_TRY(gsmooth(l, b, x, true, p->o.nu_coarse));
+        } else {
+            HH_TRY(gsmooth(l, b, x, true, p->o.nu_pre));
+            HH_TRY(resid_restrict(l, b, x, (V2*)H->b[l + 1]));
+            V2* ec;
+            HH_TRY(coarse_correction(l, &ec));
+            HH_LAUNCH(hh::launch_prolong<T>(p->lv[l], ec, x, batch(l), s));
+            HH_TRY(gsmooth(l, b, x, false, p->o.nu_post));
+        }
+        *out = x;
+        return HH_OK;
+    }
+
     // One V-cycle on level l for right side b from x = 0; result buffer in *out.
     // xstart: the first `done` pre-smoothing sweeps were already done and sit in xstart;
     // restricted: all pre-sweeps are done and the coarse residual already sits in H->b[l + 1].
     hh_status vcycle(int l, const V2* b, V2* xstart, V2** out, int done = 1, bool restricted = false) {
         const int L = p->o.levels;
+        if (gm()) return gcycle(l, b, out);  // never entered with a started iterate
         if (l == L - 1) {
             V2* x = (V2*)H->xa[l];
             if (xstart) {
@@ -604,27 +727,7 @@ struct MG {
         }
         if (!restricted) HH_TRY(resid_restrict(l, b, x, (V2*)H->b[l + 1]));
         V2* ec;
-        HH_TRY(vcycle(l + 1, (const V2*)H->b[l + 1], nullptr, &ec));
-        if (p->o.cycle_gamma > 1) {
-            // W-cycle: further cycles on the coarse problem, each on the residual that the
-            // correction so far leaves, kept outside the coarse ping-pong buffers
-            const int c = l + 1;
-            V2* keep = (V2*)H->wk[c];
-            HH_LAUNCH(hh::launch_copy<T>(keep, ec, Nl(c), batch(c), s));
-            for (int g = 1; g < p->o.cycle_gamma; ++g) {
-                hh::MArgs<T> a = margs(c, R_AL);
-                a.x = keep;
-                a.z = (const V2*)H->b[c];
-                a.y = (V2*)H->wr[c];
-                a.alpha = Cx<T>{-1, 0};
-                a.beta = Cx<T>{1, 0};
-                HH_LAUNCH(march(hh::M_AXPBY, a));
-                V2* corr;
-                HH_TRY(vcycle(c, (const V2*)H->wr[c], nullptr, &corr));
-                HH_LAUNCH(hh::launch_add<T>(keep, corr, Nl(c), batch(c), s));
-            }
-            ec = keep;
-        }
+        HH_TRY(coarse_correction(l, &ec));
         if (p->o.nu_post == 0) {
             HH_LAUNCH(hh::launch_prolong<T>(p->lv[l], ec, x, batch(l), s));
         } else if (p->o.nu_post >= 2 && fused2(l)) {
@@ -671,7 +774,8 @@ struct MG {
     // The HSS loop of Def. 4.1 on r_lo (already in this precision).  src[b] receives the
     // buffer that holds problem b's result (its loop may end before the others').
     hh_status hss_loop(std::vector<V2*>* src) {
-        const bool fuse = p->o.nu_pre >= 1 && !(p->o.levels == 1 && p->o.nu_coarse == 0);
+        // the GMRES smoother's first step needs the right side whole: no fused first sweep
+        const bool fuse = !gm() && p->o.nu_pre >= 1 && !(p->o.levels == 1 && p->o.nu_coarse == 0);
         const bool two = fuse && fused2(0) && (p->o.levels > 1 ? p->o.nu_pre : p->o.nu_coarse) >= 2;
         std::vector<V2*> after(p->max_nhss, nullptr);
         V2* u = nullptr;
@@ -1249,6 +1353,11 @@ hh_status check_args(const hh_grid* grid, int nb, const double* k, const double*
     if (o->tile_rows != 0 && o->tile_rows != 2 && o->tile_rows != 4 && o->tile_rows != 8)
         return fail(HH_ERR_INVALID, "tile_rows must be 0, 2, 4 or 8");
     if (o->tile_form < 0 || o->tile_form > 2) return fail(HH_ERR_INVALID, "tile_form must be 0, 1 or 2");
+    if (o->smoother != HH_SMOOTH_JACOBI && o->smoother != HH_SMOOTH_GMRES)
+        return fail(HH_ERR_INVALID, "smoother must be HH_SMOOTH_JACOBI or HH_SMOOTH_GMRES");
+    if (o->smoother == HH_SMOOTH_GMRES &&
+        (o->nu_pre > hh::kGsMaxIts || o->nu_post > hh::kGsMaxIts || o->nu_coarse > hh::kGsMaxIts))
+        return fail(HH_ERR_INVALID, "the GMRES smoother takes at most 8 iterations per smoothing step");
     if (o->autotune != 0 && o->autotune != 1) return fail(HH_ERR_INVALID, "autotune must be 0 or 1");
     if (o->fuse_sweeps != 0 && o->fuse_sweeps != 1) return fail(HH_ERR_INVALID, "fuse_sweeps must be 0 or 1");
     if (o->cycle_gamma < 1 || o->cycle_gamma > 4) return fail(HH_ERR_INVALID, "cycle_gamma must be in 1..4");
@@ -1308,6 +1417,7 @@ void hh_options_default(hh_options* o) {
     o->outer = HH_OUTER_FGMRES;
     o->cycle_gamma = 1;
     o->tile_form = 0;
+    o->smoother = HH_SMOOTH_JACOBI;
 }
 
 size_t hh_footprint_batch_bytes(const hh_grid* grid, const hh_options* o, int nb) {
@@ -1315,7 +1425,7 @@ size_t hh_footprint_batch_bytes(const hh_grid* grid, const hh_options* o, int nb
     const int bc0[6] = {0, 0, 0, 0, 0, 0};
     std::vector<double> one(nb, 1.0), zero(nb, 0.0);
     if (check_args(grid, nb, one.data(), zero.data(), one.data(), bc0, o) != HH_OK) return 0;
-    return hier_bytes(grid, o->levels, o->precision, nb, o->cycle_gamma) + krylov_bytes(grid, o->restart, nb);
+    return hier_bytes(grid, o, o->precision, nb) + krylov_bytes(grid, o->restart, nb);
 }
 
 size_t hh_footprint_bytes(const hh_grid* grid, const hh_options* o) { return hh_footprint_batch_bytes(grid, o, 1); }

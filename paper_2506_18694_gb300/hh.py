@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libhh.so")
 HH_OK, HH_NOT_CONVERGED = 0, 1
 HH_C128, HH_C64 = 0, 1
 HH_OUTER_FGMRES, HH_OUTER_RICHARDSON = 0, 1
+HH_SMOOTH_JACOBI, HH_SMOOTH_GMRES = 0, 1
 SOMMERFELD, DIRICHLET = 0, 1
 OP = {"K": 0, "M": 1, "MGAMMA": 2, "AL": 3, "AR": 4, "B": 5, "BHAT": 6}
 
@@ -44,7 +45,7 @@ class Options(ctypes.Structure):
         ("precision", ctypes.c_int), ("use_graphs", ctypes.c_int), ("use_pdl", ctypes.c_int),
         ("coarse_cluster_nodes", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
         ("fuse_sweeps", ctypes.c_int), ("outer", ctypes.c_int), ("cycle_gamma", ctypes.c_int),
-        ("tile_form", ctypes.c_int),
+        ("tile_form", ctypes.c_int), ("smoother", ctypes.c_int),
     ]
 
 

@@ -31,7 +31,7 @@ def test_options_default(libhh):
     assert o.cycles_per_hss == 1 and o.omega == 0.0
     assert o.restart == 30 and o.precision == hh.HH_C64 and o.use_graphs == 1
     assert o.use_pdl == 1 and o.coarse_cluster_nodes == 100000 and o.tile_rows == 0 and o.autotune == 0
-    assert o.fuse_sweeps == 1 and o.outer == hh.HH_OUTER_FGMRES and o.cycle_gamma == 1 and o.tile_form == 0
+    assert o.fuse_sweeps == 1 and o.outer == hh.HH_OUTER_FGMRES and o.cycle_gamma == 1 and o.tile_form == 0 and o.smoother == hh.HH_SMOOTH_JACOBI
 
 
 def test_footprint_bytes(libhh):
@@ -42,9 +42,15 @@ def test_footprint_bytes(libhh):
     assert hh.footprint_bytes(2, 1024, o) > 3.9 * b2
     assert hh.footprint_bytes(2, 100, o) == 0  # 100 is not divisible by 2^3
     assert hh.footprint_bytes(4, 64, o) == 0
-    for bad in (dict(tile_form=3), dict(tile_form=-1), dict(tile_rows=3), dict(cycle_gamma=5)):
+    for bad in (dict(tile_form=3), dict(tile_form=-1), dict(tile_rows=3), dict(cycle_gamma=5), dict(smoother=2),
+                dict(smoother=hh.HH_SMOOTH_GMRES, nu_coarse=9)):
         assert hh.footprint_bytes(2, 64, hh.default_options(**bad)) == 0, bad
     assert hh.footprint_bytes(2, 64, hh.default_options(tile_form=2)) == hh.footprint_bytes(2, 64, o)
+    # GMRES smoother: max(nu) + 2 more level vectors per level (basis and work vector) and FP64 sums
+    gm = hh.footprint_bytes(2, 64, hh.default_options(levels=2, smoother=hh.HH_SMOOTH_GMRES, nu_coarse=5))
+    jac = hh.footprint_bytes(2, 64, hh.default_options(levels=2))
+    assert gm - jac >= 7 * (65 * 65 + 33 * 33) * 8
+    assert hh.footprint_bytes(2, 64, hh.default_options(levels=2, smoother=hh.HH_SMOOTH_GMRES, nu_coarse=8)) > gm
 
 
 @pytest.mark.parametrize("dim,n,k,delta,dh,bc", [
