@@ -455,6 +455,14 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
     except Exception as e:
         out["w_cycle_delta_hat_2"] = {"failed": str(e)}
 
+    # the paper's multigrid settings (Sec. 5.3): W-cycles with GMRES(5) and a Jacobi
+    # preconditioner on every level, one cycle per HSS step, delta_hat = 2; on 2D 256^2 at
+    # k = 20, where V(2,2)-Jacobi with two cycles per HSS step stagnates
+    try:
+        out["gmres_smoother"] = measure_gmres_smoother(hh, inputs, torch, w)
+    except Exception as e:
+        out["gmres_smoother"] = {"failed": str(e)}
+
     # serving: Poisson arrivals of mixed 2D/3D requests through the solve server
     try:
         out["serving"] = measure_serving(hh, inputs, torch, SERVE_REQUESTS[0])
@@ -476,6 +484,28 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
     except Exception as e:  # the CPU leg must not hide the GPU numbers
         out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle", "sample": f"failed: {e}"}
     return out
+
+
+def measure_gmres_smoother(hh, inputs, torch, w, n=256, k=20.0):
+    f = torch.from_numpy(inputs.gaussian_source(2, n, tuple(w.centre)[:2], w.sigma)).cuda()
+    legs = {
+        "gmres5_w_cycle": dict(cycle_gamma=2, nu_pre=5, nu_post=5, nu_coarse=5, smoother=hh.HH_SMOOTH_GMRES),
+        "jacobi_v22_two_cycles": dict(cycles_per_hss=2),
+    }
+    res = {"grid": f"2D {n}^2 Q1 cells, Sommerfeld", "k": k, "delta_hat": 2.0, "tol": w.tol, "levels": 4}
+    for name, o in legs.items():
+        with hh.Problem(2, n, k, 0.0, 2.0, [hh.SOMMERFELD] * 4, hh.default_options(max_outer=300, **o)) as p:
+            b = p.load_vector(f)
+            p.solve(b, w.tol)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info = p.solve(b, w.tol)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+        res[name] = {"solve_s": t, "outer_its": info.outer_its, "cycles": info.vcycles,
+                     "rel_residual": info.rel_residual, "converged": info.rel_residual <= w.tol,
+                     "kernel_launches": info.kernel_launches}
+    return res
 
 
 def measure_serving(hh, inputs, torch, count, slots=4, load=0.8):

@@ -3,11 +3,14 @@
 // M = omega D^{-1} A applied by the stencil kernels' M_DAXPBY mode:
 //   z0 = omega D^{-1} (b - A x), beta = ||z0||, v_0 = z0 / beta;
 //   for j < s: w = M v_j; two passes of classical Gram-Schmidt against v_0..v_j (the
-//   coefficients of both passes added into column j of H); h_{j+1,j} = ||w||, v_{j+1} = w / h;
-//   y = argmin ||beta e1 - H y|| by Givens rotations; x += V y.
-// Inner products and norms are summed in FP64: each block writes its share, and the kernel
-// that uses a sum adds the shares in block order (every block of that kernel the same way),
-// so the result is the same whatever ran before and however the problems are batched.
+//   coefficients of both passes added into column j of H); h_{j+1,j} = ||w||, v_{j+1} = w / h,
+//   and column j reduced by Givens rotations (as in GMRES, one new rotation per step);
+//   y = R^{-1} g minimises ||beta e1 - H y||; x += V y.
+// Inner products and norms are summed in the level precision within a block (FP64 arithmetic
+// is slow on this part and the complex64 smoother does not need it) and the block shares are
+// combined in FP64: each block writes its share, and the kernel that uses a sum adds the
+// shares in a fixed order (every block of that kernel the same way), so the result is the
+// same whatever ran before and however the problems are batched.
 #include "internal.h"
 
 namespace hh {
@@ -21,27 +24,47 @@ __device__ __forceinline__ bool gs_skip(const Batch& bt, int b) {
 
 __device__ __forceinline__ double2 dadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
-// sum of every thread's acc[i] (i < nv) into out[i] (valid in thread 0's block, read after the
-// barrier); sh holds kGsThreads / 32 * kGsMaxVec entries
-__device__ void block_sums(double2 (&acc)[kGsMaxVec], int nv, double2* sh, double2* out) {
+// fused multiply-add in the level precision (FP64 arithmetic, conversions included, runs on
+// this part's narrow FP64 pipe: kept out of the per-element loops of the complex64 smoother)
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+
+// sum of every thread's acc[i] (i < nv) over the block into out[i] (as FP64), by warp
+// butterflies and then the warps in order; sh holds kGsThreads / 32 * kGsMaxVec entries
+template <typename T>
+__device__ void block_sums(Cx<T> (&acc)[kGsMaxVec], int nv, Cx<T>* sh, double2* out) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < kGsMaxVec; ++i) {
         if (i >= nv) break;
-        double2 v = acc[i];
+        Cx<T> v = acc[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-            v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+            v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
+            v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
         }
         if (lane == 0) sh[wid * kGsMaxVec + i] = v;
     }
     __syncthreads();
     if ((int)threadIdx.x < nv) {
-        double2 t = make_double2(0.0, 0.0);
-        for (int w = 0; w < kGsThreads / 32; ++w) t = dadd(t, sh[w * kGsMaxVec + threadIdx.x]);
-        out[threadIdx.x] = t;
+        Cx<T> t = cx<T>(0, 0);
+        for (int w = 0; w < kGsThreads / 32; ++w) t = t + sh[w * kGsMaxVec + threadIdx.x];
+        out[threadIdx.x] = make_double2(t.re, t.im);
     }
+}
+
+// sum of n block shares p[0], p[stride], ... by one warp: lane t adds shares t, t + 32, ...
+// in order, then the lanes are combined by a fixed butterfly (the same order on every call)
+__device__ __forceinline__ double2 warp_sum_shares(const double2* p, int n, int stride) {
+    const int lane = threadIdx.x & 31;
+    double2 t = make_double2(0.0, 0.0);
+    for (int k = lane; k < n; k += 32) t = dadd(t, p[(long long)k * stride]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+        t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+    }
+    return t;
 }
 
 // grid (nblk, nb)
@@ -52,24 +75,22 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_dot(const vec2<T>* __restrict
     pdl_entry();
     const int b = blockIdx.y;
     if (gs_skip(bt, b)) return;
-    __shared__ double2 sh[kGsThreads / 32 * kGsMaxVec];
+    __shared__ Cx<T> sh[kGsThreads / 32 * kGsMaxVec];
     const vec2<T>* Vb = V + (long long)b * N;
     const vec2<T>* wb = w + (long long)b * N;
-    double2 acc[kGsMaxVec];
+    Cx<T> acc[kGsMaxVec];
 #pragma unroll
-    for (int i = 0; i < kGsMaxVec; ++i) acc[i] = make_double2(0.0, 0.0);
+    for (int i = 0; i < kGsMaxVec; ++i) acc[i] = cx<T>(0, 0);
     const long long stride = (long long)gridDim.x * kGsThreads;
     for (long long p = (long long)blockIdx.x * kGsThreads + threadIdx.x; p < N; p += stride) {
         const Cx<T> x = ld<T>(wb, p);
-        const double xr = x.re, xi = x.im;
 #pragma unroll
         for (int i = 0; i < kGsMaxVec; ++i) {
             if (i >= nv) break;
             const Cx<T> v = ld<T>(Vb + i * ldv, p);
-            const double vr = v.re, vi = v.im;
             // conj(v) * x
-            acc[i].x = fma(vr, xr, fma(vi, xi, acc[i].x));
-            acc[i].y = fma(vr, xi, fma(-vi, xr, acc[i].y));
+            acc[i].re = fmaT(v.re, x.re, fmaT(v.im, x.im, acc[i].re));
+            acc[i].im = fmaT(v.re, x.im, fmaT(-v.im, x.re, acc[i].im));
         }
     }
     block_sums(acc, nv, sh, part + ((long long)b * gridDim.x + blockIdx.x) * kGsMaxVec);
@@ -79,32 +100,33 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_dot(const vec2<T>* __restrict
 template <typename T>
 __global__ void __launch_bounds__(kGsThreads) k_gs_orth(vec2<T>* __restrict__ w, const vec2<T>* __restrict__ V,
                                                         long long ldv, int nv, long long N,
-                                                        const double2* __restrict__ part, double2* H, int col,
+                                                        const double2* __restrict__ part, double2* ls, int col,
                                                         int accumulate, double2* __restrict__ part2, Batch bt) {
     pdl_entry();
     const int b = blockIdx.y;
     if (gs_skip(bt, b)) return;
-    __shared__ double2 c[kGsMaxVec];
-    __shared__ double2 sh[kGsThreads / 32 * kGsMaxVec];
+    __shared__ Cx<T> cneg[kGsMaxVec];  // -c_i in the level precision
+    __shared__ Cx<T> sh[kGsThreads / 32 * kGsMaxVec];
     const int nblk = gridDim.x;
-    if ((int)threadIdx.x < nv) {
-        double2 t = make_double2(0.0, 0.0);
-        const double2* pb = part + (long long)b * nblk * kGsMaxVec + threadIdx.x;
-        for (int k = 0; k < nblk; ++k) t = dadd(t, pb[(long long)k * kGsMaxVec]);
-        c[threadIdx.x] = t;
-        if (blockIdx.x == 0) {
-            double2& h = H[((long long)b * kGsMaxVec + threadIdx.x) * kGsMaxIts + col];
-            h = accumulate ? dadd(h, t) : t;
+    // coefficient i summed by warp i % 8
+    for (int i = threadIdx.x >> 5; i < nv; i += kGsThreads / 32) {
+        const double2 t = warp_sum_shares(part + (long long)b * nblk * kGsMaxVec + i, nblk, kGsMaxVec);
+        if ((threadIdx.x & 31) == 0) {
+            cneg[i] = cx<T>(T(-t.x), T(-t.y));
+            if (blockIdx.x == 0) {
+                double2& h = ls[(long long)b * kGsState + i * kGsMaxIts + col];
+                h = accumulate ? dadd(h, t) : t;
+            }
         }
     }
     __syncthreads();
     Cx<T> cc[kGsMaxVec];
 #pragma unroll
-    for (int i = 0; i < kGsMaxVec; ++i) cc[i] = i < nv ? cx<T>(T(-c[i].x), T(-c[i].y)) : cx<T>(0, 0);
+    for (int i = 0; i < kGsMaxVec; ++i) cc[i] = i < nv ? cneg[i] : cx<T>(0, 0);
     vec2<T>* wb = w + (long long)b * N;
     const vec2<T>* Vb = V + (long long)b * N;
-    double2 acc[kGsMaxVec];
-    acc[0] = make_double2(0.0, 0.0);
+    Cx<T> acc[kGsMaxVec];
+    acc[0] = cx<T>(0, 0);
     const long long stride = (long long)nblk * kGsThreads;
     for (long long p = (long long)blockIdx.x * kGsThreads + threadIdx.x; p < N; p += stride) {
         Cx<T> x = ld<T>(wb, p);
@@ -114,32 +136,80 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_orth(vec2<T>* __restrict__ w,
             x = fma_c(cc[i], ld<T>(Vb + i * ldv, p), x);
         }
         st<T>(wb, p, x);
-        const double xr = x.re, xi = x.im;
-        acc[0].x = fma(xr, xr, fma(xi, xi, acc[0].x));
+        acc[0].re = fmaT(x.re, x.re, fmaT(x.im, x.im, acc[0].re));
     }
     if (part2) block_sums(acc, 1, sh, part2 + ((long long)b * nblk + blockIdx.x) * kGsMaxVec);
+}
+
+// complex helpers in the level precision for the small least-squares problem
+template <typename T>
+__device__ __forceinline__ Cx<T> cget(const double2& d) {
+    return cx<T>(T(d.x), T(d.y));
+}
+template <typename T>
+__device__ __forceinline__ double2 cput(Cx<T> v) {
+    return make_double2(v.re, v.im);
+}
+// (p, q) <- (c p + s q, -conj(s) p + c q), c real
+template <typename T>
+__device__ __forceinline__ void rotate(T c, Cx<T> s, Cx<T>& p, Cx<T>& q) {
+    const Cx<T> p0 = p, q0 = q;
+    p = cx<T>(c * p0.re + (s.re * q0.re - s.im * q0.im), c * p0.im + (s.re * q0.im + s.im * q0.re));
+    q = cx<T>(-(s.re * p0.re + s.im * p0.im) + c * q0.re, -(s.re * p0.im - s.im * p0.re) + c * q0.im);
 }
 
 // grid (nblk, nb)
 template <typename T>
 __global__ void __launch_bounds__(kGsThreads) k_gs_scale(vec2<T>* __restrict__ out, const vec2<T>* __restrict__ w,
                                                          long long N, const double2* __restrict__ part2, int nsum,
-                                                         double2* H, int row, int col, double* beta, Batch bt) {
+                                                         double2* ls, int col, Batch bt) {
     pdl_entry();
     const int b = blockIdx.y;
     if (gs_skip(bt, b)) return;
     __shared__ T inv;
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        const double2* pb = part2 + (long long)b * nsum * kGsMaxVec;
-        for (int k = 0; k < nsum; ++k) t += pb[(long long)k * kGsMaxVec].x;
-        const double h = sqrt(t);
-        inv = h > 0.0 ? T(1.0 / h) : T(0);
-        if (blockIdx.x == 0) {
-            if (row < 0) {
-                beta[b] = h;
-            } else {
-                H[((long long)b * kGsMaxVec + row) * kGsMaxIts + col] = make_double2(h, 0.0);
+    if (threadIdx.x < 32) {
+        const T h = sqrt(T(warp_sum_shares(part2 + (long long)b * nsum * kGsMaxVec, nsum, kGsMaxVec).x));
+        if (threadIdx.x == 0) {
+            inv = h > T(0) ? T(1) / h : T(0);
+            if (blockIdx.x == 0) {
+                double2* S = ls + (long long)b * kGsState;
+                if (col < 0) {
+                    S[kGsRhs] = make_double2(h, 0.0);
+                    for (int i = 1; i < kGsMaxVec; ++i) S[kGsRhs + i] = make_double2(0.0, 0.0);
+                } else {
+                    // column col: previous rotations, then the one that zeroes h = H[col + 1][col]
+                    for (int i = 0; i < col; ++i) {
+                        Cx<T> p = cget<T>(S[i * kGsMaxIts + col]), q = cget<T>(S[(i + 1) * kGsMaxIts + col]);
+                        rotate<T>(T(S[kGsCos + i].x), cget<T>(S[kGsSin + i]), p, q);
+                        S[i * kGsMaxIts + col] = cput(p);
+                        S[(i + 1) * kGsMaxIts + col] = cput(q);
+                    }
+                    const Cx<T> a = cget<T>(S[col * kGsMaxIts + col]);
+                    const T na = sqrt(a.re * a.re + a.im * a.im);
+                    const T den = sqrt(na * na + h * h);
+                    T cs = T(1);
+                    Cx<T> sn = cx<T>(0, 0);
+                    if (den > T(0)) {
+                        if (na == T(0)) {
+                            cs = T(0);
+                            sn = cx<T>(1, 0);
+                        } else {
+                            // s = (a / |a|) conj(h) / den, h real
+                            cs = na / den;
+                            sn = cx<T>(a.re / na * h / den, a.im / na * h / den);
+                        }
+                    }
+                    Cx<T> p = a, q = cx<T>(h, 0);
+                    rotate<T>(cs, sn, p, q);
+                    S[col * kGsMaxIts + col] = cput(p);
+                    S[(col + 1) * kGsMaxIts + col] = make_double2(0.0, 0.0);
+                    S[kGsCos + col] = make_double2(cs, 0.0);
+                    S[kGsSin + col] = cput(sn);
+                    Cx<T> g0 = cget<T>(S[kGsRhs + col]), g1 = cget<T>(S[kGsRhs + col + 1]);
+                    rotate<T>(cs, sn, g0, g1);
+                    S[kGsRhs + col] = cput(g0);
+                    S[kGsRhs + col + 1] = cput(g1);
+                }
             }
         }
     }
@@ -157,65 +227,32 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_scale(vec2<T>* __restrict__ o
 // grid (nblk, nb)
 template <typename T>
 __global__ void __launch_bounds__(kGsThreads) k_gs_update(vec2<T>* __restrict__ x, const vec2<T>* __restrict__ V,
-                                                          long long ldv, int m, long long N, const double2* H,
-                                                          const double* beta, int overwrite, Batch bt) {
+                                                          long long ldv, int m, long long N, const double2* ls,
+                                                          int overwrite, Batch bt) {
     pdl_entry();
     const int b = blockIdx.y;
     if (gs_skip(bt, b)) return;
-    __shared__ double2 ys[kGsMaxIts];
+    __shared__ Cx<T> ys[kGsMaxIts];
     if (threadIdx.x == 0) {
-        // least squares min ||beta e1 - H y|| by Givens rotations (H is (m+1) x m, Hessenberg)
-        double2 R[kGsMaxVec][kGsMaxIts];
-        double2 g[kGsMaxVec];
-        const double2* Hb = H + (long long)b * kGsMaxVec * kGsMaxIts;
-        for (int i = 0; i <= m; ++i) {
-            g[i] = make_double2(i == 0 ? beta[b] : 0.0, 0.0);
-            for (int j = 0; j < m; ++j) R[i][j] = Hb[i * kGsMaxIts + j];
-        }
-        for (int j = 0; j < m; ++j) {
-            // rotation zeroing R[j+1][j] against R[j][j]: [c s; -conj(s) c] with c real
-            const double2 a = R[j][j], e = R[j + 1][j];
-            const double na = hypot(a.x, a.y), ne = hypot(e.x, e.y);
-            const double den = hypot(na, ne);
-            if (den == 0.0) continue;
-            double cs;
-            double2 sn;
-            if (na == 0.0) {
-                cs = 0.0;
-                sn = make_double2(1.0, 0.0);
-            } else {
-                cs = na / den;
-                // sn = (a / |a|) conj(e) / den
-                const double2 u = make_double2(a.x / na, a.y / na);
-                sn = make_double2((u.x * e.x + u.y * e.y) / den, (u.y * e.x - u.x * e.y) / den);
-            }
-            for (int k = j; k < m; ++k) {
-                const double2 p = R[j][k], q = R[j + 1][k];
-                // p' = cs p + sn q ; q' = -conj(sn) p + cs q
-                R[j][k] = make_double2(cs * p.x + (sn.x * q.x - sn.y * q.y), cs * p.y + (sn.x * q.y + sn.y * q.x));
-                R[j + 1][k] = make_double2(-(sn.x * p.x + sn.y * p.y) + cs * q.x, -(sn.x * p.y - sn.y * p.x) + cs * q.y);
-            }
-            const double2 p = g[j], q = g[j + 1];
-            g[j] = make_double2(cs * p.x + (sn.x * q.x - sn.y * q.y), cs * p.y + (sn.x * q.y + sn.y * q.x));
-            g[j + 1] = make_double2(-(sn.x * p.x + sn.y * p.y) + cs * q.x, -(sn.x * p.y - sn.y * p.x) + cs * q.y);
-        }
-        // back substitution; a zero pivot (breakdown: the space was already invariant) gives y_j = 0
+        // back substitution R y = g; a zero pivot (breakdown: the space was already
+        // invariant) gives y_j = 0
+        const double2* S = ls + (long long)b * kGsState;
         for (int j = m - 1; j >= 0; --j) {
-            double2 t = g[j];
+            Cx<T> t = cget<T>(S[kGsRhs + j]);
             for (int k = j + 1; k < m; ++k) {
-                const double2 r = R[j][k], yk = ys[k];
-                t = make_double2(t.x - (r.x * yk.x - r.y * yk.y), t.y - (r.x * yk.y + r.y * yk.x));
+                const Cx<T> r = cget<T>(S[j * kGsMaxIts + k]), yk = ys[k];
+                t = cx<T>(t.re - (r.re * yk.re - r.im * yk.im), t.im - (r.re * yk.im + r.im * yk.re));
             }
-            const double2 d = R[j][j];
-            const double dd = d.x * d.x + d.y * d.y;
-            ys[j] = dd > 0.0 ? make_double2((t.x * d.x + t.y * d.y) / dd, (t.y * d.x - t.x * d.y) / dd)
-                             : make_double2(0.0, 0.0);
+            const Cx<T> d = cget<T>(S[j * kGsMaxIts + j]);
+            const T dd = d.re * d.re + d.im * d.im;
+            ys[j] = dd > T(0) ? cx<T>((t.re * d.re + t.im * d.im) / dd, (t.im * d.re - t.re * d.im) / dd)
+                              : cx<T>(0, 0);
         }
     }
     __syncthreads();
     Cx<T> yc[kGsMaxIts];
 #pragma unroll
-    for (int i = 0; i < kGsMaxIts; ++i) yc[i] = i < m ? cx<T>(T(ys[i].x), T(ys[i].y)) : cx<T>(0, 0);
+    for (int i = 0; i < kGsMaxIts; ++i) yc[i] = i < m ? ys[i] : cx<T>(0, 0);
     vec2<T>* xb = x + (long long)b * N;
     const vec2<T>* Vb = V + (long long)b * N;
     const long long stride = (long long)gridDim.x * kGsThreads;
@@ -241,29 +278,29 @@ cudaError_t launch_gs_dot(const vec2<T>* V, long long ldv, int nv, const vec2<T>
 }
 
 template <typename T>
-cudaError_t launch_gs_orth(vec2<T>* w, const vec2<T>* V, long long ldv, int nv, long long N, const double2* part,
-                           double2* H, int col, int accumulate, double2* part2, const Batch& bt, cudaStream_t s) {
+cudaError_t launch_gs_orth(vec2<T>* w, const vec2<T>* V, long long ld, int nv, long long N, const double2* part,
+                           double2* ls, int col, int accumulate, double2* part2, const Batch& bt, cudaStream_t s) {
     if (nv < 1 || nv > kGsMaxVec || col < 0 || col >= kGsMaxIts) return cudaErrorInvalidValue;
     const dim3 grd((unsigned)gs_blocks(N), (unsigned)bt.nb);
-    return klaunch(k_gs_orth<T>, grd, dim3(kGsThreads), 0, s, 1, w, V, ldv, nv, N, part, H, col, accumulate, part2,
+    return klaunch(k_gs_orth<T>, grd, dim3(kGsThreads), 0, s, 1, w, V, ld, nv, N, part, ls, col, accumulate, part2,
                    bt);
 }
 
 template <typename T>
-cudaError_t launch_gs_scale(vec2<T>* out, const vec2<T>* w, long long N, const double2* part2, double2* H, int row,
-                            int col, double* beta, const Batch& bt, cudaStream_t s) {
-    if (row >= kGsMaxVec || col >= kGsMaxIts) return cudaErrorInvalidValue;
+cudaError_t launch_gs_scale(vec2<T>* out, const vec2<T>* w, long long N, const double2* part2, double2* ls, int col,
+                            const Batch& bt, cudaStream_t s) {
+    if (col >= kGsMaxIts) return cudaErrorInvalidValue;
     const int nblk = gs_blocks(N);
     const dim3 grd((unsigned)nblk, (unsigned)bt.nb);
-    return klaunch(k_gs_scale<T>, grd, dim3(kGsThreads), 0, s, 1, out, w, N, part2, nblk, H, row, col, beta, bt);
+    return klaunch(k_gs_scale<T>, grd, dim3(kGsThreads), 0, s, 1, out, w, N, part2, nblk, ls, col, bt);
 }
 
 template <typename T>
-cudaError_t launch_gs_update(vec2<T>* x, const vec2<T>* V, long long ldv, int m, long long N, const double2* H,
-                             const double* beta, int overwrite, const Batch& bt, cudaStream_t s) {
+cudaError_t launch_gs_update(vec2<T>* x, const vec2<T>* V, long long ld, int m, long long N, const double2* ls,
+                             int overwrite, const Batch& bt, cudaStream_t s) {
     if (m < 1 || m > kGsMaxIts) return cudaErrorInvalidValue;
     const dim3 grd((unsigned)gs_blocks(N), (unsigned)bt.nb);
-    return klaunch(k_gs_update<T>, grd, dim3(kGsThreads), 0, s, 1, x, V, ldv, m, N, H, beta, overwrite, bt);
+    return klaunch(k_gs_update<T>, grd, dim3(kGsThreads), 0, s, 1, x, V, ld, m, N, ls, overwrite, bt);
 }
 
 #define HH_GS_INST(T)                                                                                                 \
@@ -271,10 +308,10 @@ cudaError_t launch_gs_update(vec2<T>* x, const vec2<T>* V, long long ldv, int m,
                                           const Batch&, cudaStream_t);                                                \
     template cudaError_t launch_gs_orth<T>(vec2<T>*, const vec2<T>*, long long, int, long long, const double2*,       \
                                            double2*, int, int, double2*, const Batch&, cudaStream_t);                 \
-    template cudaError_t launch_gs_scale<T>(vec2<T>*, const vec2<T>*, long long, const double2*, double2*, int, int, \
-                                            double*, const Batch&, cudaStream_t);                                     \
+    template cudaError_t launch_gs_scale<T>(vec2<T>*, const vec2<T>*, long long, const double2*, double2*, int,       \
+                                            const Batch&, cudaStream_t);                                              \
     template cudaError_t launch_gs_update<T>(vec2<T>*, const vec2<T>*, long long, int, long long, const double2*,     \
-                                             const double*, int, const Batch&, cudaStream_t);
+                                             int, const Batch&, cudaStream_t);
 HH_GS_INST(float)
 HH_GS_INST(double)
 #undef HH_GS_INST

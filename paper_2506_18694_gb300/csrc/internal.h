@@ -254,21 +254,28 @@ inline int gs_blocks(long long N) {
 template <typename T>
 cudaError_t launch_gs_dot(const vec2<T>* V, long long ld, int nv, const vec2<T>* w, long long N, double2* part,
                           const Batch& bt, cudaStream_t s);
-// c_i = sum over blocks of part (i < nv); w -= sum_i c_i V_i; H[b][i][col] = c_i (accumulate:
+// Per-problem least-squares state (double2 entries, kGsState per problem): the Hessenberg
+// matrix H[i][j] at i * kGsMaxIts + j (rotated in place into R as columns complete), the
+// Givens rotations (c_j real at kGsCos + j, s_j at kGsSin + j) and the rotated right side g.
+constexpr int kGsCos = kGsMaxVec * kGsMaxIts;
+constexpr int kGsSin = kGsCos + kGsMaxIts;
+constexpr int kGsRhs = kGsSin + kGsMaxIts;
+constexpr int kGsState = kGsRhs + kGsMaxVec;
+// c_i = sum over blocks of part (i < nv); w -= sum_i c_i V_i; H[i][col] = c_i (accumulate:
 // += c_i); part2 != nullptr: block shares of ||w||^2 into part2[(b * nblk + blk) * kGsMaxVec]
 template <typename T>
 cudaError_t launch_gs_orth(vec2<T>* w, const vec2<T>* V, long long ld, int nv, long long N, const double2* part,
-                           double2* H, int col, int accumulate, double2* part2, const Batch& bt, cudaStream_t s);
-// h = sqrt(sum over blocks of part2); out = w / h (0 when h = 0); h stored at H[b][row][col]
-// (row < 0: in beta[b])
+                           double2* st, int col, int accumulate, double2* part2, const Batch& bt, cudaStream_t s);
+// h = sqrt(sum over blocks of part2); out = w / h (0 when h = 0).  col < 0: h is the initial
+// residual norm (g = h e1); else h = H[col + 1][col], and column col is rotated by the
+// previous rotations and a new one that zeroes h (applied to g too)
 template <typename T>
-cudaError_t launch_gs_scale(vec2<T>* out, const vec2<T>* w, long long N, const double2* part2, double2* H, int row,
-                            int col, double* beta, const Batch& bt, cudaStream_t s);
-// y = argmin ||beta e1 - H y|| over the first m columns (Givens rotations, FP64); x += V y
-// (overwrite: x = V y)
+cudaError_t launch_gs_scale(vec2<T>* out, const vec2<T>* w, long long N, const double2* part2, double2* st, int col,
+                            const Batch& bt, cudaStream_t s);
+// y = R^{-1} g over the first m columns (back substitution); x += V y (overwrite: x = V y)
 template <typename T>
-cudaError_t launch_gs_update(vec2<T>* x, const vec2<T>* V, long long ld, int m, long long N, const double2* H,
-                             const double* beta, int overwrite, const Batch& bt, cudaStream_t s);
+cudaError_t launch_gs_update(vec2<T>* x, const vec2<T>* V, long long ld, int m, long long N, const double2* st,
+                             int overwrite, const Batch& bt, cudaStream_t s);
 
 // ---- FP64 Krylov kernels (blas.cu) ----
 // Fixed reduction grid: results do not depend on timing or launch history.

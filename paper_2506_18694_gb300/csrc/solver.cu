@@ -255,9 +255,7 @@ int gs_its(const hh_options* o) {
 }
 // its FP64 scratch of one level: block sums (two sets), Hessenberg matrices, norms
 size_t gs_small_bytes(long long N, int nb) {
-    return (size_t)nb * (2 * (size_t)hh::gs_blocks(N) * hh::kGsMaxVec + hh::kGsMaxVec * hh::kGsMaxIts) *
-               sizeof(double2) +
-           (size_t)nb * sizeof(double);
+    return (size_t)nb * (2 * (size_t)hh::gs_blocks(N) * hh::kGsMaxVec + hh::kGsState) * sizeof(double2);
 }
 
 // Device bytes of one precision's multigrid buffers for nb problems plus the coefficient
@@ -609,8 +607,7 @@ struct MG {
         const int nblk = hh::gs_blocks(N);
         double2* part = (double2*)H->gsm[l];
         double2* part2 = part + (size_t)p->nb * nblk * hh::kGsMaxVec;
-        double2* Hm = part2 + (size_t)p->nb * nblk * hh::kGsMaxVec;
-        double* beta = (double*)(Hm + (size_t)p->nb * hh::kGsMaxVec * hh::kGsMaxIts);
+        double2* st = part2 + (size_t)p->nb * nblk * hh::kGsMaxVec;  // least-squares state
         // z0 = omega D^{-1} (b - A_L x), beta = ||z0||, v_0 = z0 / beta
         hh::MArgs<T> a = margs(l, R_AL);
         a.x = xzero ? nullptr : x;
@@ -621,7 +618,7 @@ struct MG {
         a.beta = Cx<T>{1, 0};
         HH_LAUNCH(march(hh::M_DAXPBY, a));
         HH_LAUNCH(hh::launch_gs_dot<T>(W, ld, 1, W, N, part, bt, s));
-        HH_LAUNCH(hh::launch_gs_scale<T>(Vb, W, N, part, Hm, -1, 0, beta, bt, s));
+        HH_LAUNCH(hh::launch_gs_scale<T>(Vb, W, N, part, st, -1, bt, s));
         for (int j = 0; j < its; ++j) {
             V2* vj = Vb + (long long)j * ld;
             hh::MArgs<T> m = margs(l, R_AL);
@@ -633,12 +630,12 @@ struct MG {
             HH_LAUNCH(march(hh::M_DAXPBY, m));
             // classical Gram-Schmidt, twice
             HH_LAUNCH(hh::launch_gs_dot<T>(Vb, ld, j + 1, W, N, part, bt, s));
-            HH_LAUNCH(hh::launch_gs_orth<T>(W, Vb, ld, j + 1, N, part, Hm, j, 0, nullptr, bt, s));
+            HH_LAUNCH(hh::launch_gs_orth<T>(W, Vb, ld, j + 1, N, part, st, j, 0, nullptr, bt, s));
             HH_LAUNCH(hh::launch_gs_dot<T>(Vb, ld, j + 1, W, N, part, bt, s));
-            HH_LAUNCH(hh::launch_gs_orth<T>(W, Vb, ld, j + 1, N, part, Hm, j, 1, part2, bt, s));
-            HH_LAUNCH(hh::launch_gs_scale<T>(Vb + (long long)(j + 1) * ld, W, N, part2, Hm, j + 1, j, beta, bt, s));
+            HH_LAUNCH(hh::launch_gs_orth<T>(W, Vb, ld, j + 1, N, part, st, j, 1, part2, bt, s));
+            HH_LAUNCH(hh::launch_gs_scale<T>(Vb + (long long)(j + 1) * ld, W, N, part2, st, j, bt, s));
         }
-        HH_LAUNCH(hh::launch_gs_update<T>(x, Vb, ld, its, N, Hm, beta, xzero ? 1 : 0, bt, s));
+        HH_LAUNCH(hh::launch_gs_update<T>(x, Vb, ld, its, N, st, xzero ? 1 : 0, bt, s));
         return HH_OK;
     }
 
