@@ -193,6 +193,23 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- native arm
+def max_over_ranks(x, device):
+    """The largest of every rank's x (each rank passes its own; all get the maximum): the job
+    takes as long as its slowest rank."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(nodes, vcycles_per_rank, total_s, world):
+    """Whole-job DoF x V-cycles per second: every rank solves its own copy of the workload
+    (replicas, weak scaling), timed by the slowest rank."""
+    return world * nodes * vcycles_per_rank / total_s
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -252,13 +269,9 @@ def main():
     step_ms = [a.elapsed_time(z) for a, z in ev]
     total_s = sum(step_ms) / 1e3
     if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+        total_s = max_over_ranks(total_s, "cuda")
     vcycles = sum(i.vcycles for i in infos)
-    value = world * N * vcycles / total_s
+    value = job_value(N, vcycles, total_s, world)
     launches = sum(i.kernel_launches for i in infos)
 
     # end to end through the public API with host buffers (copies inside the timed region)
