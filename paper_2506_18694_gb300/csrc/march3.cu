@@ -41,12 +41,12 @@ __device__ __forceinline__ int bclass3(int tx, int ty, int tz) {
     return c - (c > 13);
 }
 
-// Value of the stencil field at node (i, j, l) of the grid, which holds an unknown there.
+// Value of the stencil field at node (i, j, l) of the grid (offset p), which holds an unknown
+// there.
 template <typename T, int MODE>
 __device__ __forceinline__ Cx<T> field3(const MArgs<T>& a, const PCoef<T>& c, const Cx<T>* bw, const VPtrs<T>& v,
-                                        int i, int j, int l) {
-    const int n = a.g.n, nn = a.g.nn;
-    const long long p = ((long long)l * nn + j) * nn + i;
+                                        int i, int j, int l, long long p) {
+    const int n = a.g.n;
     if (MODE == M_JACOBI2_ZERO) {
         // first sweep from x = 0: x1 = omega D^{-1} b
         const Cx<T> b = ld<T>(v.z, p);
@@ -114,19 +114,22 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__
     const int l0 = (blockIdx.z - b * zt) * R;
     const int ic = clampi3(i, 0, n), jc = clampi3(j, 0, n);
     const bool cvoid = void1(i, n, a.g.dir[0], a.g.dir[1]) || void1(j, n, a.g.dir[2], a.g.dir[3]);
+    const long long ps = (long long)nn * nn;
+    const long long colc = (long long)jc * nn + ic;
 
     Cx<T> fv[NP], xs[NP];
 #pragma unroll
     for (int t = 0; t < NP; ++t) {
         const int l = l0 - 1 + t;
+        // (a node of a plane that is not void lies inside the cube: no clamp needed)
         fv[t] = (cvoid || void1(l, n, a.g.dir[4], a.g.dir[5])) ? cx<T>(0, 0)
-                                                               : field3<T, MODE>(a, cf, bw, v, ic, jc, clampi3(l, 0, n));
+                                                               : field3<T, MODE>(a, cf, bw, v, ic, jc, l, colc + l * ps);
     }
     Cx<T> zv[R];
     const bool out_row = w >= 1 && w <= kWarps3 - 2;
 #pragma unroll
     for (int t = 0; t < R; ++t)
-        zv[t] = (NEEDZ && out_row) ? ld<T>(v.z, ((long long)clampi3(l0 + t, 0, n) * nn + jc) * nn + ic) : cx<T>(0, 0);
+        zv[t] = (NEEDZ && out_row) ? ld<T>(v.z, colc + clampi3(l0 + t, 0, n) * ps) : cx<T>(0, 0);
 #pragma unroll
     for (int t = 0; t < NP; ++t) {
         xs[t] = shfl_up3(fv[t]) + shfl_dn3(fv[t]);
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__
         if (l > n) break;
         const int tp = t + 1;  // local plane of the output
         const Cx<T> vy2 = ysum(sv, tp + 1), sy2 = ysum(ss, tp + 1);
-        const long long p = ((long long)l * nn + j) * nn + i;
+        const long long p = colc + l * ps;
         Cx<T> ax, dinv_w;
         bool masked = false;
         if (colrow_inner && l >= 1 && l <= n - 1) {
