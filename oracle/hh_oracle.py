@@ -397,6 +397,8 @@ class Problem:
     delta: float
     delta_hat: float
     opts: Options = field(default_factory=Options)
+    al_coeff: tuple = None      # (c_K, c_M, c_G) of the operator the inner cycles solve; default
+                                # A_L of Def. 4.1 (the mixed formulation passes its own, Def. 4.2)
 
     def __post_init__(self):
         if self.k <= 0 or self.delta < 0 or self.delta_hat <= 0:
@@ -413,7 +415,8 @@ class Problem:
             self.grids.append(self.grids[-1].coarse())
         self.mats = [assemble(g) for g in self.grids]
         self.P = [prolongation(self.grids[l]) for l in range(L - 1)]
-        self.AL = [combine(m, coeff_AL(self.k, self.delta_hat)) for m in self.mats]
+        cal = self.al_coeff if self.al_coeff is not None else coeff_AL(self.k, self.delta_hat)
+        self.AL = [combine(m, cal) for m in self.mats]
         self.AR0 = combine(self.mats[0], coeff_AR(self.k, self.delta_hat))
         self.B = combine(self.mats[0], coeff_B(self.k, self.delta))
         self.free = [g.free() for g in self.grids]
