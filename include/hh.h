@@ -82,6 +82,8 @@ typedef enum { HH_C128 = 0, HH_C64 = 1 } hh_precision;
 typedef enum { HH_OUTER_FGMRES = 0, HH_OUTER_RICHARDSON = 1 } hh_outer;
 /* multigrid smoother (options.smoother) */
 typedef enum { HH_SMOOTH_JACOBI = 0, HH_SMOOTH_GMRES = 1 } hh_smoother;
+/* discretisation (options.formulation) */
+typedef enum { HH_FORM_PRIMAL = 0, HH_FORM_MIXED = 1 } hh_formulation;
 
 /* Operators that hh_apply can apply (coefficient triples of the weak forms). */
 typedef enum {
@@ -138,6 +140,16 @@ typedef struct {
                          /* Jacobi-preconditioned level system D^{-1} A_L x = D^{-1} b from    */
                          /* the current iterate (Sec. 5.3's smoother; nu <= 8); the cycle is   */
                          /* then not linear in its right side, which FGMRES allows            */
+    int formulation;     /* hh_formulation: HH_FORM_PRIMAL (default): u in Q1, the system     */
+                         /* B_delta u = b; HH_FORM_MIXED: (sigma, u) in V_h x Q1 (Sec. 2),     */
+                         /* the system A_delta (sigma, u) = (b_sigma, b_u) solved by FGMRES    */
+                         /* with the shifted-HSS preconditioner of Def. 4.2 (sigma eliminated; */
+                         /* cycles on A_mix = K + k^2 (dh - i)^2 M + k^2 (dh - i) M_Gamma).     */
+                         /* V_h: per cell, component a multilinear in the other coordinates    */
+                         /* and constant along a (it contains grad Q1).  Vectors of a mixed    */
+                         /* problem hold hh_sigma_dofs(grid) sigma entries ((cell x fastest,   */
+                         /* component a, vertex s of the other axes) order) and then the       */
+                         /* nodes; one problem per object (no batches), no solve server        */
 } hh_options;
 
 typedef struct {
@@ -218,7 +230,8 @@ HH_API void hh_destroy(hh_problem* p);
  * Solve B_delta u = rhs to ||rhs - B_delta u||_2 <= tol ||rhs||_2 (true residual,
  * recomputed in FP64 at the end of every restart cycle) for every problem of the batch.
  * rhs (load vectors), u and the optional initial guess x0 are device complex128 vectors
- * of level 0 (nb blocks).  Blocking: returns when u is written.  info, if not NULL,
+ * of hh_vector_length(p) entries per problem (nb blocks): level-0 nodes, or for a mixed
+ * problem its sigma entries and then the nodes.  Blocking: returns when u is written.  info, if not NULL,
  * points to nb records (kernel_launches is counted for the whole call in info[0]).
  * Returns HH_OK when every problem converged, HH_NOT_CONVERGED when one reached
  * max_outer (u holds the last iterates and info is filled); on errors u is unspecified
@@ -244,6 +257,15 @@ HH_API hh_status hh_solve_host_nodal(hh_problem* p, const void* f_host, double t
  * library (the paper has none): it lets a serving loop reuse a problem's hierarchy and
  * Krylov basis for the next request on the same grid.
  */
+/* sigma entries of a mixed problem on `grid`: n^dim cells x dim components x 2^(dim-1) */
+HH_API long long hh_sigma_dofs(const hh_grid* grid);
+/* entries of one problem's right side / solution for hh_solve: nodes (primal) or sigma
+ * entries and nodes (mixed) */
+HH_API long long hh_vector_length(const hh_problem* p);
+/* y = the system operator x in FP64 (B_delta, or the mixed A_delta of Sec. 2); x, y: device
+ * complex128 vectors of hh_vector_length(p) entries per problem */
+HH_API hh_status hh_apply_system(hh_problem* p, const void* x, void* y);
+
 HH_API hh_status hh_set_params(hh_problem* p, const double* k, const double* delta, const double* delta_hat);
 
 /*
@@ -281,15 +303,17 @@ HH_API hh_status hh_vcycle(hh_problem* p, int precision, const void* b, void* x)
 /* rhs = (k-1)/(k+1) A_R u + 2k/(k+1) r on level 0 (Def. 4.1); u == NULL means u = 0. */
 HH_API hh_status hh_hss_rhs(hh_problem* p, int precision, const void* u, const void* r, void* rhs);
 
-/* z = shifted-HSS preconditioner applied to r (Def. 4.1), r and z complex128 on level 0;
- * the inner V-cycles run in the problem's precision.  Blocking. */
+/* z = shifted-HSS preconditioner applied to r (Def. 4.1; Def. 4.2 for a mixed problem), r
+ * and z complex128 vectors of hh_vector_length(p) entries per problem; the inner cycles run
+ * in the problem's precision.  Blocking. */
 HH_API hh_status hh_precondition(hh_problem* p, const void* r, void* z);
 
 /* b = M f (load vector of a nodal f, Sec. 2), complex128 on level 0. */
 HH_API hh_status hh_load_vector(hh_problem* p, const void* f, void* b);
 
-/* out[2b] + i out[2b+1] = x_b^H y_b over the level-0 complex128 vectors of problem b, for
- * every problem of the batch (deterministic order; out holds 2 nb doubles).  Blocking. */
+/* out[2b] + i out[2b+1] = x_b^H y_b over the complex128 vectors of problem b
+ * (hh_vector_length(p) entries), for every problem of the batch (deterministic order; out
+ * holds 2 nb doubles).  Blocking. */
 HH_API hh_status hh_dot(hh_problem* p, const void* x, const void* y, double* out);
 
 /*

@@ -277,6 +277,26 @@ template <typename T>
 cudaError_t launch_gs_update(vec2<T>* x, const vec2<T>* V, long long ld, int m, long long N, const double2* st,
                              int overwrite, const Batch& bt, cudaStream_t s);
 
+// ---- mixed formulation (mixed.cu): sigma-space kernels, one problem ----
+// sigma vectors hold n^dim cells x dim components x 2^(dim-1) entries; u vectors the nodes.
+template <typename T> struct MixArgs {
+    GridDesc g;
+    const vec2<T>* sig;   // sigma input (launch_mix_sigma: null = 0)
+    const vec2<T>* sig2;  // launch_mix_div: second sigma input (null = 0)
+    const vec2<T>* u;     // launch_mix_sigma: u input (null = 0)
+    const vec2<T>* z;     // launch_mix_sigma: sigma-space input (null = 0)
+    vec2<T>* y;           // output
+    Cx<T> cs, cd, cz;
+    int mass_out;
+};
+// mass_out = 1: y = M_sigma (cs sig + cd D u) + cz z;  mass_out = 0: y = cs sig + cd D u + cz M_sigma^{-1} z
+// (D u: the gradient of u in V_h, so that M_sigma D = G)
+template <typename T>
+cudaError_t launch_mix_sigma(const MixArgs<T>& a, cudaStream_t s);
+// y += G^T (cs sig + cd sig2) on the free nodes (y a u vector)
+template <typename T>
+cudaError_t launch_mix_div(const MixArgs<T>& a, cudaStream_t s);
+
 // ---- FP64 Krylov kernels (blas.cu) ----
 // Fixed reduction grid: results do not depend on timing or launch history.
 constexpr int kRedBlocks = 304;

@@ -248,6 +248,7 @@ hh_status hh_server_create(int slots, size_t device_budget, const hh_options* op
     if (slots < 1 || slots > 64) return invalid("slots must be in 1..64");
     if (device_budget == 0 || !opts) return invalid("zero budget or null options");
     if (opts->levels < 1 || opts->levels > 16) return invalid("levels must be in 1..16");
+    if (opts->formulation != HH_FORM_PRIMAL) return invalid("the server solves primal problems");
     const hh_grid g{2, std::max(2, 1 << (opts->levels - 1))};
     if (hh_footprint_bytes(&g, opts) == 0) return HH_ERR_INVALID;  // options rejected, message set
     auto* S = new hh_server();

@@ -71,6 +71,12 @@ Triple triple_B(double k, double delta) {
 }
 Triple triple_AL(double k, double dh) { return {1.0, zc(dh * dh - k * k, -2.0 * dh * k * k), zc(dh, -k * k)}; }
 Triple triple_AR(double k, double dh) { return {-1.0, zc(k * k - dh * dh, -2.0 * dh * k * k), zc(-dh, -k * k)}; }
+// the u-operator of the mixed shifted-HSS step after eliminating sigma (Def. 4.2):
+// K + k^2 (dh - i)^2 M + k^2 (dh - i) M_Gamma
+Triple triple_AMIX(double k, double dh) {
+    const zc s(dh, -1.0);
+    return {1.0, k * k * s * s, k * k * s};
+}
 
 template <typename T>
 OpCoef<T> to_coef(const Triple& t) {
@@ -92,7 +98,10 @@ constexpr int kModes = 12;      // hh::MarchMode values 0..10 and the coarsest-l
 constexpr int kCoarseMode = 11;
 
 // Operators with a coefficient table (per problem and level).
-enum Role { R_K = 0, R_M, R_MG, R_AL, R_AR, R_B, R_BHAT, R_COUNT };
+// R_AL is the operator the cycles solve (A_mix for a mixed problem); R_MIXU the u-rows of the
+// mixed system, (delta - i k) M + M_Gamma; R_MIXH those of the mixed HSS step's right side,
+// k (dh + i) M + k M_Gamma.
+enum Role { R_K = 0, R_M, R_MG, R_AL, R_AR, R_B, R_BHAT, R_MIXU, R_MIXH, R_COUNT };
 
 // Device buffers of the multigrid hierarchy in one precision (nb problems per vector).
 struct Hier {
@@ -102,6 +111,9 @@ struct Hier {
     std::vector<void*> wk, wr;        // W-cycles (levels >= 1): kept correction, its residual
     std::vector<void*> gv, gsm;       // GMRES smoother, per level: basis and work vector; sums,
                                       // Hessenberg matrices and norms (FP64)
+    void* sig = nullptr;              // mixed: sigma iterate of the HSS loop and M_sigma^{-1} g_s
+    void* ws = nullptr;
+    void** ssrc = nullptr;            // mixed: device pointer to sig (for the gather kernel)
     void* r_lo = nullptr;             // level-0 copy of the preconditioner input
     void* rhs = nullptr;              // level-0 HSS right side
     void* ca = nullptr;               // extra level-0 buffers for cycles_per_hss > 1
@@ -139,7 +151,9 @@ struct hh_problem {
     int* h_active = nullptr;   // pinned mirror
     Hier hier[2];
     // FP64 Krylov storage (level 0), laid out [vector][problem][node]
-    long long N = 0;
+    long long N = 0;            // entries per problem of the Krylov vectors (+ ns when mixed)
+    bool mixed = false;         // mixed formulation (one problem)
+    long long ns = 0;           // its sigma entries
     double2* V = nullptr;       // (restart+1) x nb x N
     double2* Z = nullptr;       // restart x nb x N
     double2* x = nullptr;       // nb x N
@@ -182,9 +196,14 @@ GridDesc level_desc(const hh_grid& grid, const int* bc, int l) {
 }
 
 // Device bytes of the Krylov storage and batch bookkeeping for nb problems (matches create).
-size_t krylov_bytes(const hh_grid* grid, int restart, int nb) {
+long long sigma_dofs(const hh_grid* grid) {
+    const long long n = grid->n;
+    return grid->dim == 3 ? n * n * n * 3 * 4 : n * n * 2 * 2;
+}
+
+size_t krylov_bytes(const hh_grid* grid, int restart, int nb, long long extra) {
     long long nn = grid->n + 1;
-    long long N = nn * nn * (grid->dim == 3 ? nn : 1);
+    long long N = nn * nn * (grid->dim == 3 ? nn : 1) + extra;
     const size_t m = (size_t)restart, B = (size_t)nb;
     size_t tot = 2 * sizeof(int) * B;                      // nhss, active
     tot += (2 * m + 1 + 3) * B * (size_t)N * 16;           // V, Z, x, bvec, r
@@ -197,7 +216,7 @@ size_t krylov_bytes(const hh_grid* grid, int restart, int nb) {
 template <typename T>
 PCoef<T> make_pcoef(const hh_problem* p, int role, const GridDesc& g, int b) {
     const double k = p->k[b], dh = p->dh[b], delta = p->delta[b];
-    Triple op, opd = triple_AL(k, dh);
+    Triple op, opd = p->mixed ? triple_AMIX(k, dh) : triple_AL(k, dh);
     double al = 0.0, be = 0.0;
     switch (role) {
         case R_K: op = {1.0, 0.0, 0.0}; break;
@@ -210,6 +229,8 @@ PCoef<T> make_pcoef(const hh_problem* p, int role, const GridDesc& g, int b) {
             be = 2.0 * k / (k + 1.0);
             break;
         case R_B: op = triple_B(k, delta); break;
+        case R_MIXU: op = {0.0, zc(delta, -k), 1.0}; break;
+        case R_MIXH: op = {0.0, zc(k * dh, k), k}; break;
         default: op = triple_B(k, dh); break;
     }
     if (role != R_AR && role != R_AL) opd = op;
@@ -272,6 +293,8 @@ size_t hier_bytes(const hh_grid* grid, const hh_options* o, int prec, int nb) {
         if (l == 0) tot += 5 * (size_t)N * elem * B;  // r_lo, rhs, ca, cb, cres
         if (gs > 0) tot += (size_t)(gs + 2) * N * elem * B + gs_small_bytes(N, nb);  // basis, w, sums
     }
+    if (o->formulation == HH_FORM_MIXED)  // r_lo's sigma part, sig, ws, the pointer table
+        tot += 3 * (size_t)sigma_dofs(grid) * elem * B + sizeof(void*) * B;
     tot += sizeof(void*) * B;  // usrc
     // coefficient tables of both precisions (and the 3D boundary-class tables)
     tot += (size_t)R_COUNT * levels * B * (sizeof(PCoef<float>) + sizeof(PCoef<double>));
@@ -327,7 +350,15 @@ hh_status ensure_hier(hh_problem* p, int prec) {
         HH_CUDA(cudaMemsetAsync(H.t[l], 0, nbytes, p->s));
     }
     const size_t n0 = (size_t)p->lv[0].N * p->nb * H.elem;
-    HH_TRY(dmalloc(p, &H.r_lo, n0));
+    const size_t nsb = (size_t)p->ns * p->nb * H.elem;
+    HH_TRY(dmalloc(p, &H.r_lo, n0 + nsb));
+    if (p->mixed) {
+        HH_TRY(dmalloc(p, &H.sig, nsb));
+        HH_TRY(dmalloc(p, &H.ws, nsb));
+        HH_TRY(dmalloc(p, (void**)&H.ssrc, sizeof(void*)));
+        HH_CUDA(cudaMemcpyAsync(H.ssrc, &H.sig, sizeof(void*), cudaMemcpyHostToDevice, p->s));
+        HH_CUDA(cudaStreamSynchronize(p->s));
+    }
     HH_TRY(dmalloc(p, &H.rhs, n0));
     HH_TRY(dmalloc(p, &H.ca, n0));
     HH_TRY(dmalloc(p, &H.cb, n0));
@@ -768,6 +799,73 @@ struct MG {
         return HH_OK;
     }
 
+    // The shifted-HSS preconditioner of Def. 4.2 for a mixed problem on r_lo = (R_s, R_u),
+    // through the elimination of sigma.  Each step, from (sigma, u):
+    //   w_s    = M_s^{-1} g_s = c1 k (dh + i) sigma + c1 D u + c2 M_s^{-1} R_s
+    //   rhs_u  = k (dh - i) [c1 (k (dh + i) M + k M_Gamma) u + c2 R_u] - G^T (k (dh - i) c1 sigma + w_s)
+    //   u'     = cycles on A_mix u' = rhs_u
+    //   sigma' = (w_s + D u') / (k (dh - i))
+    // (g_s, g_u: the right sides of Def. 4.2's tau- and v-rows; G = M_s D).  *u_out receives the
+    // buffer holding u; sigma ends in H->sig.
+    hh_status mixed_hss_loop(V2** u_out) {
+        const double k = p->k[0], dh = p->dh[0];
+        const double c1 = (k - 1.0) / (k + 1.0), c2 = 2.0 * k / (k + 1.0);
+        const std::complex<double> kp(k * dh, k), km(k * dh, -k);  // k (dh + i), k (dh - i)
+        auto C = [](std::complex<double> z) { return Cx<T>{T(z.real()), T(z.imag())}; };
+        const V2* Rs = (const V2*)H->r_lo;
+        const V2* Ru = Rs + p->ns;
+        V2* sig = (V2*)H->sig;
+        V2* ws = (V2*)H->ws;
+        V2* rhs = (V2*)H->rhs;
+        HH_LAUNCH(hh::launch_zero<T>(sig, p->ns, batch(0), s));
+        V2* u = nullptr;
+        for (int it = 0; it < p->max_nhss; ++it) {
+            hh::MixArgs<T> a{};
+            a.g = p->lv[0];
+            a.sig = sig;
+            a.u = u;
+            a.z = Rs;
+            a.y = ws;
+            a.cs = C(c1 * kp);
+            a.cd = C(std::complex<double>(c1, 0.0));
+            a.cz = C(std::complex<double>(c2, 0.0));
+            a.mass_out = 0;
+            HH_LAUNCH(hh::launch_mix_sigma<T>(a, s));
+            hh::MArgs<T> m = margs(0, R_MIXH);
+            m.x = u;
+            m.xzero = u == nullptr;
+            m.z = Ru;
+            m.y = rhs;
+            m.alpha = C(c1 * km);
+            m.beta = C(c2 * km);
+            HH_LAUNCH(march(hh::M_AXPBY, m));
+            hh::MixArgs<T> d{};
+            d.g = p->lv[0];
+            d.sig = sig;
+            d.sig2 = ws;
+            d.y = rhs;
+            d.cs = C(-c1 * km);
+            d.cd = C(std::complex<double>(-1.0, 0.0));
+            HH_LAUNCH(hh::launch_mix_div<T>(d, s));
+            HH_TRY(mg_solve(rhs, nullptr, &u));
+            hh::MixArgs<T> r{};
+            r.g = p->lv[0];
+            r.sig = ws;
+            r.u = u;
+            r.y = sig;
+            r.cs = C(1.0 / km);
+            r.cd = C(1.0 / km);
+            r.mass_out = 0;
+            HH_LAUNCH(hh::launch_mix_sigma<T>(r, s));
+        }
+        if (!u) {  // no HSS step: u = 0
+            u = (V2*)H->cres;
+            HH_LAUNCH(hh::launch_zero<T>(u, Nl(0), batch(0), s));
+        }
+        *u_out = u;
+        return HH_OK;
+    }
+
     // The HSS loop of Def. 4.1 on r_lo (already in this precision).  src[b] receives the
     // buffer that holds problem b's result (its loop may end before the others').
     hh_status hss_loop(std::vector<V2*>* src) {
@@ -826,10 +924,19 @@ MG<T> make_mg(hh_problem* p, int prec, cudaStream_t s) {
 }
 
 template <typename T>
+hh_status run_hss(MG<T>& m, std::vector<hh::vec2<T>*>* src) {
+    if (!m.p->mixed) return m.hss_loop(src);
+    hh::vec2<T>* u;
+    HH_TRY(m.mixed_hss_loop(&u));
+    src->assign(1, u);
+    return HH_OK;
+}
+
+template <typename T>
 hh_status record_hss(hh_problem* p, int prec) {
     MG<T> m = make_mg<T>(p, prec, p->s);
     std::vector<hh::vec2<T>*> src;
-    HH_TRY(m.hss_loop(&src));
+    HH_TRY(run_hss<T>(m, &src));
     Hier& H = p->hier[prec];
     // the pointer table is read by the gather kernel after the loop (constant per problem)
     static_assert(sizeof(void*) == sizeof(hh::vec2<T>*), "pointer size");
@@ -844,7 +951,7 @@ hh_status precondition_async(hh_problem* p, const double2* r, double2* z) {
     HH_TRY(ensure_hier(p, prec));
     Hier& H = p->hier[prec];
     const long long N = p->lv[0].N;
-    const long long NT = N * p->nb;
+    const long long NT = p->N * p->nb;  // (sigma and) nodes
     if (prec == HH_C64) {
         HH_LAUNCH(hh::launch_cast_d2f(r, (float2*)H.r_lo, NT, p->s));
     } else {
@@ -860,7 +967,7 @@ hh_status precondition_async(hh_problem* p, const double2* r, double2* z) {
             MG<double> md = make_mg<double>(p, prec, p->s);
             std::vector<float2*> sf;
             std::vector<double2*> sd;
-            hh_status st = prec == HH_C64 ? mf.hss_loop(&sf) : md.hss_loop(&sd);
+            hh_status st = prec == HH_C64 ? run_hss<float>(mf, &sf) : run_hss<double>(md, &sd);
             cudaError_t ec = cudaStreamEndCapture(p->s, &g);
             if (st != HH_OK) {
                 if (ec == cudaSuccess) cudaGraphDestroy(g);
@@ -885,10 +992,15 @@ hh_status precondition_async(hh_problem* p, const double2* r, double2* z) {
             HH_TRY(record_hss<double>(p, prec));
         }
     }
+    double2* zu = z + p->ns;  // mixed (one problem): sigma, then the nodes
     if (prec == HH_C64) {
-        HH_LAUNCH(hh::launch_gather_c128<float>((const float2* const*)H.usrc, z, N, p->nb, active_flags(p), p->s));
+        if (p->mixed)
+            HH_LAUNCH(hh::launch_gather_c128<float>((const float2* const*)H.ssrc, z, p->ns, 1, nullptr, p->s));
+        HH_LAUNCH(hh::launch_gather_c128<float>((const float2* const*)H.usrc, zu, N, p->nb, active_flags(p), p->s));
     } else {
-        HH_LAUNCH(hh::launch_gather_c128<double>((const double2* const*)H.usrc, z, N, p->nb, active_flags(p), p->s));
+        if (p->mixed)
+            HH_LAUNCH(hh::launch_gather_c128<double>((const double2* const*)H.ssrc, z, p->ns, 1, nullptr, p->s));
+        HH_LAUNCH(hh::launch_gather_c128<double>((const double2* const*)H.usrc, zu, N, p->nb, active_flags(p), p->s));
     }
     return HH_OK;
 }
@@ -911,12 +1023,41 @@ hh_status op_axpby(hh_problem* p, int l, int role, const hh::vec2<T>* x, const h
     return HH_OK;
 }
 
+// Mixed system (Sec. 2): y = sgn A_delta x + b, x = (sigma, u), b = (b_s, b_u) or none:
+//   sigma-rows: M_s (sgn (delta - i k) sigma - sgn D u) + b_s;
+//   u-rows:     sgn ((delta - i k) M + M_Gamma) u + b_u + sgn G^T sigma.
+hh_status mixed_system(hh_problem* p, const double2* x, const double2* b, double sgn, double2* y) {
+    const zc z(p->delta[0], -p->k[0]);
+    hh::MixArgs<double> a{};
+    a.g = p->lv[0];
+    a.sig = x;
+    a.u = x + p->ns;
+    a.z = b;
+    a.y = y;
+    a.cs = Cx<double>{sgn * z.real(), sgn * z.imag()};
+    a.cd = Cx<double>{-sgn, 0};
+    a.cz = Cx<double>{b ? 1.0 : 0.0, 0};
+    a.mass_out = 1;
+    HH_LAUNCH(hh::launch_mix_sigma<double>(a, p->s));
+    HH_TRY(op_axpby<double>(p, 0, R_MIXU, x + p->ns, b ? b + p->ns : nullptr, y + p->ns, Cx<double>{sgn, 0},
+                            Cx<double>{b ? 1.0 : 0.0, 0}, p->s));
+    hh::MixArgs<double> d{};
+    d.g = p->lv[0];
+    d.sig = x;
+    d.y = y + p->ns;
+    d.cs = Cx<double>{sgn, 0};
+    HH_LAUNCH(hh::launch_mix_div<double>(d, p->s));
+    return HH_OK;
+}
+
 hh_status apply_B(hh_problem* p, const double2* x, double2* y) {
+    if (p->mixed) return mixed_system(p, x, nullptr, 1.0, y);
     return op_axpby<double>(p, 0, R_B, x, nullptr, y, Cx<double>{1, 0}, Cx<double>{0, 0}, p->s);
 }
 
 // r = bvec - B x
 hh_status residual_B(hh_problem* p, const double2* x, double2* r) {
+    if (p->mixed) return mixed_system(p, x, p->bvec, -1.0, r);
     return op_axpby<double>(p, 0, R_B, x, p->bvec, r, Cx<double>{-1, 0}, Cx<double>{1, 0}, p->s);
 }
 
@@ -1350,6 +1491,9 @@ hh_status check_args(const hh_grid* grid, int nb, const double* k, const double*
     if (o->tile_rows != 0 && o->tile_rows != 2 && o->tile_rows != 4 && o->tile_rows != 8)
         return fail(HH_ERR_INVALID, "tile_rows must be 0, 2, 4 or 8");
     if (o->tile_form < 0 || o->tile_form > 2) return fail(HH_ERR_INVALID, "tile_form must be 0, 1 or 2");
+    if (o->formulation != HH_FORM_PRIMAL && o->formulation != HH_FORM_MIXED)
+        return fail(HH_ERR_INVALID, "formulation must be HH_FORM_PRIMAL or HH_FORM_MIXED");
+    if (o->formulation == HH_FORM_MIXED && nb != 1) return fail(HH_ERR_INVALID, "mixed problems are not batched");
     if (o->smoother != HH_SMOOTH_JACOBI && o->smoother != HH_SMOOTH_GMRES)
         return fail(HH_ERR_INVALID, "smoother must be HH_SMOOTH_JACOBI or HH_SMOOTH_GMRES");
     if (o->smoother == HH_SMOOTH_GMRES &&
@@ -1415,6 +1559,7 @@ void hh_options_default(hh_options* o) {
     o->cycle_gamma = 1;
     o->tile_form = 0;
     o->smoother = HH_SMOOTH_JACOBI;
+    o->formulation = HH_FORM_PRIMAL;
 }
 
 size_t hh_footprint_batch_bytes(const hh_grid* grid, const hh_options* o, int nb) {
@@ -1422,7 +1567,8 @@ size_t hh_footprint_batch_bytes(const hh_grid* grid, const hh_options* o, int nb
     const int bc0[6] = {0, 0, 0, 0, 0, 0};
     std::vector<double> one(nb, 1.0), zero(nb, 0.0);
     if (check_args(grid, nb, one.data(), zero.data(), one.data(), bc0, o) != HH_OK) return 0;
-    return hier_bytes(grid, o, o->precision, nb) + krylov_bytes(grid, o->restart, nb);
+    return hier_bytes(grid, o, o->precision, nb) +
+           krylov_bytes(grid, o->restart, nb, o->formulation == HH_FORM_MIXED ? sigma_dofs(grid) : 0);
 }
 
 size_t hh_footprint_bytes(const hh_grid* grid, const hh_options* o) { return hh_footprint_batch_bytes(grid, o, 1); }
@@ -1468,7 +1614,9 @@ hh_status hh_create_batch(const hh_grid* grid, int nb, const double* k, const do
         p->max_nhss = std::max(p->max_nhss, p->nhss.back());
     }
     for (int l = 0; l < opts->levels; ++l) p->lv.push_back(level_desc(*grid, p->bc, l));
-    p->N = p->lv[0].N;
+    p->mixed = opts->formulation == HH_FORM_MIXED;
+    p->ns = p->mixed ? sigma_dofs(grid) : 0;
+    p->N = p->lv[0].N + p->ns;
     p->user = (cudaStream_t)cuda_stream;
     hh_status st = HH_OK;
     auto bail = [&](hh_status s) {
@@ -1569,6 +1717,17 @@ long long hh_level_nodes(const hh_problem* p, int level) {
     return p->lv[level].N;
 }
 
+// dst = src with exact zeros at the Dirichlet nodes (a mixed problem's sigma part copied as is)
+hh_status masked_copy(hh_problem* p, const double2* src, double2* dst) {
+    if (p->mixed) {
+        HH_CUDA(cudaMemcpyAsync(dst, src, (size_t)p->ns * 16, cudaMemcpyDeviceToDevice, p->s));
+        HH_LAUNCH(hh::launch_mask_copy(p->lv[0], src + p->ns, dst + p->ns, 1, p->s));
+    } else {
+        HH_LAUNCH(hh::launch_mask_copy(p->lv[0], src, dst, p->nb, p->s));
+    }
+    return HH_OK;
+}
+
 hh_status hh_solve(hh_problem* p, const void* rhs, double tol, void* u, const void* x0, hh_info* info) {
     if (!p || !rhs || !u) return fail(HH_ERR_INVALID, "null argument");
     if (!(tol > 0)) return fail(HH_ERR_INVALID, "tol must be > 0");
@@ -1580,9 +1739,9 @@ hh_status hh_solve(hh_problem* p, const void* rhs, double tol, void* u, const vo
     }
     auto t0 = std::chrono::steady_clock::now();
     HH_TRY(join_in(p));
-    HH_LAUNCH(hh::launch_mask_copy(p->lv[0], (const double2*)rhs, p->bvec, p->nb, p->s));
+    HH_TRY(masked_copy(p, (const double2*)rhs, p->bvec));
     if (x0) {
-        HH_LAUNCH(hh::launch_mask_copy(p->lv[0], (const double2*)x0, p->x, p->nb, p->s));
+        HH_TRY(masked_copy(p, (const double2*)x0, p->x));
     } else {
         HH_CUDA(cudaMemsetAsync(p->x, 0, (size_t)p->nb * p->N * 16, p->s));
     }
@@ -1618,7 +1777,7 @@ static hh_status solve_host_impl(hh_problem* p, const void* rhs_host, bool nodal
     if (nodal) {
         HH_TRY(op_axpby<double>(p, 0, R_M, p->r, nullptr, p->bvec, Cx<double>{1, 0}, Cx<double>{0, 0}, p->s));
     } else {
-        HH_LAUNCH(hh::launch_mask_copy(p->lv[0], p->r, p->bvec, p->nb, p->s));
+        HH_TRY(masked_copy(p, p->r, p->bvec));
     }
     HH_CUDA(cudaMemsetAsync(p->x, 0, bytes, p->s));
     hh_status st = solve_core(p, tol, inf);
@@ -1640,7 +1799,23 @@ hh_status hh_solve_host(hh_problem* p, const void* rhs_host, double tol, void* u
 }
 
 hh_status hh_solve_host_nodal(hh_problem* p, const void* f_host, double tol, void* u_host, hh_info* info) {
+    if (p && p->mixed) return fail(HH_ERR_INVALID, "nodal sources are for primal problems");
     return solve_host_impl(p, f_host, true, tol, u_host, info);
+}
+
+long long hh_sigma_dofs(const hh_grid* grid) {
+    if (!grid || (grid->dim != 2 && grid->dim != 3) || grid->n < 1) return 0;
+    return sigma_dofs(grid);
+}
+
+long long hh_vector_length(const hh_problem* p) { return p ? p->N : 0; }
+
+hh_status hh_apply_system(hh_problem* p, const void* x, void* y) {
+    if (!p || !x || !y) return fail(HH_ERR_INVALID, "null argument");
+    if (p->mixed && x == y) return fail(HH_ERR_INVALID, "x and y must differ");
+    HH_TRY(join_in(p));
+    HH_TRY(apply_B(p, (const double2*)x, (double2*)y));
+    return join_out(p);
 }
 
 // ---------------------------------------------------------------- building blocks

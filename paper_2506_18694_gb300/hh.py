@@ -20,6 +20,7 @@ HH_OK, HH_NOT_CONVERGED = 0, 1
 HH_C128, HH_C64 = 0, 1
 HH_OUTER_FGMRES, HH_OUTER_RICHARDSON = 0, 1
 HH_SMOOTH_JACOBI, HH_SMOOTH_GMRES = 0, 1
+HH_FORM_PRIMAL, HH_FORM_MIXED = 0, 1
 SOMMERFELD, DIRICHLET = 0, 1
 OP = {"K": 0, "M": 1, "MGAMMA": 2, "AL": 3, "AR": 4, "B": 5, "BHAT": 6}
 
@@ -29,7 +30,8 @@ EXPORTED = (
     "hh_solve_host", "hh_solve_host_nodal", "hh_level_nodes", "hh_apply", "hh_jacobi", "hh_residual_restrict",
     "hh_prolong_correct", "hh_vcycle", "hh_hss_rhs", "hh_precondition", "hh_load_vector", "hh_dot",
     "hh_multidot_noalloc", "hh_server_create", "hh_server_submit", "hh_server_wait", "hh_server_get_stats",
-    "hh_server_destroy", "hh_status_string", "hh_last_error",
+    "hh_server_destroy", "hh_status_string", "hh_last_error", "hh_sigma_dofs", "hh_vector_length",
+    "hh_apply_system",
 )
 
 
@@ -45,7 +47,7 @@ class Options(ctypes.Structure):
         ("precision", ctypes.c_int), ("use_graphs", ctypes.c_int), ("use_pdl", ctypes.c_int),
         ("coarse_cluster_nodes", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
         ("fuse_sweeps", ctypes.c_int), ("outer", ctypes.c_int), ("cycle_gamma", ctypes.c_int),
-        ("tile_form", ctypes.c_int), ("smoother", ctypes.c_int),
+        ("tile_form", ctypes.c_int), ("smoother", ctypes.c_int), ("formulation", ctypes.c_int),
     ]
 
 
@@ -105,6 +107,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "hh_create_batch": (I, [ctypes.POINTER(Grid), I, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Options), P, ctypes.POINTER(P)]),
         "hh_batch_size": (I, [P]),
+        "hh_sigma_dofs": (ctypes.c_longlong, [ctypes.POINTER(Grid)]),
+        "hh_vector_length": (ctypes.c_longlong, [P]),
+        "hh_apply_system": (I, [P, P, P]),
         "hh_autotune": (I, [P, I, ctypes.POINTER(ctypes.c_int)]),
         "hh_set_params": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
         "hh_prepare": (I, [P]),
@@ -266,6 +271,18 @@ class Problem:
         """Entries of a batch vector of level `level` (nb x nodes)."""
         return self.nb * self.nodes(level)
 
+    def system_size(self) -> int:
+        """Entries of a batch right side / solution of hh_solve (nb x hh_vector_length):
+        the nodes, or for a mixed problem its sigma entries and then the nodes."""
+        return self.nb * int(self._lib.hh_vector_length(self._p))
+
+    def apply_system(self, x, y=None):
+        """y = the system operator x in FP64 (B_delta, or the mixed A_delta)."""
+        y = torch.empty_like(x) if y is None else y
+        n = self.system_size()
+        _check(self._lib.hh_apply_system(self._p, _ptr(x, n), _ptr(y, n)))
+        return y
+
     def zeros(self, level=0, dtype=torch.complex128):
         return torch.zeros(self.size(level), dtype=dtype, device="cuda")
 
@@ -276,7 +293,7 @@ class Problem:
     def solve(self, rhs, tol=1e-8, x0=None, u=None):
         u = torch.empty_like(rhs) if u is None else u
         infos = (Info * self.nb)()
-        n0 = self.size(0)
+        n0 = self.system_size()
         st = self._lib.hh_solve(self._p, _ptr(rhs, n0), float(tol), _ptr(u, n0), _ptr(x0, n0), infos)
         _check(st, allow_not_converged=True)
         return u, self._info(infos)
@@ -285,7 +302,7 @@ class Problem:
         """Solve from host arrays (copies included); nodal=True: rhs is the nodal source f."""
         rhs = np.ascontiguousarray(rhs, dtype=np.complex128)
         out = np.empty_like(rhs) if out is None else out
-        if rhs.size != self.size(0) or out.size != rhs.size or out.dtype != np.complex128 \
+        if rhs.size != self.system_size() or out.size != rhs.size or out.dtype != np.complex128 \
                 or not out.flags.c_contiguous:
             raise ValueError("host vectors must be contiguous complex128 of nb x nodes entries")
         infos = (Info * self.nb)()
@@ -332,7 +349,7 @@ class Problem:
 
     def precondition(self, r, z=None):
         z = torch.empty_like(r) if z is None else z
-        n0 = self.size(0)
+        n0 = self.system_size()
         _check(self._lib.hh_precondition(self._p, _ptr(r, n0), _ptr(z, n0)))
         return z
 
@@ -345,7 +362,7 @@ class Problem:
     def dot(self, x, y):
         """x_b^H y_b per problem: a complex (single problem) or a list (batch)."""
         out = (ctypes.c_double * (2 * self.nb))()
-        n0 = self.size(0)
+        n0 = self.system_size()
         _check(self._lib.hh_dot(self._p, _ptr(x, n0), _ptr(y, n0), out))
         vals = [complex(out[2 * b], out[2 * b + 1]) for b in range(self.nb)]
         return vals if self.batched else vals[0]

@@ -46,6 +46,13 @@ def test_footprint_bytes(libhh):
                 dict(smoother=hh.HH_SMOOTH_GMRES, nu_coarse=9)):
         assert hh.footprint_bytes(2, 64, hh.default_options(**bad)) == 0, bad
     assert hh.footprint_bytes(2, 64, hh.default_options(tile_form=2)) == hh.footprint_bytes(2, 64, o)
+    # mixed formulation: sigma entries n^d d 2^(d-1) in the Krylov vectors; one problem per object
+    lib = hh.load_library()
+    assert lib.hh_sigma_dofs(hh.Grid(2, 64)) == 64 * 64 * 4 and lib.hh_sigma_dofs(hh.Grid(3, 8)) == 8 ** 3 * 12
+    mx = hh.default_options(formulation=hh.HH_FORM_MIXED)
+    assert hh.footprint_bytes(2, 64, mx) - hh.footprint_bytes(2, 64, o) >= 61 * 64 * 64 * 4 * 16
+    assert hh.footprint_bytes(2, 64, mx, nb=2) == 0
+    assert hh.footprint_bytes(2, 64, hh.default_options(formulation=2)) == 0
     # GMRES smoother: max(nu) + 2 more level vectors per level (basis and work vector) and FP64 sums
     gm = hh.footprint_bytes(2, 64, hh.default_options(levels=2, smoother=hh.HH_SMOOTH_GMRES, nu_coarse=5))
     jac = hh.footprint_bytes(2, 64, hh.default_options(levels=2))
@@ -125,3 +132,5 @@ def test_server_validation_on_host(libhh):
     bad = hh.default_options(levels=20)
     assert libhh.hh_server_create(2, 1 << 30, ctypes.byref(bad), ctypes.byref(out)) == -1
     assert libhh.hh_last_error()
+    mixed = hh.default_options(formulation=hh.HH_FORM_MIXED)
+    assert libhh.hh_server_create(2, 1 << 30, ctypes.byref(mixed), ctypes.byref(out)) == -1 and not out.value
