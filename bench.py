@@ -476,6 +476,13 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
     except Exception as e:
         out["gmres_smoother"] = {"failed": str(e)}
 
+    # the mixed formulation (Sec. 2) with the paper's multigrid for it (Sec. 5.3: two W-cycles
+    # per HSS step, GMRES(4) with Jacobi on every level), delta_hat = 2, against the primal one
+    try:
+        out["mixed_formulation"] = measure_mixed(hh, inputs, torch, w)
+    except Exception as e:
+        out["mixed_formulation"] = {"failed": str(e)}
+
     # serving: Poisson arrivals of mixed 2D/3D requests through the solve server
     try:
         out["serving"] = measure_serving(hh, inputs, torch, SERVE_REQUESTS[0])
@@ -518,6 +525,33 @@ def measure_gmres_smoother(hh, inputs, torch, w, n=256, k=20.0):
         res[name] = {"solve_s": t, "outer_its": info.outer_its, "cycles": info.vcycles,
                      "rel_residual": info.rel_residual, "converged": info.rel_residual <= w.tol,
                      "kernel_launches": info.kernel_launches}
+    return res
+
+
+def measure_mixed(hh, inputs, torch, w, n=256, k=20.0):
+    f = torch.from_numpy(inputs.gaussian_source(2, n, tuple(w.centre)[:2], w.sigma)).cuda()
+    mg = dict(cycle_gamma=2, cycles_per_hss=2, nu_pre=4, nu_post=4, nu_coarse=4, smoother=hh.HH_SMOOTH_GMRES)
+    res = {"grid": f"2D {n}^2 Q1 cells, Sommerfeld", "k": k, "delta_hat": 2.0, "tol": w.tol, "levels": 4,
+           "multigrid": "two W-cycles per HSS step, GMRES(4) with Jacobi on every level"}
+    for name, form in (("mixed", hh.HH_FORM_MIXED), ("primal", hh.HH_FORM_PRIMAL)):
+        with hh.Problem(2, n, k, 0.0, 2.0, [hh.SOMMERFELD] * 4,
+                        hh.default_options(max_outer=300, formulation=form, **mg)) as p:
+            bu = p.load_vector(f)
+            if form == hh.HH_FORM_MIXED:
+                # (F_sigma, F_u) = (0, M f / (delta - i k)), delta = 0
+                b = torch.cat([torch.zeros(p.system_size() - bu.numel(), dtype=bu.dtype, device=bu.device),
+                               bu * (1j / k)])
+            else:
+                b = bu
+            p.solve(b, w.tol)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info = p.solve(b, w.tol)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+        res[name] = {"solve_s": t, "outer_its": info.outer_its, "cycles": info.vcycles,
+                     "rel_residual": info.rel_residual, "converged": info.rel_residual <= w.tol,
+                     "unknowns": int(b.numel()), "kernel_launches": info.kernel_launches}
     return res
 
 
