@@ -5,8 +5,9 @@ The GPU orthogonalises by classical Gram-Schmidt twice and solves the small leas
 problem by Givens rotations; the oracle uses modified Gram-Schmidt and a dense least-squares
 solve, so the two agree to rounding: 1e-10 relative in complex128 (a few levels of s <= 5
 iterations, each a well-conditioned 6 x 5 least-squares problem) and 2e-4 in complex64 (FP32
-basis vectors; FP64 sums).  Solves are checked against sparse LU; batches and graph replays
-must equal lone, eager runs bit for bit (fixed-order FP64 sums).
+basis vectors and block sums; the block shares combined in FP64).  Solves are checked against
+sparse LU; batches and graph replays must equal lone, eager runs bit for bit (fixed-order
+sums).
 """
 import numpy as np
 import pytest
