@@ -239,6 +239,27 @@ def test_p5_hss_contraction_every_step(k, n, dh):
     assert ratios[-1] > 0.9 * nu
 
 
+def test_p5_hss_iteration_count_grows_linearly_in_k():
+    """The O(k) growth that Prop. 3.2 implies: the exact-inner-solve HSS steps needed for a
+    fixed H-norm error reduction (1e-3) stay under the bound ln(1e3) / ln(1 / nu_s), and double
+    with k (10 points per wavelength or more, delta_hat = 2)."""
+    counts = {}
+    for k, n in ((8.0, 16), (16.0, 32), (32.0, 64)):
+        g = O.Grid(2, n, (S,) * 4)
+        prob = O.Problem(g, k, 0.0, 2.0, O.Options(levels=1))
+        rng = np.random.default_rng(7)
+        R = (rng.standard_normal(g.N) + 1j * rng.standard_normal(g.N)) * g.free()
+        nu = O.hss_weights(k)[0]
+        bound = math.ceil(math.log(1e3) / math.log(1.0 / nu))
+        errs = _hss_errors(prob, R, bound)
+        hit = np.nonzero(errs <= 1e-3 * errs[0])[0]
+        assert hit.size, (k, errs[-1] / errs[0])
+        counts[k] = int(hit[0])
+        assert counts[k] <= bound
+    for lo, hi in ((8.0, 16.0), (16.0, 32.0)):
+        assert 1.6 <= counts[hi] / counts[lo] <= 2.4, counts
+
+
 # --------------------------------------------------------------------- multigrid
 def _dense_vcycle_operator(prob, l):
     """Approximate inverse B_l of one V-cycle from x = 0, as a dense matrix.
