@@ -196,7 +196,9 @@ class Problem:
     """A Helmholtz problem (scalar k, delta, delta_hat) or a batch of them (sequences of
     equal length): one grid, boundary tags and options, its own k/delta/delta_hat per
     problem.  Vectors of a batch hold the nb problems' level vectors one after another
-    (flat, or shaped (nb, nodes))."""
+    (flat, or shaped (nb, nodes)).  With options.formulation = HH_FORM_MIXED (one problem)
+    the right side and solution of solve / precondition / apply_system hold the sigma
+    entries and then the nodes (system_size() entries); level vectors stay nodal."""
 
     def __init__(self, dim, n, k, delta, delta_hat, bc, options: Options | None = None, stream=None):
         lib = load_library()
