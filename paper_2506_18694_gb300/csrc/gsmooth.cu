@@ -12,6 +12,7 @@
 // shares in a fixed order (every block of that kernel the same way), so the result is the
 // same whatever ran before and however the problems are batched.
 #include "internal.h"
+#include "march2_common.cuh"
 
 namespace hh {
 
@@ -267,7 +268,196 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_update(vec2<T>* __restrict__ 
     }
 }
 
+// ---- the whole smoothing step in one CTA per problem (small 2D levels) ----
+constexpr int kGsCtaThreads = 1024;
+
+// sum over the block of every thread's acc[i] (i < nv) into out[i] (shared), fixed order
+template <typename T>
+__device__ void cta_sums(Cx<T> (&acc)[kGsMaxVec], int nv, Cx<T> (*red)[kGsMaxVec], Cx<T>* out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < kGsMaxVec; ++i) {
+        if (i >= nv) break;
+        Cx<T> v = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
+            v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
+        }
+        if (lane == 0) red[wid][i] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nv) {
+        Cx<T> t = cx<T>(0, 0);
+        for (int w = 0; w < kGsCtaThreads / 32; ++w) t = t + red[w][threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+// grid (nb): problem blockIdx.x.  x (in/out), b, and the basis V_0..V_its (+ work vector
+// V_{its+1}) at Vb + i * ldv, all with problem offsets b * N.
+template <typename T>
+__global__ void __launch_bounds__(kGsCtaThreads) k_gs_cta(const __grid_constant__ MArgs<T> a,
+                                                          const vec2<T>* __restrict__ bvec, vec2<T>* x, int xzero,
+                                                          int its, vec2<T>* Vb, long long ldv) {
+    pdl_entry();
+    const int pb = blockIdx.x;
+    if (a.pc && problem_skipped(a, pb)) return;  // the whole CTA
+    const PCoef<T>& c = a.pc ? a.pc[pb] : a.c0;
+    const int n = a.g.n, nn = a.g.nn;
+    const long long N = a.g.N;
+    const long long off = (long long)pb * N;
+    const vec2<T>* bb = bvec + off;
+    vec2<T>* xb = x + off;
+    auto V = [&](int i) { return Vb + (long long)i * ldv + off; };
+    vec2<T>* W = V(its + 1);
+    __shared__ Cx<T> red[kGsCtaThreads / 32][kGsMaxVec];
+    __shared__ Cx<T> hc[kGsMaxVec];
+    __shared__ Cx<T> R[kGsMaxVec][kGsMaxIts];
+    __shared__ Cx<T> g[kGsMaxVec], sn[kGsMaxIts], ys[kGsMaxIts];
+    __shared__ T csv[kGsMaxIts];
+    __shared__ T scal;
+    auto dirn = [&](int i, int j) {
+        return (i == 0 && a.g.dir[0]) || (i == n && a.g.dir[1]) || (j == 0 && a.g.dir[2]) || (j == n && a.g.dir[3]);
+    };
+    auto val = [&](const vec2<T>* v, int i, int j) {
+        return (i < 0 || i > n || j < 0 || j > n || dirn(i, j)) ? cx<T>(0, 0) : ld<T>(v, (long long)j * nn + i);
+    };
+    // omega D^{-1} (alpha (A v) + beta z) at node (i, j); v == nullptr: v = 0
+    auto dapply = [&](const vec2<T>* v, const vec2<T>* z, Cx<T> alpha, Cx<T> beta, int i, int j) {
+        if (dirn(i, j)) return cx<T>(0, 0);
+        Cx<T> ax = cx<T>(0, 0), dinv_w;
+        const bool fast = i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1;
+        const int tx = i == 0 ? 0 : (i == n ? 2 : 1), ty = j == 0 ? 0 : (j == n ? 2 : 1);
+        if (v) {
+            stencil_node2<T>(c, val(v, i, j - 1), val(v, i, j), val(v, i, j + 1), val(v, i - 1, j - 1),
+                             val(v, i - 1, j), val(v, i - 1, j + 1), val(v, i + 1, j - 1), val(v, i + 1, j),
+                             val(v, i + 1, j + 1), fast, tx, ty, ax, dinv_w);
+        } else {
+            dinv_w = fast ? c.wdinv : c.bdinv[bclass2(tx, ty)];
+        }
+        const Cx<T> zv = z ? ld<T>(z, (long long)j * nn + i) : cx<T>(0, 0);
+        return cmul(dinv_w, fma_c(alpha, ax, cmul(beta, zv)));
+    };
+    const Cx<T> one = cx<T>(1, 0), mone = cx<T>(-1, 0), zero = cx<T>(0, 0);
+    Cx<T> acc[kGsMaxVec];
+    // z0 = omega D^{-1} (b - A x), beta = ||z0||, v_0 = z0 / beta
+    acc[0] = zero;
+    for (long long p = threadIdx.x; p < N; p += kGsCtaThreads) {
+        const int i = (int)(p % nn), j = (int)(p / nn);
+        const Cx<T> w = dapply(xzero ? nullptr : xb, bb, mone, one, i, j);
+        st<T>(W, p, w);
+        acc[0].re += w.re * w.re + w.im * w.im;
+    }
+    cta_sums<T>(acc, 1, red, hc);
+    if (threadIdx.x == 0) {
+        const T beta = sqrt(hc[0].re);
+        scal = beta > T(0) ? T(1) / beta : T(0);
+        g[0] = cx<T>(beta, 0);
+        for (int i = 1; i < kGsMaxVec; ++i) g[i] = zero;
+    }
+    __syncthreads();
+    for (long long p = threadIdx.x; p < N; p += kGsCtaThreads) {
+        const Cx<T> w = ld<T>(W, p);
+        st<T>(V(0), p, cx<T>(w.re * scal, w.im * scal));
+    }
+    __syncthreads();
+    for (int j = 0; j < its; ++j) {
+        const vec2<T>* vj = V(j);
+        for (long long p = threadIdx.x; p < N; p += kGsCtaThreads) {
+            const int i = (int)(p % nn), jj = (int)(p / nn);
+            st<T>(W, p, dapply(vj, nullptr, one, zero, i, jj));
+        }
+        __syncthreads();
+        // classical Gram-Schmidt, twice
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int i = 0; i <= j; ++i) acc[i] = zero;
+            for (long long p = threadIdx.x; p < N; p += kGsCtaThreads) {
+                const Cx<T> w = ld<T>(W, p);
+                for (int i = 0; i <= j; ++i) {
+                    const Cx<T> v = ld<T>(V(i), p);
+                    acc[i].re += v.re * w.re + v.im * w.im;
+                    acc[i].im += v.re * w.im - v.im * w.re;
+                }
+            }
+            cta_sums<T>(acc, j + 1, red, hc);
+            if ((int)threadIdx.x <= j) R[threadIdx.x][j] = pass ? R[threadIdx.x][j] + hc[threadIdx.x] : hc[threadIdx.x];
+            acc[0] = zero;
+            for (long long p = threadIdx.x; p < N; p += kGsCtaThreads) {
+                Cx<T> w = ld<T>(W, p);
+                for (int i = 0; i <= j; ++i) w = fma_c(cx<T>(-hc[i].re, -hc[i].im), ld<T>(V(i), p), w);
+                st<T>(W, p, w);
+                acc[0].re += w.re * w.re + w.im * w.im;
+            }
+            __syncthreads();
+        }
+        cta_sums<T>(acc, 1, red, hc);  // ||w||^2 after the second pass
+        if (threadIdx.x == 0) {
+            const T h = sqrt(hc[0].re);
+            scal = h > T(0) ? T(1) / h : T(0);
+            // previous rotations on column j, then the one that zeroes h
+            for (int i = 0; i < j; ++i) {
+                const Cx<T> p0 = R[i][j], q0 = R[i + 1][j];
+                const T cc = csv[i];
+                const Cx<T> s0 = sn[i];
+                R[i][j] = cx<T>(cc * p0.re + (s0.re * q0.re - s0.im * q0.im), cc * p0.im + (s0.re * q0.im + s0.im * q0.re));
+                R[i + 1][j] = cx<T>(-(s0.re * p0.re + s0.im * p0.im) + cc * q0.re, -(s0.re * p0.im - s0.im * p0.re) + cc * q0.im);
+            }
+            const Cx<T> av = R[j][j];
+            const T na = sqrt(av.re * av.re + av.im * av.im), den = sqrt(na * na + h * h);
+            T cc = T(1);
+            Cx<T> s0 = zero;
+            if (den > T(0)) {
+                if (na == T(0)) {
+                    cc = T(0);
+                    s0 = one;
+                } else {
+                    cc = na / den;
+                    s0 = cx<T>(av.re / na * h / den, av.im / na * h / den);
+                }
+            }
+            csv[j] = cc;
+            sn[j] = s0;
+            R[j][j] = cx<T>(cc * av.re + s0.re * h, cc * av.im + s0.im * h);
+            const Cx<T> g0 = g[j];
+            g[j] = cx<T>(cc * g0.re, cc * g0.im);
+            g[j + 1] = cx<T>(-(s0.re * g0.re + s0.im * g0.im), -(s0.re * g0.im - s0.im * g0.re));
+        }
+        __syncthreads();
+        vec2<T>* vn = V(j + 1);
+        for (long long p = threadIdx.x; p < N; p += kGsCtaThreads) {
+            const Cx<T> w = ld<T>(W, p);
+            st<T>(vn, p, cx<T>(w.re * scal, w.im * scal));
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int j = its - 1; j >= 0; --j) {
+            Cx<T> t = g[j];
+            for (int k = j + 1; k < its; ++k) t = t - cmul(R[j][k], ys[k]);
+            const Cx<T> d = R[j][j];
+            const T dd = d.re * d.re + d.im * d.im;
+            ys[j] = dd > T(0) ? cx<T>((t.re * d.re + t.im * d.im) / dd, (t.im * d.re - t.re * d.im) / dd) : zero;
+        }
+    }
+    __syncthreads();
+    for (long long p = threadIdx.x; p < N; p += kGsCtaThreads) {
+        Cx<T> u = xzero ? zero : ld<T>(xb, p);
+        for (int i = 0; i < its; ++i) u = fma_c(ys[i], ld<T>(V(i), p), u);
+        st<T>(xb, p, u);
+    }
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_gs_cta(const MArgs<T>& a, const vec2<T>* b, vec2<T>* x, int xzero, int its, vec2<T>* V,
+                          long long ldv, cudaStream_t s) {
+    if (a.g.dim != 2 || its < 1 || its > kGsMaxIts || a.g.N > kGsCtaNodes) return cudaErrorInvalidValue;
+    if (!a.pc && a.nb != 1) return cudaErrorInvalidValue;
+    return klaunch(k_gs_cta<T>, dim3((unsigned)a.nb), dim3(kGsCtaThreads), 0, s, 1, a, b, x, xzero, its, V, ldv);
+}
 
 template <typename T>
 cudaError_t launch_gs_dot(const vec2<T>* V, long long ldv, int nv, const vec2<T>* w, long long N, double2* part,
@@ -312,6 +502,10 @@ cudaError_t launch_gs_update(vec2<T>* x, const vec2<T>* V, long long ld, int m, 
                                             const Batch&, cudaStream_t);                                              \
     template cudaError_t launch_gs_update<T>(vec2<T>*, const vec2<T>*, long long, int, long long, const double2*,     \
                                              int, const Batch&, cudaStream_t);
+template cudaError_t launch_gs_cta<float>(const MArgs<float>&, const vec2<float>*, vec2<float>*, int, int,
+                                          vec2<float>*, long long, cudaStream_t);
+template cudaError_t launch_gs_cta<double>(const MArgs<double>&, const vec2<double>*, vec2<double>*, int, int,
+                                           vec2<double>*, long long, cudaStream_t);
 HH_GS_INST(float)
 HH_GS_INST(double)
 #undef HH_GS_INST

@@ -254,6 +254,13 @@ inline int gs_blocks(long long N) {
 template <typename T>
 cudaError_t launch_gs_dot(const vec2<T>* V, long long ld, int nv, const vec2<T>* w, long long N, double2* part,
                           const Batch& bt, cudaStream_t s);
+// A whole smoothing step of `its` iterations in one CTA per problem, for 2D levels of at most
+// kGsCtaNodes nodes: x (in/out; xzero: from 0) on b, basis and work vector at V + i * ldv
+// (i <= its + 1), the operator and batch from a (margs of R_AL).
+constexpr long long kGsCtaNodes = 4225;
+template <typename T>
+cudaError_t launch_gs_cta(const MArgs<T>& a, const vec2<T>* b, vec2<T>* x, int xzero, int its, vec2<T>* V,
+                          long long ldv, cudaStream_t s);
 // Per-problem least-squares state (double2 entries, kGsState per problem): the Hessenberg
 // matrix H[i][j] at i * kGsMaxIts + j (rotated in place into R as columns complete), the
 // Givens rotations (c_j real at kGsCos + j, s_j at kGsSin + j) and the rotated right side g.

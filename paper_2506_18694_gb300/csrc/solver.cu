@@ -634,6 +634,12 @@ struct MG {
         }
         const long long ld = N * p->nb;  // basis vector stride
         V2* Vb = (V2*)H->gv[l];
+        if (d2() && N <= hh::kGsCtaNodes) {
+            // small 2D level: the whole step in one CTA per problem (one launch instead of 6 its + 4)
+            hh::MArgs<T> a = margs(l, R_AL);
+            HH_LAUNCH(hh::launch_gs_cta<T>(a, b, x, xzero ? 1 : 0, its, Vb, ld, s));
+            return HH_OK;
+        }
         V2* W = Vb + (long long)(its + 1) * ld;  // after the basis
         const int nblk = hh::gs_blocks(N);
         double2* part = (double2*)H->gsm[l];
