@@ -78,11 +78,11 @@ def test_hss_step_elimination_equals_block_solve(dim, n, bc):
     assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(a)
 
 
-@pytest.mark.parametrize("k,dh", [(6.0, 1.0), (12.0, 0.3)])
-def test_mixed_hss_contracts_in_h_norm(k, dh):
+@pytest.mark.parametrize("dim,k,dh", [(2, 6.0, 1.0), (2, 12.0, 0.3), (3, 5.0, 0.5)])
+def test_mixed_hss_contracts_in_h_norm(dim, k, dh):
     """Prop. 3.6: for the shifted mixed system (delta = dh > 0) each HSS step contracts the
     error by (k - 1)/(k + 1) or better in the H_mixed norm."""
-    g = O.Grid(2, 8, (S, S, S, D))
+    g = O.Grid(dim, 8 if dim == 2 else 4, (S, S, S, D) if dim == 2 else (S, S, S, S, D, S))
     p = X.MixedProblem(g, k, dh, dh)
     F = p.rhs(inputs.random_complex(g.N, 60) * g.free())
     Ustar = p.lu_solve(F)
