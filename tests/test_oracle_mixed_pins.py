@@ -115,3 +115,23 @@ def test_mixed_fgmres_matches_primal_lu():
         _, u = p.split(U)
         assert rel <= tol and its <= 60
         assert np.linalg.norm(u - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_mixed_outer_counts_follow_primal():
+    """After the elimination of sigma the mixed preconditioner solves a primal-type shifted
+    problem (Sec. 3.2), so with the same multigrid (4 levels, V(2,2)-Jacobi) the outer FGMRES
+    counts of the two formulations stay within a few iterations of each other, both
+    k-independent at delta_hat = 2."""
+    g = O.Grid(2, 32, (S,) * 4)
+    f = O.load_vector_nodal(g, inputs.gaussian_source(2, 32, (0.4, 0.4), 0.05))
+    counts = {}
+    for k in (6.0, 12.0):
+        prim = O.Problem(g, k, 0.0, 2.0, O.Options(levels=4))
+        _, its_p, rel_p, _ = O.solve(prim, f, 1e-8)
+        fn = spla.spsolve(prim.mats[0][1].tocsc(), f)
+        xp = X.MixedProblem(g, k, 0.0, 2.0, O.Options(levels=4))
+        _, its_m, rel_m, _ = xp.solve(xp.rhs(fn), 1e-8)
+        assert rel_p <= 1e-8 and rel_m <= 1e-8
+        assert abs(its_m - its_p) <= 3, (k, its_m, its_p)
+        counts[k] = its_m
+    assert counts[12.0] <= counts[6.0] + 3
