@@ -257,6 +257,12 @@ HH_API hh_status hh_solve_host_nodal(hh_problem* p, const void* f_host, double t
  * library (the paper has none): it lets a serving loop reuse a problem's hierarchy and
  * Krylov basis for the next request on the same grid.
  */
+/* Cap, for every problem created or grown afterwards in this process, on the device bytes one
+ * problem may hold (0 = no cap, the default).  An allocation past it fails with HH_ERR_OOM
+ * before any device call, as a real out-of-memory would (creation then returns NULL, a
+ * solve reports the status).  For failure injection and for callers sharing a device. */
+HH_API void hh_set_allocation_limit(size_t bytes);
+
 /* sigma entries of a mixed problem on `grid`: n^dim cells x dim components x 2^(dim-1) */
 HH_API long long hh_sigma_dofs(const hh_grid* grid);
 /* entries of one problem's right side / solution for hh_solve: nodes (primal) or sigma

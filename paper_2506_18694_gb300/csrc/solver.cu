@@ -15,6 +15,7 @@
 #include <tuple>
 #include <chrono>
 #include <cmath>
+#include <atomic>
 #include <complex>
 #include <cstdio>
 #include <cstring>
@@ -171,7 +172,17 @@ struct hh_problem {
 
 namespace {
 
+// process-wide cap on the device bytes one problem may hold (0: none), for failure injection
+// and for callers that share the device
+std::atomic<size_t> g_alloc_limit{0};
+
 hh_status dmalloc(hh_problem* p, void** ptr, size_t bytes) {
+    const size_t cap = g_alloc_limit.load();
+    if (cap && p->bytes + bytes > cap) {
+        *ptr = nullptr;
+        return fail(HH_ERR_OOM, "allocation of " + std::to_string(bytes) + " bytes exceeds the limit of " +
+                                    std::to_string(cap) + " bytes per problem");
+    }
     cudaError_t e = cudaMalloc(ptr, bytes);
     if (e != cudaSuccess) {
         *ptr = nullptr;
@@ -1815,6 +1826,8 @@ long long hh_sigma_dofs(const hh_grid* grid) {
 }
 
 long long hh_vector_length(const hh_problem* p) { return p ? p->N : 0; }
+
+void hh_set_allocation_limit(size_t bytes) { g_alloc_limit.store(bytes); }
 
 hh_status hh_apply_system(hh_problem* p, const void* x, void* y) {
     if (!p || !x || !y) return fail(HH_ERR_INVALID, "null argument");

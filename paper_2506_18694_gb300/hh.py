@@ -31,7 +31,7 @@ EXPORTED = (
     "hh_prolong_correct", "hh_vcycle", "hh_hss_rhs", "hh_precondition", "hh_load_vector", "hh_dot",
     "hh_multidot_noalloc", "hh_server_create", "hh_server_submit", "hh_server_wait", "hh_server_get_stats",
     "hh_server_destroy", "hh_status_string", "hh_last_error", "hh_sigma_dofs", "hh_vector_length",
-    "hh_apply_system",
+    "hh_apply_system", "hh_set_allocation_limit",
 )
 
 
@@ -110,6 +110,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "hh_sigma_dofs": (ctypes.c_longlong, [ctypes.POINTER(Grid)]),
         "hh_vector_length": (ctypes.c_longlong, [P]),
         "hh_apply_system": (I, [P, P, P]),
+        "hh_set_allocation_limit": (V, [ctypes.c_size_t]),
         "hh_autotune": (I, [P, I, ctypes.POINTER(ctypes.c_int)]),
         "hh_set_params": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
         "hh_prepare": (I, [P]),

@@ -279,6 +279,26 @@ def test_solve_zero_rhs_and_initial_guess(libhh):
         assert i2.outer_its == 0 and i2.rel_residual <= 1e-8
 
 
+def test_allocation_limit_injects_oom(libhh):
+    """A per-problem device cap fails creation with HH_ERR_OOM before any allocation (no
+    device fault, nothing leaked), and lifting it lets the same problem be created and solved."""
+    lib = hh.load_library()
+    opts = hh.default_options(levels=3)
+    need = hh.footprint_bytes(2, 16, opts)
+    try:
+        lib.hh_set_allocation_limit(need // 2)
+        with pytest.raises(hh.HHError) as e:
+            hh.Problem(2, 16, 5.0, 0.0, 2.0, (S,) * 4, opts)
+        assert e.value.status == -2 and "limit" in str(e.value)
+        lib.hh_set_allocation_limit(need)
+        with hh.Problem(2, 16, 5.0, 0.0, 2.0, (S,) * 4, opts) as p:
+            b = p.load_vector(to_dev(inputs.gaussian_source(2, 16, (0.5, 0.5)), hh.HH_C128))
+            _, info = p.solve(b, 1e-8)
+            assert info.rel_residual <= 1e-8 and info.device_bytes <= need
+    finally:
+        lib.hh_set_allocation_limit(0)
+
+
 def test_nonfinite_rhs_reported(libhh):
     with hh.Problem(2, 16, 5.0, 0.0, 2.0, (S,) * 4, hh.default_options(levels=3)) as p:
         b = p.zeros()
