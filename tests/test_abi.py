@@ -134,3 +134,32 @@ def test_server_validation_on_host(libhh):
     assert libhh.hh_last_error()
     mixed = hh.default_options(formulation=hh.HH_FORM_MIXED)
     assert libhh.hh_server_create(2, 1 << 30, ctypes.byref(mixed), ctypes.byref(out)) == -1 and not out.value
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the ABI structs have the C compiler's size and field offsets
+    (a field added, dropped or reordered on one side only would corrupt every call)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"hh_grid": hh.Grid, "hh_options": hh.Options, "hh_info": hh.Info, "hh_request": hh.Request,
+               "hh_server_stats": hh.ServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hh.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
