@@ -646,3 +646,20 @@ def test_gmres_cycle_two_grid_exact_coarse_and_homogeneous():
     c = 0.7 - 2.1j
     x = prob2.vcycle(0, b)
     assert np.linalg.norm(prob2.vcycle(0, c * b) - c * x) <= 1e-12 * abs(c) * np.linalg.norm(x)
+
+
+def test_gmres_smoother_keeps_outer_counts_flat_in_k():
+    """Sec. 5.3's multigrid (W-cycles, GMRES(5) with Jacobi on every level) at delta_hat = 2
+    keeps the outer FGMRES counts nearly k-independent (10+ points per wavelength), while
+    W(2,2) with damped Jacobi lets them grow: the reason the paper smooths with GMRES."""
+    gm, jac = {}, {}
+    for k, n in ((4.0, 16), (8.0, 32), (16.0, 64)):
+        g = O.Grid(2, n, (S,) * 4)
+        f = O.load_vector_nodal(g, inputs.gaussian_source(2, n, (0.4, 0.4), 0.05))
+        for name, o in (("gmres", O.Options(levels=3, nu_pre=5, nu_post=5, nu_coarse=5, gamma=2, smoother="gmres")),
+                        ("jacobi", O.Options(levels=3, gamma=2))):
+            _, its, rel, _ = O.solve(O.Problem(g, k, 0.0, 2.0, o), f, 1e-8)
+            assert rel <= 1e-8
+            (gm if name == "gmres" else jac)[k] = its
+    assert max(gm.values()) - min(gm.values()) <= 5, gm
+    assert gm[16.0] < jac[16.0] and jac[16.0] - jac[4.0] > gm[16.0] - gm[4.0], (gm, jac)
