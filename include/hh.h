@@ -257,6 +257,8 @@ HH_API hh_status hh_solve_host_nodal(hh_problem* p, const void* f_host, double t
  * library (the paper has none): it lets a serving loop reuse a problem's hierarchy and
  * Krylov basis for the next request on the same grid.
  */
+HH_API hh_status hh_set_params(hh_problem* p, const double* k, const double* delta, const double* delta_hat);
+
 /* Cap, for every problem created or grown afterwards in this process, on the device bytes one
  * problem may hold (0 = no cap, the default).  An allocation past it fails with HH_ERR_OOM
  * before any device call, as a real out-of-memory would (creation then returns NULL, a
@@ -271,8 +273,6 @@ HH_API long long hh_vector_length(const hh_problem* p);
 /* y = the system operator x in FP64 (B_delta, or the mixed A_delta of Sec. 2); x, y: device
  * complex128 vectors of hh_vector_length(p) entries per problem */
 HH_API hh_status hh_apply_system(hh_problem* p, const void* x, void* y);
-
-HH_API hh_status hh_set_params(hh_problem* p, const double* k, const double* delta, const double* delta_hat);
 
 /*
  * Capture the preconditioner graph (and allocate the multigrid buffers) now instead of
@@ -337,8 +337,11 @@ HH_API hh_status hh_dot(hh_problem* p, const void* x, const void* y, double* out
  * Returns HH_ERR_INVALID (with a message in hh_last_error) for nvec outside 1..64, n < 0,
  * ld < n or a null pointer, HH_ERR_CUDA if a launch fails.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls share the one array, so
- * calls that overlap on the GPU (different streams, no ordering between them) race.
+ * make that first call before any stream capture.  The address is kept for the life of
+ * the process: after a cudaDeviceReset of a device (which also invalidates every
+ * hh_problem on it) the library must not be used on that device again.  All calls share
+ * the one array, so calls that overlap on the GPU (different streams, no ordering between
+ * them) race.
  */
 HH_API hh_status hh_multidot_noalloc(const void* V, long long ld, int nvec, const void* w, long long n,
                                      void* out, void* cuda_stream);

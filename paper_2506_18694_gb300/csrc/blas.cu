@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(256) k_multi_axpy(double2* __restrict__ w, con
 
 static inline unsigned ew_blocks(long long N) {
     long long b = (N + 255) / 256;
-    if (b > 152 * 8) b = 152 * 8;
+    const long long cap = 8LL * num_sms();
+    if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (unsigned)b;
 }

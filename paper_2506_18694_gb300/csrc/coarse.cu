@@ -369,7 +369,7 @@ cudaError_t prepare_coarse() {
 template <typename T>
 static int batch_cluster_size(const GridDesc& g, int nb) {
     int cs = coarse_cluster_size();
-    while (cs > 1 && (long long)nb * cs > 2LL * 152 && coarse_cluster_ok<T>(g, cs / 2)) cs /= 2;
+    while (cs > 1 && (long long)nb * cs > 2LL * num_sms() && coarse_cluster_ok<T>(g, cs / 2)) cs /= 2;
     return cs;
 }
 

@@ -10,6 +10,10 @@ namespace hh {
 // Message returned by hh_last_error() for the calling thread.
 void set_last_error(const char* msg);
 
+// Streaming multiprocessors of the current device (queried once per device; the launch
+// heuristics size persistent grids and occupancy targets by it).
+int num_sms();
+
 // Kernels launched by this thread through the launchers below (graph captures included).
 extern thread_local long long g_kernel_launches;
 // 1: launch with programmatic stream serialization (overlaps a kernel's launch with the

@@ -349,7 +349,7 @@ static cudaError_t gof(MArgs<T> a, cudaStream_t s) {
     a.ih = T(1.0 / a.g.h);
     if (a.pc && !a.pc2) return cudaErrorInvalidValue;
     const int strips = (a.g.nn + 27) / 28;
-    int rows = ((long long)strips * ((a.g.nn + 3) / 4) * a.nb >= 152LL * 24) ? 4 : 2;
+    int rows = ((long long)strips * ((a.g.nn + 3) / 4) * a.nb >= 24LL * num_sms()) ? 4 : 2;
     if (a.tile_rows == 2 || a.tile_rows == 4) rows = a.tile_rows;
     const int chunks = (a.g.nn + rows - 1) / rows;
     const dim3 grd((unsigned)strips, (unsigned)((chunks + 3) / 4), (unsigned)a.nb);
@@ -511,7 +511,7 @@ static cudaError_t run2b(const MArgs<T>& a, int strips, int chunks, cudaStream_t
                 per_sm = 1;
             }
         }
-        const long long resident_blocks = 152LL * per_sm;
+        const long long resident_blocks = (long long)num_sms() * per_sm;
         // automatic: persistent once there are several tiles per resident warp
         const bool persist =
             a.tile_form == 2 || (a.tile_form == 0 && MODE != M_RESID_RESTRICT && tiles >= 16 * resident_blocks);
@@ -538,7 +538,7 @@ template <typename T, int MODE>
 static cudaError_t go2(MArgs<T> a, cudaStream_t s) {
     a.h = T(a.g.h);
     a.ih = T(1.0 / a.g.h);
-    const long long want = 152LL * 24;
+    const long long want = 24LL * num_sms();
     if constexpr (MODE == M_RESID_RESTRICT) {
         const int nnc = a.g.n / 2 + 1;
         const int strips = (nnc + 13) / 14;

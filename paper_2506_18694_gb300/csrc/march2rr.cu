@@ -188,7 +188,7 @@ static cudaError_t gorr(MArgs<T> a, cudaStream_t s) {
     if (a.pc && !a.pc2) return cudaErrorInvalidValue;
     const int nnc = a.g.n / 2 + 1;
     const int strips = (a.g.nn + G1::S - 1) / G1::S;
-    int cr = ((long long)strips * ((nnc + 1) / 2) * a.nb >= 152LL * 24) ? 2 : 1;
+    int cr = ((long long)strips * ((nnc + 1) / 2) * a.nb >= 24LL * num_sms()) ? 2 : 1;
     if (a.tile_rows == 1 || a.tile_rows == 2) cr = a.tile_rows;
     const int chunks = (nnc + cr - 1) / cr;
     const dim3 grd((unsigned)strips, (unsigned)((chunks + 3) / 4), (unsigned)a.nb);

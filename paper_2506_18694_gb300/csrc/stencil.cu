@@ -2,12 +2,32 @@
 // restriction (3D and the building-block API), bi/trilinear prolongation, vector add and
 // copy, precision casts, masked copies.  Problem b of a batch works at offset b * bs (its
 // level vector) or b * bsc (its coarse vector); blockIdx.z (or y) selects the problem.
+#include <atomic>
+
 #include "internal.h"
 
 namespace hh {
 
 thread_local long long g_kernel_launches = 0;
 thread_local int g_use_pdl = 1;
+
+int num_sms() {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return 1;
+    }
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+        cudaGetLastError();
+        v = 1;
+    }
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
 
 __device__ __forceinline__ bool batch_skipped(const Batch& bt, int b) {
     if (bt.active && !bt.active[b]) return true;
@@ -127,7 +147,8 @@ cudaError_t launch_prolong(const GridDesc& gf, const vec2<T>* ec, vec2<T>* x, co
 // ---------------------------------------------------------------- elementwise
 static inline unsigned ew_blocks(long long N) {
     long long b = (N + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    const long long cap = 16LL * num_sms();
+    if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (unsigned)b;
 }

@@ -13,13 +13,12 @@ import pytest
 import torch
 
 from oracle import hh_oracle as O
+from nodewise import rel
 from paper_2506_18694_gb300 import hh, inputs
 
 pytestmark = pytest.mark.gpu
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 @pytest.fixture(scope="module")

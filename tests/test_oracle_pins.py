@@ -306,6 +306,31 @@ def test_vcycle_matches_error_propagation_formula(bc, gamma):
     assert np.abs(prob.vcycle(0, b) - B @ b).max() <= 1e-11 * np.abs(B @ b).max()
 
 
+@pytest.mark.parametrize("cycles", [1, 2, 3])
+@pytest.mark.parametrize("bc", [(S, S, S, S), (D, S, S, D)])
+def test_mg_solve_cycles_match_error_propagation_power(bc, cycles):
+    """cycles_per_hss = c cycles per inexact A_L solve of the HSS step (Def. 4.1), each on the
+    residual the previous ones leave, are the stationary iteration x <- x + B (b - A x) from 0:
+    the error after c cycles is (I - B A)^c e_0, so x = (I - (I - B A)^c) A^{-1} b on the free
+    nodes, with B the dense single-cycle operator above."""
+    g = O.Grid(2, 8, bc)
+    prob = O.Problem(g, 5.0, 0.0, 2.0,
+                     O.Options(levels=3, nu_pre=1, nu_post=2, nu_coarse=3, cycles_per_hss=cycles))
+    B = _dense_vcycle_operator(prob, 0)
+    A = prob.AL[0].toarray()
+    f = prob.free[0]
+    rng = np.random.default_rng(11 + cycles)
+    b = (rng.standard_normal(g.N) + 1j * rng.standard_normal(g.N)) * g.free()
+    x_exact = np.zeros(g.N, dtype=complex)
+    x_exact[f] = np.linalg.solve(A[np.ix_(f, f)], b[f])
+    E = np.eye(g.N) - B @ A
+    want = x_exact - np.linalg.matrix_power(E, cycles) @ x_exact
+    got = prob.mg_solve(b)
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+    assert np.all(got[~f] == 0)
+    assert prob.counters["vcycles"] == cycles
+
+
 def test_vcycle_contracts_shifted_operator():
     """The V-cycle is a convergent approximate inverse of A_L at the default settings."""
     g = O.Grid(2, 64, (S,) * 4)
