@@ -118,37 +118,47 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle leg
-def oracle_vcycle_rate(w, seconds=12.0, max_cycles=200):
-    """Oracle (FP64, scipy CSR, single thread) HSS iterations on the workload: DoF*V-cycles/s."""
+def host_cores():
+    """Cores this process may run on (its affinity mask), and the machine's count."""
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count() or 1
+    return usable, os.cpu_count() or usable
+
+
+def oracle_problem(w):
+    """The FP64 oracle's matrices for workload w (Python assembly) and its C OpenMP runner."""
     from oracle import hh_oracle as O
+    from oracle import hss_omp as C
     from paper_2506_18694_gb300 import inputs
 
     g = O.Grid(w.dim, w.n, w.bc)
     prob = O.Problem(g, w.k, w.delta, w.delta_hat, O.Options())
     f = inputs.gaussian_source(w.dim, w.n, w.centre, w.sigma)
-    r = O.load_vector_nodal(g, f)
-    u = np.zeros_like(r)
-    t0 = time.perf_counter()
-    cycles = 0
-    while cycles < max_cycles:
-        u = prob.mg_solve(prob.hss_rhs(u, r))
-        cycles += 1
-        if time.perf_counter() - t0 >= seconds:
-            break
-    dt = time.perf_counter() - t0
-    return g.N * cycles / dt, cycles, dt
+    r = prob.mats[0][1] @ f  # b = M f
+    return g, C.COracle(prob), r, C
 
 
-def cpu_threads():
+def oracle_vcycle_rate(w, seconds=8.0):
+    """The oracle's HSS steps (one V-cycle each, FP64 CSR, OpenMP over rows) on the workload,
+    on all usable host cores and on one core: DoF*V-cycles/s for each."""
+    g, c, r, C = oracle_problem(w)
+    usable, machine = host_cores()
+    saved = C.COracle.threads()
     try:
-        import threadpoolctl  # noqa: F401
-        from threadpoolctl import threadpool_info
-
-        nt = [i.get("num_threads", 1) for i in threadpool_info()]
-        # scipy CSR products and numpy elementwise work run on one thread
-        return 1 if nt else 1
-    except Exception:
-        return 1
+        C.COracle.threads(usable)
+        steps_all, dt_all = c.time_steps(r, seconds)
+        C.COracle.threads(1)
+        steps_one, dt_one = c.time_steps(r, seconds)
+    finally:
+        C.COracle.threads(saved)
+    return {"value": g.N * steps_all / dt_all, "unit": UNIT, "cores": usable, "machine_cores": machine,
+            "kind": "oracle",
+            "sample": f"{steps_all} HSS steps (one V(2,2) cycle each) of the {w.name} workload in {dt_all:.1f} s "
+                      f"on {usable} threads; FP64 CSR, plain C with OpenMP over rows (oracle/hss_omp.c)",
+            "one_core": {"value": g.N * steps_one / dt_one, "cores": 1,
+                         "sample": f"{steps_one} HSS steps in {dt_one:.1f} s on 1 thread"}}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -159,37 +169,26 @@ def run_reference(args):
     from paper_2506_18694_gb300 import inputs
 
     w = inputs.workload(args.workload, args.delta_hat)
-    from oracle import hh_oracle as O
-
-    g = O.Grid(w.dim, w.n, w.bc)
-    prob = O.Problem(g, w.k, w.delta, w.delta_hat, O.Options())
-    f = inputs.gaussian_source(w.dim, w.n, w.centre, w.sigma)
-    r = O.load_vector_nodal(g, f)
-    per_step_cycles = 2  # one bounded sample per step: two HSS iterations (two V-cycles)
-
-    def step():
-        u = np.zeros_like(r)
-        for _ in range(per_step_cycles):
-            u = prob.mg_solve(prob.hss_rhs(u, r))
-        return u
-
+    g, c, r, C = oracle_problem(w)
+    usable, machine = host_cores()
+    C.COracle.threads(usable)
+    per_step = 4 if w.dim == 2 else 1  # one bounded sample per step: HSS steps (V-cycles)
     for _ in range(args.warmup):
-        step()
+        c.time_steps(r, 0.0, per_step)
     times = []
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        step()
-        times.append(time.perf_counter() - t0)
+        _, dt = c.time_steps(r, 0.0, per_step)
+        times.append(dt)
     tot = sum(times)
-    value = g.N * per_step_cycles * args.steps / tot
+    value = g.N * per_step * args.steps / tot
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": w.name, "delta_hat": w.delta_hat, "nodes": g.N},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                         "sample": f"{per_step_cycles} HSS iterations (V-cycles) per step of the "
-                                   f"{w.name} workload, FP64 scipy CSR"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": usable, "machine_cores": machine, "kind": "oracle",
+                         "sample": f"{per_step} HSS steps (V-cycles) per step of the {w.name} workload, FP64 CSR, "
+                                   f"plain C with OpenMP over rows on {usable} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -498,12 +497,9 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
     except Exception as e:  # report, do not hide the other numbers
         out["batch64"] = {"failed": str(e)}
 
-    # FP64 CPU oracle on a bounded sample of the same workload
+    # FP64 CPU oracle on a bounded sample of the same workload, all cores and one core
     try:
-        v, cycles, dt = oracle_vcycle_rate(w)
-        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                               "sample": f"{cycles} HSS iterations (one V-cycle each) of the {w.name} "
-                                         f"workload in {dt:.1f} s, FP64 scipy CSR"}
+        out["cpu_baseline"] = oracle_vcycle_rate(w)
     except Exception as e:  # the CPU leg must not hide the GPU numbers
         out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle", "sample": f"failed: {e}"}
     return out

@@ -66,7 +66,7 @@ typedef enum {
     HH_ERR_OOM = -2,        /* device allocation failed                               */
     HH_ERR_CUDA = -3,       /* a CUDA runtime call failed                             */
     HH_ERR_NONFINITE = -4,  /* NaN or Inf met in the right side or the iteration      */
-    HH_ERR_TIMEOUT = -5     /* reserved for bounded device waits                      */
+    HH_ERR_TIMEOUT = -5     /* a bounded device wait (grid-wide barrier) ran out      */
 } hh_status;
 
 /* Boundary tags of Sec. 1: Gamma (radiation condition) and dOmega_0 (u = 0). */
@@ -150,6 +150,15 @@ typedef struct {
                          /* problem hold hh_sigma_dofs(grid) sigma entries ((cell x fastest,   */
                          /* component a, vertex s of the other axes) order) and then the       */
                          /* nodes; one problem per object (no batches), no solve server        */
+    int persistent;      /* 2D, V(2,2) scaled-Jacobi cycles, one per HSS step: 1: on levels of */
+                         /* at most 600000 nodes (all problems of a batch together) the whole  */
+                         /* HSS loop of a preconditioner application runs as ONE cooperative  */
+                         /* kernel whose CTAs meet at grid-wide barriers between the passes of */
+                         /* each cycle; 2: at every size; 0 (default): one kernel per pass,    */
+                         /* replayed from a CUDA graph.  Same result bit for bit               */
+    long long sync_spin_limit; /* polls a grid-wide barrier wait may take before the kernel     */
+                         /* gives up and the call returns HH_ERR_TIMEOUT; 0 = 4194304 (about   */
+                         /* a second or more); tiny values make the waits run out on purpose   */
 } hh_options;
 
 typedef struct {
@@ -167,7 +176,7 @@ typedef struct hh_problem hh_problem;
 /* Defaults: theta 1, 4 levels, V(2,2), 8 coarse sweeps, omega automatic, restart 30,
  * max_outer 1000, complex FP32 V-cycles, graphs and programmatic launch on,
  * coarse_cluster_nodes 100000, tile shapes from the grid size (no autotuning), fused
- * two-sweep kernels. */
+ * two-sweep kernels, one kernel per pass (no persistent HSS loop). */
 HH_API void hh_options_default(hh_options* opts);
 
 /* Device bytes a problem with this grid and these options allocates for its solves

@@ -12,6 +12,7 @@
 #include <cooperative_groups.h>
 
 #include "internal.h"
+#include "march2_common.cuh"
 #include "node.cuh"
 
 namespace cg = cooperative_groups;
@@ -180,29 +181,6 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem(const __grid_co
 // Inner nodes use the interior weights and side nodes the weights of their boundary class,
 // exactly as the 2D stencil kernels do, so the result equals nsweeps separate sweeps bit
 // for bit.  Slabs of one row (tiny grids) exchange after every sweep.
-template <typename T>
-__device__ __forceinline__ Cx<T> coarse_update2(const PCoef<T>& c, const vec2<T>* __restrict__ xc, int pi, int W,
-                                               int kind, Cx<T> bq) {
-    const bool inner = kind == 8;
-    const Cx<T> dinv = inner ? c.wdinv : c.bdinv[kind];
-    const Cx<T> f0 = ld<T>(xc, pi), fm = ld<T>(xc, pi - W), fp = ld<T>(xc, pi + W);
-    const Cx<T> l0 = ld<T>(xc, pi - 1), r0v = ld<T>(xc, pi + 1);
-    const Cx<T> lm = ld<T>(xc, pi - W - 1), rm = ld<T>(xc, pi - W + 1);
-    const Cx<T> lp = ld<T>(xc, pi + W - 1), rp = ld<T>(xc, pi + W + 1);
-    Cx<T> ax;
-    if (inner) {
-        const Cx<T> edge = (l0 + r0v) + (fm + fp);
-        const Cx<T> diag = (lm + rm) + (lp + rp);
-        ax = fma_c(c.iw[2], diag, fma_c(c.iw[1], edge, cmul(c.iw[0], f0)));
-    } else {
-        const Cx<T> hx = l0 + r0v;
-        const Cx<T> vy = fm + fp;
-        const Cx<T> dg = (lm + rm) + (lp + rp);
-        ax = fma_c(c.bw[kind][3], dg, fma_c(c.bw[kind][2], vy, fma_c(c.bw[kind][1], hx, cmul(c.bw[kind][0], f0))));
-    }
-    return fma_c(dinv, bq - ax, f0);
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem2(const __grid_constant__ MArgs<T> a, int nsweeps,
                                                                   int per) {

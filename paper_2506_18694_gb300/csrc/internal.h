@@ -243,6 +243,40 @@ template <typename T>
 cudaError_t launch_coarse_solve(const MArgs<T>& a, int nsweeps, cudaStream_t s);
 
 
+// ---- the whole 2D HSS loop in one cooperative launch (hssp.cu) ----
+// Passes of one HSS step with one V(2,2) cycle on L levels (2 <= L <= kPMaxLevels): pre[0]
+// the HSS right side, two sweeps and the restricted residual on level 0 (`first` is the same
+// for the first step, with u = 0); pre[l], 1 <= l < L - 1, two sweeps from 0 and the
+// restricted residual; `coarse` nu_coarse sweeps from 0 on level L - 1 (z: right side, y:
+// result), `coarse_rows` rows per CTA band; post[l], l < L - 1, the prolongation of the coarse
+// result and two sweeps.  Strips and chunks give each pass's warp tiles (as the separate
+// kernels would launch them).  count: the grid barrier's arrival counter (zeroed by the
+// launcher); status: 0, or an hh_status a CTA recorded (HH_ERR_TIMEOUT when a barrier wait
+// ran past spin_limit polls); the host reads and clears it.
+constexpr int kPMaxLevels = 5;
+template <typename T> struct HssLoop2 {
+    MArgs<T> first;
+    MArgs<T> pre[kPMaxLevels];
+    MArgs<T> post[kPMaxLevels];
+    MArgs<T> coarse;
+    int pre_strips[kPMaxLevels], pre_chunks[kPMaxLevels];
+    int post_strips[kPMaxLevels], post_chunks[kPMaxLevels];
+    int levels, nsteps, nb, nu_coarse, coarse_rows;
+    unsigned* count;
+    int* status;
+    unsigned long long spin_limit;
+};
+// dynamic shared memory of the coarsest-level pass for coarse grid gc and bands of `rows` rows
+// (at most kLoopSmemMax; the solver takes narrower bands until it fits, else one kernel per pass)
+constexpr size_t kLoopSmemMax = 96 * 1024;
+template <typename T>
+size_t hss_loop2_smem(const GridDesc& gc, int nu_coarse, int rows);
+// CTAs of the cooperative grid (resident at once; at most 4 per SM), 0 if none fit
+template <typename T>
+int hss_loop2_ctas(bool batch, size_t smem);
+template <typename T>
+cudaError_t launch_hss_loop2(const HssLoop2<T>& P, int ctas, size_t smem, cudaStream_t s);
+
 // ---- GMRES smoother with a Jacobi preconditioner (gsmooth.cu) ----
 // Level vectors of nb problems (problem b at offset b * N); the Krylov basis holds vector i
 // of problem b at V + i * ld + b * N.  Sums in FP64 over a fixed block grid (gs_blocks(N)), so

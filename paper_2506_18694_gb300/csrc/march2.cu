@@ -14,45 +14,6 @@
 
 namespace hh {
 
-// x + P e_c on the NR fine rows rfirst, rfirst + 1, ... of this lane's column ic (P = parity
-// of rfirst), zero where no unknown lives.  Each coarse row the tile touches is read once
-// per lane: the lane at an even fine column takes its coarse value, a lane at an odd column
-// the mean of its own and its right neighbour's (by shuffle; lane 31 reads its second value
-// itself); odd fine rows then average two interpolated coarse rows.  Coarse nodes on a
-// Dirichlet side carry no basis function and count as zero.
-template <typename T, int NR, int P>
-__device__ __forceinline__ void prolong_rows(const MArgs<T>& a, const VPtrs<T>& v, int ic, int rfirst, bool cvoid,
-                                             Cx<T>* out) {
-    const int n = a.g.n, nc = n >> 1, nnc = nc + 1;
-    const int lane = threadIdx.x & 31;
-    const int I = ic >> 1;
-    const int I1 = I + 1 <= nc ? I + 1 : nc;
-    const bool odd = ic & 1;
-    const bool v0 = (I == 0 && a.g.dir[0]) || (I == nc && a.g.dir[1]);
-    const bool v1 = (I1 == 0 && a.g.dir[0]) || (I1 == nc && a.g.dir[1]);
-    constexpr int NCR = ((P + NR) >> 1) + 1;
-    const int J0 = rfirst >> 1;  // floor(rfirst / 2)
-    Cx<T> ex[NCR];
-#pragma unroll
-    for (int q = 0; q < NCR; ++q) {
-        const int J = J0 + q;
-        const bool jv = J < 0 || J > nc || (J == 0 && a.g.dir[2]) || (J == nc && a.g.dir[3]);
-        const long long row = (long long)clampi(J, 0, nc) * nnc;
-        const Cx<T> c0 = (jv || v0) ? cx<T>(0, 0) : ld<T>(v.ec, row + I);
-        Cx<T> c1 = shfl_dn(c0);
-        if (lane == 31) c1 = (jv || v1) ? cx<T>(0, 0) : ld<T>(v.ec, row + I1);
-        ex[q] = odd ? T(0.5) * (c0 + c1) : c0;
-    }
-#pragma unroll
-    for (int t = 0; t < NR; ++t) {
-        const int r = rfirst + t;
-        const long long p = (long long)clampi(r, 0, n) * a.g.nn + ic;
-        const int lq = (P + t) >> 1;
-        const Cx<T> e = ((P + t) & 1) == 0 ? ex[lq] : T(0.5) * (ex[lq] + ex[lq + 1]);
-        out[t] = (cvoid || row_void(a, r)) ? cx<T>(0, 0) : ld<T>(v.x, p) + e;
-    }
-}
-
 // One warp tile: a strip of 30 output columns (lanes 1..30; lanes 0 and 31 are the halo)
 // and ROWS consecutive output rows (RESID_RESTRICT: ROWS coarse rows, 2 ROWS + 1 residual
 // rows, 28 fine columns per strip).  tile_load issues every load of the tile (all in
@@ -210,119 +171,6 @@ __device__ __forceinline__ void tile_compute(const MArgs<T>& a, const PCoef<T>& 
             // Jacobi update of the field: field + omega D^{-1} (b - op field)
             const Cx<T> b = (MODE == M_JACOBI2_ZERO) ? tl.bv[t] : tl.zv[t - 1];
             st<T>(v.y, p, fma_c(dinv_w, b - ax, fv[t]));
-        }
-    }
-}
-
-// ---- two sweeps in one pass ----
-// Tile of the fused modes: 28 output columns (lanes 2..29) and ROWS output rows.  The field
-// is loaded on ROWS + 4 rows; the first stage (a sweep, or the HSS right side and its
-// pointwise first sweep) is formed on the ROWS + 2 rows and lanes 1..30 around the outputs,
-// the second sweep on the outputs.  Every node's arithmetic is that of the one-sweep modes,
-// so the result equals the two separate passes bit for bit.
-template <typename T, int ROWS> struct TileF {
-    static constexpr int NR = ROWS + 4;
-    Cx<T> fv[NR];      // field: x + P ec (PROLONG_JACOBI2) or u (HSS_FIRST2)
-    Cx<T> zv[NR - 2];  // b (PROLONG_JACOBI2) or r (HSS_FIRST2) on rows 1..NR-2
-};
-
-template <typename T, int MODE, int ROWS>
-__device__ __forceinline__ void tilef_load(const MArgs<T>& a, const VPtrs<T>& v, int strip, int cy,
-                                           TileF<T, ROWS>& tl) {
-    constexpr int NR = TileF<T, ROWS>::NR;
-    const int lane = threadIdx.x & 31;
-    const int n = a.g.n;
-    const int i = strip * 28 + lane - 2;
-    const int rfirst = cy * ROWS - 2;
-    const int ic = clampi(i, 0, n);
-    const bool cvoid = col_void(a, i);
-    if (MODE == M_PROLONG_JACOBI2) {
-        prolong_rows<T, NR, 0>(a, v, ic, rfirst, cvoid, tl.fv);  // (first row cy * ROWS - 2 is even)
-    } else {
-#pragma unroll
-        for (int t = 0; t < NR; ++t) {
-            const int r = rfirst + t;
-            const long long p = (long long)clampi(r, 0, n) * a.g.nn + ic;
-            tl.fv[t] = (a.xzero || cvoid || row_void(a, r)) ? cx<T>(0, 0) : ld<T>(v.x, p);
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < NR - 2; ++t) tl.zv[t] = ld<T>(v.z, (long long)clampi(rfirst + 1 + t, 0, n) * a.g.nn + ic);
-}
-
-template <typename T, int MODE, int ROWS>
-__device__ __forceinline__ void tilef_compute(const MArgs<T>& a, const PCoef<T>& c, const PCoef<T>& cl,
-                                              const VPtrs<T>& v, int strip, int cy, TileF<T, ROWS>& tl) {
-    constexpr int NR = TileF<T, ROWS>::NR;
-    const int lane = threadIdx.x & 31;
-    const int n = a.g.n;
-    const int i = strip * 28 + lane - 2;
-    const int rfirst = cy * ROWS - 2;
-    const int ic = clampi(i, 0, n);
-    const bool col_in = (i >= 0 && i <= n);
-    const bool col_inner = (i >= 1 && i <= n - 1);
-    const bool cvoid = col_void(a, i);
-    const int tx = ic == 0 ? 0 : (ic == n ? 2 : 1);
-    const Cx<T>* fv = tl.fv;
-    Cx<T> lf[NR], rg[NR];
-#pragma unroll
-    for (int t = 0; t < NR; ++t) {
-        lf[t] = shfl_up(fv[t]);
-        rg[t] = shfl_dn(fv[t]);
-    }
-    // first stage on rows 1..NR-2: x1, and the right side of the second sweep
-    Cx<T> x1[NR], b2[NR];
-    x1[0] = x1[NR - 1] = b2[0] = b2[NR - 1] = cx<T>(0, 0);
-    const Cx<T> alpha = a.use_pc_ab ? c.alpha : a.alpha, beta = a.use_pc_ab ? c.beta : a.beta;
-#pragma unroll
-    for (int t = 1; t < NR - 1; ++t) {
-        const int j = rfirst + t;
-        const int jc = clampi(j, 0, n);
-        const bool fast = col_inner && j >= 1 && j <= n - 1;
-        const int ty = jc == 0 ? 0 : (jc == n ? 2 : 1);
-        Cx<T> ax, dinv_w;
-        stencil_node2(c, fv[t - 1], fv[t], fv[t + 1], lf[t - 1], lf[t], lf[t + 1], rg[t - 1], rg[t], rg[t + 1], fast,
-                      tx, ty, ax, dinv_w);
-        const bool vd = cvoid || row_void(a, j);
-        if (MODE == M_PROLONG_JACOBI2) {
-            b2[t] = tl.zv[t - 1];
-            x1[t] = vd ? cx<T>(0, 0) : fma_c(dinv_w, tl.zv[t - 1] - ax, fv[t]);
-        } else {
-            const Cx<T> rhs = fma_c(alpha, ax, cmul(beta, tl.zv[t - 1]));
-            b2[t] = vd ? cx<T>(0, 0) : rhs;
-            x1[t] = vd ? cx<T>(0, 0) : cmul(dinv_w, rhs);
-        }
-    }
-    // second sweep (operator cl) on the output rows 2..NR-3
-#pragma unroll
-    for (int t = 0; t < NR; ++t) {
-        lf[t] = shfl_up(x1[t]);
-        rg[t] = shfl_dn(x1[t]);
-    }
-#pragma unroll
-    for (int t = 2; t < NR - 2; ++t) {
-        const int j = rfirst + t;
-        const bool row_in = (j >= 0 && j <= n);
-        const int jc = clampi(j, 0, n);
-        const bool fast = col_inner && j >= 1 && j <= n - 1;
-        const int ty = jc == 0 ? 0 : (jc == n ? 2 : 1);
-        Cx<T> ax, dinv_w;
-        stencil_node2(cl, x1[t - 1], x1[t], x1[t + 1], lf[t - 1], lf[t], lf[t + 1], rg[t - 1], rg[t], rg[t + 1], fast,
-                      tx, ty, ax, dinv_w);
-        if (!(lane >= 2 && lane <= 29 && col_in && row_in)) continue;
-        const long long p = (long long)jc * a.g.nn + ic;
-        const bool masked = !fast && (cvoid || row_void(a, j));
-        if (masked) {
-            st<T>(v.y, p, cx<T>(0, 0));
-            if (MODE == M_HSS_FIRST2) st<T>(v.y2, p, cx<T>(0, 0));
-            continue;
-        }
-        const Cx<T> x2 = fma_c(dinv_w, b2[t] - ax, x1[t]);
-        if (MODE == M_PROLONG_JACOBI2) {
-            st<T>(v.y, p, x2);
-        } else {
-            st<T>(v.y, p, b2[t]);
-            st<T>(v.y2, p, x2);
         }
     }
 }

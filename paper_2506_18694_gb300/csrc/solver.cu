@@ -126,6 +126,12 @@ struct Hier {
     void** usrc = nullptr;            // device: per problem, the buffer holding u after the HSS loop
     cudaGraphExec_t graph = nullptr;  // one preconditioner application (the HSS loop)
     long long graph_kernels = 0;      // kernel nodes in the graph
+    // the persistent form of the HSS loop (hh::HssLoop2<T> of this precision), built with the
+    // graph's buffers and coefficients and dropped when they change
+    std::vector<unsigned char> loop;
+    int loop_ctas = 0;
+    size_t loop_smem = 0;
+    bool loop_unfit = false;  // its grid does not fit the device: separate kernels instead
 };
 
 }  // namespace
@@ -150,6 +156,9 @@ struct hh_problem {
     int* d_nhss = nullptr;     // device: HSS iterations per problem
     int* d_active = nullptr;   // device: 1 = problem takes part in the launches
     int* h_active = nullptr;   // pinned mirror
+    unsigned* d_sync = nullptr;  // device: grid-barrier counter [0] and status word [1] of the
+                                 // persistent HSS loop
+    int* h_sync = nullptr;       // pinned copy of the status word
     Hier hier[2];
     // FP64 Krylov storage (level 0), laid out [vector][problem][node]
     long long N = 0;            // entries per problem of the Krylov vectors (+ ns when mixed)
@@ -216,7 +225,7 @@ size_t krylov_bytes(const hh_grid* grid, int restart, int nb, long long extra) {
     long long nn = grid->n + 1;
     long long N = nn * nn * (grid->dim == 3 ? nn : 1) + extra;
     const size_t m = (size_t)restart, B = (size_t)nb;
-    size_t tot = 2 * sizeof(int) * B;                      // nhss, active
+    size_t tot = 2 * sizeof(int) * B + 16;                 // nhss, active, barrier words
     tot += (2 * m + 1 + 3) * B * (size_t)N * 16;           // V, Z, x, bvec, r
     tot += B * (m + 1) * hh::kRedBlocks * 16;              // partials
     tot += B * (2 * (m + 1) + 1) * 16 + B * m * 16;        // hbuf, ybuf
@@ -883,6 +892,72 @@ struct MG {
         return HH_OK;
     }
 
+    // The passes of the persistent HSS loop (hssp.cu) with the buffers hss_loop uses for the same
+    // cycle: level 0 x1 in xa[0] and u in xb[0], level l's pre-smoothed x in xa[l] and its
+    // post-smoothed x in xb[l], right sides in b[l], the coarsest result in xa[L - 1].
+    void loop_plan(hh::HssLoop2<T>* P) {
+        const int L = p->o.levels;
+        std::memset((void*)P, 0, sizeof(*P));
+        P->levels = L;
+        P->nsteps = p->max_nhss;
+        P->nb = p->nb;
+        P->nu_coarse = p->o.nu_coarse;
+        auto geo = [&](hh::MArgs<T>& a, int l) {
+            a.h = T(p->lv[l].h);
+            a.ih = T(1.0 / p->lv[l].h);
+            a.hss_it = -1;
+        };
+        auto X = [&](std::vector<void*>& v, int l) { return (V2*)v[l]; };
+        hh::MArgs<T> a = margs2(0, R_AR);
+        geo(a, 0);
+        a.x = X(H->xb, 0);
+        a.z = (const V2*)H->r_lo;
+        a.y = (V2*)H->rhs;
+        a.y2 = X(H->xa, 0);
+        a.yc = X(H->b, 1);
+        a.use_pc_ab = 1;
+        P->pre[0] = a;
+        a.x = nullptr;
+        a.xzero = 1;
+        P->first = a;
+        const int nn0 = p->lv[0].n + 1;
+        P->pre_strips[0] = (nn0 + 23) / 24;
+        P->pre_chunks[0] = p->lv[0].n / 2 + 1;
+        for (int l = 1; l < L - 1; ++l) {
+            hh::MArgs<T> q = margs2(l, R_AL);
+            geo(q, l);
+            q.z = X(H->b, l);
+            q.y = X(H->xa, l);
+            q.yc = X(H->b, l + 1);
+            P->pre[l] = q;
+            P->pre_strips[l] = (p->lv[l].nn + 25) / 26;
+            P->pre_chunks[l] = p->lv[l].n / 2 + 1;
+        }
+        hh::MArgs<T> c = margs(L - 1, R_AL);
+        geo(c, L - 1);
+        c.z = X(H->b, L - 1);
+        c.y = X(H->xa, L - 1);
+        P->coarse = c;
+        P->coarse_rows = std::max(1, (p->lv[L - 1].nn + 31) / 32);
+        while (P->coarse_rows > 1 &&
+               hh::hss_loop2_smem<T>(p->lv[L - 1], p->o.nu_coarse, P->coarse_rows) > hh::kLoopSmemMax)
+            --P->coarse_rows;
+        for (int l = L - 2; l >= 0; --l) {
+            hh::MArgs<T> q = margs2(l, R_AL);
+            geo(q, l);
+            q.x = X(H->xa, l);
+            q.ec = l == L - 2 ? X(H->xa, L - 1) : X(H->xb, l + 1);
+            q.z = l == 0 ? (const V2*)H->rhs : X(H->b, l);
+            q.y = X(H->xb, l);
+            P->post[l] = q;
+            P->post_strips[l] = (p->lv[l].nn + 27) / 28;
+            P->post_chunks[l] = (p->lv[l].nn + 1) / 2;
+        }
+        P->count = p->d_sync;
+        P->status = (int*)(p->d_sync + 1);
+        P->spin_limit = p->o.sync_spin_limit > 0 ? (unsigned long long)p->o.sync_spin_limit : 4194304ULL;
+    }
+
     // The HSS loop of Def. 4.1 on r_lo (already in this precision).  src[b] receives the
     // buffer that holds problem b's result (its loop may end before the others').
     hh_status hss_loop(std::vector<V2*>* src) {
@@ -961,6 +1036,54 @@ hh_status record_hss(hh_problem* p, int prec) {
     return HH_OK;
 }
 
+// Whether the whole HSS loop runs as one cooperative kernel (hssp.cu): 2D primal problems with
+// V(2,2) scaled-Jacobi cycles, one per HSS step, on 2..kPMaxLevels levels; automatically only
+// while the fused two-sweep passes are used (levels of at most 600000 nodes).
+bool persistent_loop(const hh_problem* p) {
+    const hh_options& o = p->o;
+    if (o.persistent == 0 || p->grid.dim != 2 || p->mixed) return false;
+    if (o.smoother != HH_SMOOTH_JACOBI || o.cycle_gamma != 1 || o.cycles_per_hss != 1) return false;
+    if (o.nu_pre != 2 || o.nu_post != 2 || o.levels < 2 || o.levels > hh::kPMaxLevels) return false;
+    return o.persistent == 2 || p->lv[0].N * p->nb <= 600000;
+}
+
+// Launch the persistent HSS loop; *used = false (and nothing launched) when its grid does not
+// fit the device, so that the caller runs the passes as separate kernels instead.
+template <typename T>
+hh_status launch_loop(hh_problem* p, int prec, bool* used) {
+    Hier& H = p->hier[prec];
+    *used = false;
+    if (H.loop_unfit) return HH_OK;
+    if (H.loop.empty()) {
+        MG<T> m = make_mg<T>(p, prec, p->s);
+        H.loop.resize(sizeof(hh::HssLoop2<T>));
+        m.loop_plan(reinterpret_cast<hh::HssLoop2<T>*>(H.loop.data()));
+        const auto* P = reinterpret_cast<const hh::HssLoop2<T>*>(H.loop.data());
+        H.loop_smem = hh::hss_loop2_smem<T>(p->lv[p->o.levels - 1], p->o.nu_coarse, P->coarse_rows);
+        H.loop_ctas = hh::hss_loop2_ctas<T>(p->nb > 1, H.loop_smem);
+        if (H.loop_ctas < 1) {
+            H.loop.clear();
+            H.loop_unfit = true;
+            return HH_OK;
+        }
+        // the result pointer table of the gather (u in xb[0]; problems without HSS steps: 0)
+        std::vector<hh::vec2<T>*> src(p->nb);
+        const long long N0 = p->lv[0].N;
+        bool need_zero = false;
+        for (int b = 0; b < p->nb; ++b) {
+            src[b] = (p->nhss[b] > 0 ? (hh::vec2<T>*)H.xb[0] : (hh::vec2<T>*)H.cres) + (long long)b * N0;
+            need_zero = need_zero || p->nhss[b] == 0;
+        }
+        if (need_zero) HH_CUDA(cudaMemsetAsync(H.cres, 0, (size_t)N0 * p->nb * sizeof(hh::vec2<T>), p->s));
+        HH_CUDA(cudaMemcpyAsync(H.usrc, src.data(), sizeof(void*) * p->nb, cudaMemcpyHostToDevice, p->s));
+        HH_CUDA(cudaStreamSynchronize(p->s));
+    }
+    HH_CUDA(hh::launch_hss_loop2<T>(*reinterpret_cast<const hh::HssLoop2<T>*>(H.loop.data()), H.loop_ctas,
+                                     H.loop_smem, p->s));
+    *used = true;
+    return HH_OK;
+}
+
 // z (c128, nb x N) = shifted-HSS preconditioner of r (c128), on the problem stream, for the
 // active problems.
 hh_status precondition_async(hh_problem* p, const double2* r, double2* z) {
@@ -974,7 +1097,11 @@ hh_status precondition_async(hh_problem* p, const double2* r, double2* z) {
     } else {
         HH_CUDA(cudaMemcpyAsync(H.r_lo, r, (size_t)NT * 16, cudaMemcpyDeviceToDevice, p->s));
     }
-    if (p->o.use_graphs) {
+    bool looped = false;
+    if (persistent_loop(p))
+        HH_TRY(prec == HH_C64 ? launch_loop<float>(p, prec, &looped) : launch_loop<double>(p, prec, &looped));
+    if (looped) {
+    } else if (p->o.use_graphs) {
         if (!H.graph) {
             // the pointer table of the results is written once, outside the graph
             cudaGraph_t g;
@@ -1254,11 +1381,24 @@ hh_status norm2_dev(hh_problem* p, const double2* v, int slot) {
     return HH_OK;
 }
 
+// The status word of the persistent HSS loop (copied with every fetch): a non-zero value is
+// an error a CTA recorded; it is cleared here and returned.
+hh_status check_sync(hh_problem* p) {
+    const int st = *p->h_sync;
+    if (st == 0) return HH_OK;
+    *p->h_sync = 0;
+    HH_CUDA(cudaMemsetAsync(p->d_sync + 1, 0, sizeof(int), p->s));
+    HH_CUDA(cudaStreamSynchronize(p->s));
+    return fail((hh_status)st, st == HH_ERR_TIMEOUT ? "a grid-wide barrier wait of the persistent HSS loop ran out"
+                                                    : "the persistent HSS loop reported an error");
+}
+
 hh_status fetch(hh_problem* p) {
     HH_CUDA(cudaMemcpyAsync(p->h_host, p->hbuf, (size_t)p->nb * hstride(p) * sizeof(double2), cudaMemcpyDeviceToHost,
                             p->s));
+    HH_CUDA(cudaMemcpyAsync(p->h_sync, p->d_sync + 1, sizeof(int), cudaMemcpyDeviceToHost, p->s));
     HH_CUDA(cudaStreamSynchronize(p->s));
-    return HH_OK;
+    return check_sync(p);
 }
 
 bool finite(double v) { return std::isfinite(v); }
@@ -1521,6 +1661,8 @@ hh_status check_args(const hh_grid* grid, int nb, const double* k, const double*
     if (o->cycle_gamma < 1 || o->cycle_gamma > 4) return fail(HH_ERR_INVALID, "cycle_gamma must be in 1..4");
     if (o->outer != HH_OUTER_FGMRES && o->outer != HH_OUTER_RICHARDSON)
         return fail(HH_ERR_INVALID, "outer must be HH_OUTER_FGMRES or HH_OUTER_RICHARDSON");
+    if (o->persistent < 0 || o->persistent > 2) return fail(HH_ERR_INVALID, "persistent must be 0, 1 or 2");
+    if (o->sync_spin_limit < 0) return fail(HH_ERR_INVALID, "sync_spin_limit < 0");
     if (!bc) return fail(HH_ERR_INVALID, "null bc");
     for (int s = 0; s < 2 * grid->dim; ++s)
         if (bc[s] != HH_BC_SOMMERFELD && bc[s] != HH_BC_DIRICHLET) return fail(HH_ERR_INVALID, "bad boundary tag");
@@ -1577,6 +1719,8 @@ void hh_options_default(hh_options* o) {
     o->tile_form = 0;
     o->smoother = HH_SMOOTH_JACOBI;
     o->formulation = HH_FORM_PRIMAL;
+    o->persistent = 0;
+    o->sync_spin_limit = 0;
 }
 
 size_t hh_footprint_batch_bytes(const hh_grid* grid, const hh_options* o, int nb) {
@@ -1601,6 +1745,7 @@ void hh_destroy(hh_problem* p) {
     for (void* a : p->allocs) cudaFree(a);
     if (p->h_host) cudaFreeHost(p->h_host);
     if (p->h_active) cudaFreeHost(p->h_active);
+    if (p->h_sync) cudaFreeHost(p->h_sync);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);
     if (p->s) cudaStreamDestroy(p->s);
@@ -1649,6 +1794,7 @@ hh_status hh_create_batch(const hh_grid* grid, int nb, const double* k, const do
     const size_t hs = (size_t)(2 * (m + 1) + 1);
     if ((st = dmalloc(p, (void**)&p->d_nhss, sizeof(int) * nb)) != HH_OK) return bail(st);
     if ((st = dmalloc(p, (void**)&p->d_active, sizeof(int) * nb)) != HH_OK) return bail(st);
+    if ((st = dmalloc(p, (void**)&p->d_sync, 16)) != HH_OK) return bail(st);
     if ((st = dmalloc(p, (void**)&p->V, (size_t)(m + 1) * nb * N * 16)) != HH_OK) return bail(st);
     if ((st = dmalloc(p, (void**)&p->Z, (size_t)m * nb * N * 16)) != HH_OK) return bail(st);
     if ((st = dmalloc(p, (void**)&p->x, (size_t)nb * N * 16)) != HH_OK) return bail(st);
@@ -1658,9 +1804,12 @@ hh_status hh_create_batch(const hh_grid* grid, int nb, const double* k, const do
     if ((st = dmalloc(p, (void**)&p->hbuf, (size_t)nb * hs * 16)) != HH_OK) return bail(st);
     if ((st = dmalloc(p, (void**)&p->ybuf, (size_t)nb * m * 16)) != HH_OK) return bail(st);
     if (cudaMallocHost((void**)&p->h_host, (size_t)nb * hs * 16) != cudaSuccess ||
-        cudaMallocHost((void**)&p->h_active, sizeof(int) * nb) != cudaSuccess)
+        cudaMallocHost((void**)&p->h_active, sizeof(int) * nb) != cudaSuccess ||
+        cudaMallocHost((void**)&p->h_sync, sizeof(int)) != cudaSuccess)
         return bail(fail(HH_ERR_OOM, "pinned host allocation failed"));
-    if (cudaMemcpyAsync(p->d_nhss, p->nhss.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, p->s) != cudaSuccess)
+    *p->h_sync = 0;
+    if (cudaMemcpyAsync(p->d_nhss, p->nhss.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, p->s) != cudaSuccess ||
+        cudaMemsetAsync(p->d_sync, 0, 16, p->s) != cudaSuccess)
         return bail(fail(HH_ERR_CUDA, "initialisation failed"));
     if ((st = set_active(p, nullptr)) != HH_OK) return bail(st);
     if ((st = ensure_hier(p, opts->precision)) != HH_OK) return bail(st);
@@ -1689,12 +1838,14 @@ hh_status hh_set_params(hh_problem* p, const double* k, const double* delta, con
     HH_CUDA(cudaMemcpyAsync(p->d_nhss, p->nhss.data(), sizeof(int) * p->nb, cudaMemcpyHostToDevice, p->s));
     HH_TRY(build_tables<float>(p, p->hier[HH_C64]));
     HH_TRY(build_tables<double>(p, p->hier[HH_C128]));
-    // the preconditioner graphs hold the old coefficients and HSS lengths
-    for (int q = 0; q < 2; ++q)
+    // the preconditioner graphs and loop plans hold the old coefficients and HSS lengths
+    for (int q = 0; q < 2; ++q) {
         if (p->hier[q].graph) {
             cudaGraphExecDestroy(p->hier[q].graph);
             p->hier[q].graph = nullptr;
         }
+        p->hier[q].loop.clear();
+    }
     return HH_OK;
 }
 
@@ -1703,9 +1854,10 @@ hh_status hh_prepare(hh_problem* p) {
     HH_TRY(join_in(p));
     HH_CUDA(cudaMemsetAsync(p->r, 0, (size_t)p->nb * p->N * 16, p->s));
     HH_TRY(precondition_async(p, p->r, p->Z));
+    HH_CUDA(cudaMemcpyAsync(p->h_sync, p->d_sync + 1, sizeof(int), cudaMemcpyDeviceToHost, p->s));
     HH_TRY(join_out(p));
     HH_CUDA(cudaStreamSynchronize(p->s));
-    return HH_OK;
+    return check_sync(p);
 }
 
 hh_status hh_create_problem(const hh_grid* grid, double k, double delta, double delta_hat, const int* bc,
@@ -1944,9 +2096,10 @@ hh_status hh_precondition(hh_problem* p, const void* r, void* z) {
     if (!p || !r || !z) return fail(HH_ERR_INVALID, "null argument");
     HH_TRY(join_in(p));
     HH_TRY(precondition_async(p, (const double2*)r, (double2*)z));
+    HH_CUDA(cudaMemcpyAsync(p->h_sync, p->d_sync + 1, sizeof(int), cudaMemcpyDeviceToHost, p->s));
     HH_TRY(join_out(p));
     HH_CUDA(cudaStreamSynchronize(p->s));
-    return HH_OK;
+    return check_sync(p);
 }
 
 hh_status hh_load_vector(hh_problem* p, const void* f, void* b) {

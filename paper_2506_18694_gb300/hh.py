@@ -17,6 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libhh.so")
 
 HH_OK, HH_NOT_CONVERGED = 0, 1
+HH_ERR_INVALID, HH_ERR_OOM, HH_ERR_CUDA, HH_ERR_NONFINITE, HH_ERR_TIMEOUT = -1, -2, -3, -4, -5
 HH_C128, HH_C64 = 0, 1
 HH_OUTER_FGMRES, HH_OUTER_RICHARDSON = 0, 1
 HH_SMOOTH_JACOBI, HH_SMOOTH_GMRES = 0, 1
@@ -48,6 +49,7 @@ class Options(ctypes.Structure):
         ("coarse_cluster_nodes", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
         ("fuse_sweeps", ctypes.c_int), ("outer", ctypes.c_int), ("cycle_gamma", ctypes.c_int),
         ("tile_form", ctypes.c_int), ("smoother", ctypes.c_int), ("formulation", ctypes.c_int),
+        ("persistent", ctypes.c_int), ("sync_spin_limit", ctypes.c_longlong),
     ]
 
 
