@@ -35,7 +35,7 @@ WORKLOAD = "2d_n512_k80"
 GRIDS = {"2d_n512_k80": "2D unit square, 512x512 Q1 cells (513^2 nodes), Sommerfeld on all sides",
          "3d_n128_k40": "3D unit cube, 128^3 Q1 cells (129^3 nodes), u=0 on z=0, Sommerfeld elsewhere"}
 L2_FLUSH_BYTES = 256 << 20
-SERVE_REQUESTS = [16]
+SERVE_REQUESTS = [100]
 
 
 def parse():
@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=["2d_n512_k80", "3d_n128_k40"],
                     help="2D 512^2 k=80 (default) or 3D 128^3 k=40 (FGMRES restart 60)")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 / roofline / CPU legs")
-    ap.add_argument("--serve-requests", type=int, default=16,
+    ap.add_argument("--serve-requests", type=int, default=100,
                     help="requests of the serving workload replayed by the serving leg (its full size is 1000)")
     ap.add_argument("--serve-only", action="store_true", help="run the serving leg alone and print its line")
     ap.add_argument("--max-outer", type=int, default=0,
@@ -370,20 +370,10 @@ def time_kernel(torch, fn, reps, flush=None):
     return tot / reps / 1e3
 
 
-def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    out = {}
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-
-    # dominant kernel: fine-level Jacobi sweep (c64).  24 algorithmic bytes per node
-    # (read x, b; write x').  Timed at the workload size (L2-resident) and on a 4096^2
-    # grid whose vectors (134 MB each) exceed L2, which is where the HBM roofline applies.
+def sweep_roofline(hh, torch, w, prob, b, hbm, peak_src, flush):
+    """HBM roofline of the scaled-Jacobi sweep (24 algorithmic bytes per node) on a grid whose
+    vectors exceed L2 (2D 4097^2 or 3D 257^3), timed with CUDA events over back-to-back launches,
+    and its effective rate at the workload's own size (L2-resident)."""
     N = prob.nodes()
     x = torch.zeros(N, dtype=torch.complex64, device="cuda")
     b32 = b.to(torch.complex64)
@@ -407,12 +397,77 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
         kname, prof, src = ("k_march3<float, JACOBI, 4> (scaled-Jacobi sweep)", "jacobi_3d_257cube_c64.md",
                             "paper_2506_18694_gb300/csrc/march3.cu")
         size = "257^3 nodes (3 x 136 MB vectors > L2)"
-    out["roofline"] = {"bound": "hbm", "kernel": kname,
-                       "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                       "traffic": profiled_traffic(prof, src), "size": size,
-                       "bytes_per_node": 24, "peak_source": peak_src,
-                       "at_workload": {"nodes": N, "us": t_w * 1e6, "effective_gbs": 24 * N / t_w / 1e9,
-                                       "note": "513^2 vectors are L2-resident"}}
+    return {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": profiled_traffic(prof, src), "size": size, "bytes_per_node": 24, "peak_source": peak_src,
+            "at_workload": {"nodes": N, "us": t_w * 1e6, "effective_gbs": 24 * N / t_w / 1e9,
+                            "note": "the workload's vectors are L2-resident"}}
+
+
+def measure_c3(hh, inputs, torch, hbm, peak_src, flush, steps=2):
+    """The 3D unit-cube workload: 128^3 Q1 cells, k = 40, delta_hat = k, u = 0 on z = 0, complex64
+    V-cycles inside FGMRES(60) to 1e-8; device-resident solves timed with CUDA events (L2 flushed
+    before each), one end-to-end solve through hh_solve_host, and the 3D sweep's roofline."""
+    w = inputs.workload("3d_n128_k40")
+    opts = hh.default_options(precision=hh.HH_C64, restart=60)
+    stream = torch.cuda.current_stream()
+    with hh.Problem(w.dim, w.n, w.k, w.delta, w.delta_hat, w.bc, opts) as p:
+        N = p.nodes()
+        f = torch.from_numpy(inputs.gaussian_source(w.dim, w.n, w.centre, w.sigma)).cuda()
+        b = p.load_vector(f)
+        u = torch.empty_like(b)
+        p.solve(b, w.tol, u=u)  # warm-up (graph capture)
+        ms, infos = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, info = p.solve(b, w.tol, u=u)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            infos.append(info)
+        rhs_host = b.cpu().numpy()
+        out_host = np.empty_like(rhs_host)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, ie = p.solve_host(rhs_host, w.tol, out=out_host)
+        e2e_s = time.perf_counter() - t0
+        roof = sweep_roofline(hh, torch, w, p, b, hbm, peak_src, flush)
+    tot = sum(ms) / 1e3
+    return {"workload": w.name, "grid": GRIDS[w.name], "k": w.k, "delta_hat": w.delta_hat, "tol": w.tol,
+            "restart": 60, "value": N * sum(i.vcycles for i in infos) / tot, "unit": UNIT,
+            "ms_per_solve": 1e3 * tot / steps,
+            "per_solve": {"outer_its": infos[-1].outer_its, "vcycles": infos[-1].vcycles,
+                          "rel_residual": infos[-1].rel_residual},
+            "e2e": {"value": N * ie.vcycles / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * 16,
+                    "d2h_bytes_per_step": N * 16, "ms_per_step": 1e3 * e2e_s},
+            "roofline": roof}
+
+
+def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    out = {}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # dominant kernel: fine-level Jacobi sweep (c64).  24 algorithmic bytes per node
+    # (read x, b; write x').  Timed at the workload size (L2-resident) and on a 4096^2
+    # grid whose vectors (134 MB each) exceed L2, which is where the HBM roofline applies.
+    out["roofline"] = sweep_roofline(hh, torch, w, prob, b, hbm, peak_src, flush)
+
+    # the 3D 128^3, k = 40 workload (complex64 V-cycles, FGMRES(60) to 1e-8) with the roofline
+    # of its sweep kernel on 257^3 nodes
+    if w.dim == 2:
+        try:
+            out["c3"] = measure_c3(hh, inputs, torch, hbm, peak_src, flush)
+        except Exception as e:
+            out["c3"] = {"failed": str(e)}
 
     # FP64 V-cycles on the same workload (single solve), error vs the mixed result
     opts64 = hh.default_options(precision=hh.HH_C128, restart=opts.restart)
@@ -554,59 +609,71 @@ def measure_mixed(hh, inputs, torch, w, n=256, k=20.0):
     return res
 
 
-def measure_serving(hh, inputs, torch, count, slots=4, load=0.8):
-    """The serving workload (mixed 2D/3D grids and wavenumbers, nodal Gaussian sources,
-    delta_hat = k, tol 1e-8, FGMRES restart 60, at most 3000 iterations) through the
-    solve server.  Pass 1 runs the requests one at a time (1 slot) and gives the
-    sequential service capacity; pass 2
-    replays them with Poisson arrivals at `load` times that capacity into a server with
-    `slots` slots (latency); pass 3 queues them all at once (throughput with overlap)."""
+def serving_options(hh):
+    """Options of the serving workload's first solve (V(2,2)-Jacobi cycles at delta_hat = k,
+    FGMRES restart 60, given up once it stalls) and of the fallback solve for requests that do
+    not converge with them (the paper's multigrid at delta_hat = 2: W-cycles with GMRES(5) and a
+    Jacobi preconditioner on every level, Sec. 5.3)."""
+    first = hh.default_options(precision=hh.HH_C64, restart=60, max_outer=3000, stall_cycles=4)
+    fallback = hh.default_options(precision=hh.HH_C64, restart=30, max_outer=600, cycle_gamma=2, nu_pre=5,
+                                  nu_post=5, nu_coarse=5, smoother=hh.HH_SMOOTH_GMRES)
+    return first, fallback
+
+
+def measure_serving(hh, inputs, torch, count, slots=4, load=0.8, tol=1e-8):
+    """The serving workload (mixed 2D/3D grids and wavenumbers, nodal Gaussian sources, tol 1e-8)
+    through the solve server with the fallback policy of serving_options.  Pass 1 queues every
+    request at once: the server's capacity (solves/s) and each request's service record.  Pass 2
+    replays them with the seeded Poisson arrival times rescaled to `load` times that capacity:
+    latency p50/p99.  A request that ends above tol counts as failed and not in solves/s."""
     reqs = inputs.serving_requests(count)
     srcs = [r.source() for r in reqs]
-    opts = hh.default_options(precision=hh.HH_C64, restart=60, max_outer=3000)
+    first, fallback = serving_options(hh)
     budget = int(torch.cuda.mem_get_info()[0] * 0.6)
 
-    def run(slots, arrivals):
-        with hh.Server(slots=slots, budget_bytes=budget, options=opts) as srv:
+    def run(arrivals):
+        with hh.Server(slots=slots, budget_bytes=budget, options=first) as srv:
+            srv.set_fallback(fallback, 2.0)
             t0 = time.perf_counter()
             tickets = []
             for r, f, a in zip(reqs, srcs, arrivals):
                 now = time.perf_counter() - t0
                 if a > now:
                     time.sleep(a - now)
-                tickets.append(srv.submit(r.dim, r.n, r.k, r.delta, r.delta_hat, r.bc, f, 1e-8, nodal=True))
+                tickets.append(srv.submit(r.dim, r.n, r.k, r.delta, r.delta_hat, r.bc, f, tol, nodal=True))
             res = [srv.wait(t) for t in tickets]
             span = time.perf_counter() - t0
             st = srv.stats()
         return res, span, st
 
-    seq, seq_span, _ = run(1, [0.0] * len(reqs))
-    service = [x[1].seconds for x in seq]
-    cap = len(reqs) / sum(service)
-    rate = load * cap
+    sat, sat_span, sat_st = run([0.0] * len(reqs))
+    ok_sat = [x[1].rel_residual <= tol for x in sat]
+    cap = sum(ok_sat) / sat_span
+    rate = load * len(reqs) / sat_span
     arr = [r.arrival / reqs[-1].arrival * (len(reqs) / rate) for r in reqs]  # seeded Poisson times, rescaled
-    res, span, st = run(slots, arr)
-    _, sat_span, sat_st = run(slots, [0.0] * len(reqs))  # everything queued at once
+    res, span, st = run(arr)
+    ok = [x[1].rel_residual <= tol for x in res]
     lat = [x[2] for x in res]
     work = sum(r.nodes * x[1].vcycles for r, x in zip(reqs, res))
     return {
         "workload": "serving: half 2D n in [64,1024], half 3D n in [32,96] (log-uniform, multiple of 8), "
-                    "k uniform [10,160] capped at 2 pi n/10, delta_hat = k, tol 1e-8",
+                    "k uniform [10,160] capped at 2 pi n/10, tol 1e-8; first solve V(2,2)-Jacobi at delta_hat = k "
+                    "(FGMRES(60), given up after 4 restart cycles without halving the residual), fallback the "
+                    "paper's multigrid at delta_hat = 2 (W-cycles, GMRES(5) + Jacobi on every level)",
         "requests": len(reqs), "of_full": 1000, "slots": slots, "budget_bytes": budget,
-        "sequential_capacity_solves_per_s": cap, "arrival_rate_per_s": rate, "load": load,
-        "solves_per_s": len(reqs) / span, "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
-                                                         "p99": 1e3 * float(np.percentile(lat, 99))},
+        "capacity_solves_per_s": cap, "arrival_rate_per_s": rate, "load": load,
+        "solves_per_s": sum(ok) / span, "failed": len(ok) - sum(ok), "failed_saturated": len(ok_sat) - sum(ok_sat),
+        "fallbacks": sum(x[1].fallback for x in res),
+        "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},
         "queue_ms_p50": 1e3 * float(np.percentile([x[3] for x in res], 50)),
         "value": work / span, "unit": UNIT,
         "max_rel_residual": max(x[1].rel_residual for x in res),
         "max_concurrent": st["max_concurrent"], "peak_bytes": st["peak_bytes"],
         "problems_created": st["problems_created"], "problems_reused": st["problems_reused"],
         "problems_evicted": st["problems_evicted"],
-        "sequential_s": seq_span,
-        "saturated": {"solves_per_s": len(reqs) / sat_span, "vs_sequential": seq_span / sat_span,
-                      "max_concurrent": sat_st["max_concurrent"]},
-        "per_request": [[r.dim, r.n, round(r.k, 1), x[1].outer_its, x[1].rel_residual, round(x[1].seconds, 3)]
-                        for r, x in zip(reqs, seq)],
+        "saturated": {"solves_per_s": cap, "span_s": sat_span, "max_concurrent": sat_st["max_concurrent"]},
+        "per_request": [[r.dim, r.n, round(r.k, 1), x[1].outer_its, x[1].rel_residual, round(x[1].seconds, 3),
+                         x[1].fallback] for r, x in zip(reqs, sat)],
     }
 
 

@@ -116,8 +116,8 @@ typedef struct {
     int use_graphs;      /* 1: replay each preconditioner application from a CUDA graph       */
     int use_pdl;         /* 1: programmatic dependent launch between consecutive kernels      */
     int coarse_cluster_nodes; /* the coarsest level, if it has at most this many nodes and   */
-                              /* fits, runs all its sweeps in one thread-block cluster with  */
-                              /* the level in distributed shared memory; 0 = never           */
+                              /* fits, runs all its sweeps in one launch (coarse_kernel);    */
+                              /* 0 = never (one launch per sweep)                            */
     int tile_rows;       /* rows (2D) / z-planes (3D) per warp tile of the stencil kernels:   */
                          /* 2, 4 or 8; 0 = chosen from the grid size                          */
     int autotune;        /* 1: run hh_autotune for `precision` when the problem is created    */
@@ -159,6 +159,15 @@ typedef struct {
     long long sync_spin_limit; /* polls a grid-wide barrier wait may take before the kernel     */
                          /* gives up and the call returns HH_ERR_TIMEOUT; 0 = 4194304 (about   */
                          /* a second or more); tiny values make the waits run out on purpose   */
+    int stall_cycles;    /* > 0: FGMRES gives a problem up (HH_NOT_CONVERGED, last iterate in u) */
+                         /* when stall_cycles restart cycles in a row did not halve its true    */
+                         /* residual; 0 (default): only max_outer ends it                       */
+    int coarse_kernel;   /* the coarsest level's one-launch solve (see coarse_cluster_nodes): 0    */
+                         /* (default) or 1: a thread-block cluster (level in distributed shared  */
+                         /* memory, halos exchanged between sweeps); 2 (2D only): bands of rows, */
+                         /* one CTA each, every sweep in shared memory with the halo rows         */
+                         /* recomputed, no exchange between CTAs (what packs and the persistent  */
+                         /* loop use).  Same result bit for bit                                  */
 } hh_options;
 
 typedef struct {
@@ -169,6 +178,8 @@ typedef struct {
     double seconds;         /* wall time of the call                             */
     size_t device_bytes;    /* device memory held by the problem                 */
     long long kernel_launches; /* kernels this call ran (graph replays counted per node) */
+    int fallback;           /* solve server only: 1 if the request was solved again with the     */
+                            /* server's fallback settings (hh_server_set_fallback)              */
 } hh_info;
 
 typedef struct hh_problem hh_problem;
@@ -356,6 +367,47 @@ HH_API hh_status hh_multidot_noalloc(const void* V, long long ld, int nvec, cons
                                      void* out, void* cuda_stream);
 
 /*
+ * ---- packs: problems of different grids in shared launches (a service of this library; the
+ *      paper has none) ----
+ * A pack runs the FGMRES solves of up to `capacity` problems side by side.  Every outer
+ * iteration of a member is the same sequence of operations as in its own hh_solve (same kernels,
+ * on the member's own stream), except that the preconditioner applications (Def. 4.1) of all
+ * members that need one in the same round run together: each pass of the V-cycle is ONE launch
+ * covering the tiles of every member, whatever its grid, replayed from a CUDA graph.  Members
+ * join (hh_pack_add) and leave (hh_pack_take) between rounds, so a finished member's slot can be
+ * refilled at once while the others go on.  Each member's result equals its own hh_solve's bit
+ * for bit.  Members: problems of hh_create_problem (one problem each) in 2D, primal, with
+ * V(2,2) scaled-Jacobi cycles, one per HSS step, complex64 cycles, FGMRES, and the same number
+ * of levels (2..5); a member problem must not be used otherwise until it is taken.  The pack
+ * does not own its members' problems.  Blocking calls; not thread-safe.
+ */
+typedef struct hh_pack hh_pack;
+
+/* An empty pack for at most `capacity` (1..256) members on the current device. */
+HH_API hh_status hh_pack_create(int capacity, hh_pack** out);
+
+/* Add problem p with right side rhs (io 0: device load vector; 1: host load vector; 2: host
+ * nodal source f, b = M f), tolerance tol (as hh_solve) and output u (device for io 0, host
+ * otherwise; (n + 1)^2 complex128 entries, written when the member finishes).  *slot receives
+ * the member's slot.  HH_ERR_INVALID if p cannot be packed, the pack is full or p is in it. */
+HH_API hh_status hh_pack_add(hh_pack* k, hh_problem* p, const void* rhs, int io, double tol, void* u, int* slot);
+
+/* Run rounds (every running member advances to its next synchronisation point) until at least
+ * one member has finished, no member is running, or max_rounds rounds (> 0) have run; done (room
+ * for `capacity` ints) receives the slots of every finished member not yet taken, *ndone their
+ * number. */
+HH_API hh_status hh_pack_run(hh_pack* k, int max_rounds, int* done, int* ndone);
+
+/* The status and info of the finished member in `slot` (as hh_solve returns them; seconds from
+ * hh_pack_add to its end); frees the slot and releases the problem to the caller. */
+HH_API hh_status hh_pack_take(hh_pack* k, int slot, hh_info* info);
+
+/* Members in the pack (running or finished and not yet taken). */
+HH_API int hh_pack_members(const hh_pack* k);
+
+HH_API void hh_pack_destroy(hh_pack* k);
+
+/*
  * ---- continuous-batching solve server (a service of this library; the paper has none) ----
  * A request loop on the current device: requests of any grid, wavenumber and shifts are
  * queued, admitted in arrival order as worker slots and device memory free up, and solved
@@ -405,6 +457,25 @@ HH_API hh_status hh_server_submit(hh_server* s, const hh_request* req, const voi
 HH_API hh_status hh_server_wait(hh_server* s, long long ticket, hh_info* info, double* latency_s, double* queue_s);
 
 HH_API hh_status hh_server_get_stats(hh_server* s, hh_server_stats* out);
+
+/* Pack the server's 2D requests (before the first request; the server's options must be packable,
+ * see hh_pack_create): a dispatcher thread runs up to `capacity` (1..256) of them as members of
+ * one pack, so that their preconditioner applications share launches, and admits queued ones
+ * between rounds as members finish and device memory frees up (continuous batching); other
+ * requests, and fallback solves, run on the worker slots as before.  Results equal the lone
+ * solves bit for bit. */
+HH_API hh_status hh_server_set_pack(hh_server* s, int capacity);
+
+/* Fallback for requests that do not converge: a request whose solve ends HH_NOT_CONVERGED (its
+ * max_outer reached, or stalled under opts.stall_cycles) is solved once more from zero on a
+ * problem built with *opts and this delta_hat (> 0) instead of the request's, and its result,
+ * status and info (outer_its, hss_its, vcycles and seconds summed over both attempts, fallback =
+ * 1) are those of that second solve.  The solution of B_delta u = b does not depend on delta_hat
+ * or the preconditioner; only whether FGMRES reaches it does (e.g. the paper's multigrid, W-cycles
+ * with GMRES(5) and Jacobi on every level at delta_hat = 2, Sec. 5.3, where V-cycles with scaled
+ * Jacobi at delta_hat = k stall).  opts NULL removes the fallback.  Applies to requests submitted
+ * afterwards; the fallback problems count against the same device budget. */
+HH_API hh_status hh_server_set_fallback(hh_server* s, const hh_options* opts, double delta_hat);
 
 /* Finish every queued and running request, then free all problems and stop the workers. */
 HH_API void hh_server_destroy(hh_server* s);

@@ -52,6 +52,13 @@ template <typename T> __device__ __forceinline__ Cx<T> fma_r(T s, Cx<T> b, Cx<T>
 template <typename T> __device__ __forceinline__ Cx<T> fma_c(Cx<T> c, Cx<T> b, Cx<T> a) {
     return {fma(c.re, b.re, fma(-c.im, b.im, a.re)), fma(c.re, b.im, fma(c.im, b.re, a.im))};
 }
+// a / 2 rounded on its own.  The intrinsics are never fused into a following add, so every kernel
+// rounds the interpolation and restriction halves the same way: for subnormal values a / 2 is
+// inexact, and a contraction of "x + a / 2" into one fused multiply-add in some kernels but not in
+// others would change the last bit.
+__device__ __forceinline__ float half_rn1(float a) { return __fmul_rn(0.5f, a); }
+__device__ __forceinline__ double half_rn1(double a) { return __dmul_rn(0.5, a); }
+template <typename T> __device__ __forceinline__ Cx<T> half_rn(Cx<T> a) { return {half_rn1(a.re), half_rn1(a.im)}; }
 template <typename T> __device__ __forceinline__ Cx<T> cinv(Cx<T> a) {
     T d = fma(a.re, a.re, a.im * a.im);
     T s = T(1) / d;

@@ -110,61 +110,14 @@ __device__ __forceinline__ void f_pass(const MArgs<T>& a, int strips, int chunks
 // nsw scaled-Jacobi sweeps from 0 on the coarsest level, one band of R rows per CTA job
 template <typename T, bool BATCH>
 __device__ __forceinline__ void coarse_pass(const MArgs<T>& a, int nsw, int R, int it, unsigned char* smem) {
-    const int nn = a.g.nn, n = a.g.n, Wd = nn + 2;
-    const int H = nsw > 1 ? nsw - 1 : 0;
-    const int rows_buf = R + 2 * H + 2;
-    const int buf = rows_buf * Wd;
-    vec2<T>* xs[2] = {reinterpret_cast<vec2<T>*>(smem), reinterpret_cast<vec2<T>*>(smem) + buf};
-    vec2<T>* bs = reinterpret_cast<vec2<T>*>(smem) + 2 * buf;
+    const int nn = a.g.nn;
     const int bands = (nn + R - 1) / R;
     const int jobs = bands * a.nb;
     for (int job = blockIdx.x; job < jobs; job += gridDim.x) {
         const int b = BATCH ? job / bands : 0;
         if (BATCH && loop_skipped(a, b, it)) continue;  // uniform over the CTA
-        const int r0 = (job - b * bands) * R, r1 = min(r0 + R, nn);
-        const int top = r0 - H - 1;  // grid row of buffer row 0
-        const PCoef<T>& c = BATCH ? a.pc[b] : a.c0;
-        const vec2<T>* bz = a.z + (long long)b * a.bs;
-        vec2<T>* y = a.y + (long long)b * a.bs;
-        // iterates start at 0 (and stay 0 outside the grid and at Dirichlet nodes); the right
-        // side of the band and its halo rows is staged once
-        for (int q = threadIdx.x; q < 3 * buf; q += blockDim.x) st<T>(xs[0], q, cx<T>(0, 0));
-        __syncthreads();
-        {
-            const int ja = max(r0 - H, 0), jb = min(r1 + H, nn);
-            for (int q = threadIdx.x; q < (jb - ja) * nn; q += blockDim.x) {
-                const int j = ja + q / nn, i = q - (q / nn) * nn;
-                st<T>(bs, (j - top) * Wd + i + 1, ld<T>(bz, (long long)j * nn + i));
-            }
-        }
-        __syncthreads();
-        int cur = 0;
-        for (int s = 1; s <= nsw; ++s) {
-            const int ext = nsw - s;  // rows beyond the band that later sweeps still read
-            const int ja = max(r0 - ext, 0), jb = min(r1 + ext, nn);
-            const vec2<T>* xin = xs[cur];
-            vec2<T>* xout = xs[cur ^ 1];
-            for (int q = threadIdx.x; q < (jb - ja) * nn; q += blockDim.x) {
-                const int j = ja + q / nn, i = q - (q / nn) * nn;
-                const bool vd = (i == 0 && a.g.dir[0]) || (i == n && a.g.dir[1]) || (j == 0 && a.g.dir[2]) ||
-                                (j == n && a.g.dir[3]);
-                if (vd) continue;
-                const int tx = i == 0 ? 0 : (i == n ? 2 : 1), ty = j == 0 ? 0 : (j == n ? 2 : 1);
-                const int cls = ty * 3 + tx;
-                const int kind = cls == 4 ? 8 : cls - (cls > 4);
-                const int pi = (j - top) * Wd + i + 1;
-                const Cx<T> bq = ld<T>(bs, pi);
-                const Cx<T> xv = s == 1 ? cmul(kind == 8 ? c.wdinv : c.bdinv[kind], bq)
-                                        : coarse_update2(c, xin, pi, Wd, kind, bq);
-                st<T>(xout, pi, xv);
-            }
-            __syncthreads();
-            cur ^= 1;
-        }
-        for (int q = threadIdx.x; q < (r1 - r0) * nn; q += blockDim.x) {
-            const int j = r0 + q / nn, i = q - (q / nn) * nn;
-            st<T>(y, (long long)j * nn + i, ld<T>(xs[cur], (j - top) * Wd + i + 1));
-        }
+        const int r0 = (job - b * bands) * R;
+        coarse_band2<T>(a, BATCH ? a.pc[b] : a.c0, b, r0, min(r0 + R, nn), nsw, smem);
         __syncthreads();  // before the next job overwrites the buffers
     }
 }
@@ -198,8 +151,7 @@ __global__ void __launch_bounds__(128) k_hss2p(const __grid_constant__ HssLoop2<
 
 template <typename T>
 size_t hss_loop2_smem(const GridDesc& gc, int nu_coarse, int rows) {
-    const int H = nu_coarse > 1 ? nu_coarse - 1 : 0;
-    return (size_t)3 * (rows + 2 * H + 2) * (gc.nn + 2) * sizeof(vec2<T>);
+    return band2_smem<T>(gc.nn, nu_coarse, rows);
 }
 
 template <typename T>

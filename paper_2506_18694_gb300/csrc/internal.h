@@ -277,6 +277,17 @@ int hss_loop2_ctas(bool batch, size_t smem);
 template <typename T>
 cudaError_t launch_hss_loop2(const HssLoop2<T>& P, int ctas, size_t smem, cudaStream_t s);
 
+// ---- packed passes over problems of different grids (pack.cu) ----
+// One launch of pass `kind` for nm problems: 0 level-0 HSS right side + two sweeps + restriction,
+// 1 two sweeps from 0 + restriction on `level`, 2 the coarsest level (bands; smem bytes of shared
+// memory), 3 prolongation + two sweeps on `level`.  plans[m]: problem m's loop plan (nb = 1);
+// starts: prefix of the problems' tiles (warp tiles; bands for kind 2), total = starts[nm].
+template <typename T>
+cudaError_t prepare_pack();
+template <typename T>
+cudaError_t launch_pack_pass(int kind, const HssLoop2<T>* plans, const int* starts, int nm, int total, int level,
+                             int it, const int* live, size_t smem, cudaStream_t s);
+
 // ---- GMRES smoother with a Jacobi preconditioner (gsmooth.cu) ----
 // Level vectors of nb problems (problem b at offset b * N); the Krylov basis holds vector i
 // of problem b at V + i * ld + b * N.  Sums in FP64 over a fixed block grid (gs_blocks(N)), so

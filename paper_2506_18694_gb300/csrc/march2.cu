@@ -146,7 +146,7 @@ __device__ __forceinline__ void tile_compute(const MArgs<T>& a, const PCoef<T>& 
                         st<T>(v.y, (long long)J * (nc + 1) + I, cm ? cx<T>(0, 0) : acc);
                     }
                 }
-                acc = T(0.5) * rr;
+                acc = half_rn(rr);
             }
             continue;
         }

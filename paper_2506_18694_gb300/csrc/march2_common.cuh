@@ -86,14 +86,14 @@ __device__ __forceinline__ void prolong_rows(const MArgs<T>& a, const VPtrs<T>& 
         const Cx<T> c0 = (jv || v0) ? cx<T>(0, 0) : ld<T>(v.ec, row + I);
         Cx<T> c1 = shfl_dn(c0);
         if (lane == 31) c1 = (jv || v1) ? cx<T>(0, 0) : ld<T>(v.ec, row + I1);
-        ex[q] = odd ? T(0.5) * (c0 + c1) : c0;
+        ex[q] = odd ? half_rn(c0 + c1) : c0;
     }
 #pragma unroll
     for (int t = 0; t < NR; ++t) {
         const int r = rfirst + t;
         const long long p = (long long)clampi(r, 0, n) * a.g.nn + ic;
         const int lq = (P + t) >> 1;
-        const Cx<T> e = ((P + t) & 1) == 0 ? ex[lq] : T(0.5) * (ex[lq] + ex[lq + 1]);
+        const Cx<T> e = ((P + t) & 1) == 0 ? ex[lq] : half_rn(ex[lq] + ex[lq + 1]);
         out[t] = (cvoid || row_void(a, r)) ? cx<T>(0, 0) : ld<T>(v.x, p) + e;
     }
 }
@@ -369,7 +369,7 @@ __device__ __forceinline__ void rr_tile(const MArgs<T>& a, int b, int strip, int
                     st<T>(yc, (long long)J * (nc + 1) + I, cm ? cx<T>(0, 0) : acc);
                 }
             }
-            acc = T(0.5) * rr;
+            acc = half_rn(rr);
         }
     }
 }
@@ -397,6 +397,70 @@ __device__ __forceinline__ Cx<T> coarse_update2(const PCoef<T>& c, const vec2<T>
         ax = fma_c(c.bw[kind][3], dg, fma_c(c.bw[kind][2], vy, fma_c(c.bw[kind][1], hx, cmul(c.bw[kind][0], f0))));
     }
     return fma_c(dinv, bq - ax, f0);
+}
+
+
+// The coarsest-level solve on one band of rows r0 .. r1 - 1 of problem b: nsw scaled-Jacobi sweeps
+// from x = 0 with coefficients c, the result written to a.y.  The band and a halo of nsw - 1 rows
+// on each side are staged in shared memory (smem: hss_band2_smem bytes) and every sweep runs
+// there, the halo rows recomputed instead of exchanged, so that one CTA needs nothing from any
+// other; each node's arithmetic is that of coarse_update2 (the one-sweep kernels' arithmetic).
+template <typename T>
+__host__ __device__ __forceinline__ size_t band2_smem(int nn, int nsw, int R) {
+    const int H = nsw > 1 ? nsw - 1 : 0;
+    return (size_t)3 * (R + 2 * H + 2) * (nn + 2) * sizeof(vec2<T>);
+}
+
+template <typename T>
+__device__ __forceinline__ void coarse_band2(const MArgs<T>& a, const PCoef<T>& c, int b, int r0, int r1, int nsw,
+                                             unsigned char* smem) {
+    const int nn = a.g.nn, n = a.g.n, Wd = nn + 2;
+    const int H = nsw > 1 ? nsw - 1 : 0;
+    const int buf = (r1 - r0 + 2 * H + 2) * Wd;
+    vec2<T>* xs[2] = {reinterpret_cast<vec2<T>*>(smem), reinterpret_cast<vec2<T>*>(smem) + buf};
+    vec2<T>* bs = reinterpret_cast<vec2<T>*>(smem) + 2 * buf;
+    const int top = r0 - H - 1;  // grid row of buffer row 0
+    const vec2<T>* bz = a.z + (long long)b * a.bs;
+    vec2<T>* y = a.y + (long long)b * a.bs;
+    // iterates start at 0 (and stay 0 outside the grid and at Dirichlet nodes); the right side
+    // of the band and its halo rows is staged once
+    for (int q = threadIdx.x; q < 3 * buf; q += blockDim.x) st<T>(xs[0], q, cx<T>(0, 0));
+    __syncthreads();
+    {
+        const int ja = max(r0 - H, 0), jb = min(r1 + H, nn);
+        for (int q = threadIdx.x; q < (jb - ja) * nn; q += blockDim.x) {
+            const int j = ja + q / nn, i = q - (q / nn) * nn;
+            st<T>(bs, (j - top) * Wd + i + 1, ld<T>(bz, (long long)j * nn + i));
+        }
+    }
+    __syncthreads();
+    int cur = 0;
+    for (int s = 1; s <= nsw; ++s) {
+        const int ext = nsw - s;  // rows beyond the band that later sweeps still read
+        const int ja = max(r0 - ext, 0), jb = min(r1 + ext, nn);
+        const vec2<T>* xin = xs[cur];
+        vec2<T>* xout = xs[cur ^ 1];
+        for (int q = threadIdx.x; q < (jb - ja) * nn; q += blockDim.x) {
+            const int j = ja + q / nn, i = q - (q / nn) * nn;
+            const bool vd = (i == 0 && a.g.dir[0]) || (i == n && a.g.dir[1]) || (j == 0 && a.g.dir[2]) ||
+                            (j == n && a.g.dir[3]);
+            if (vd) continue;
+            const int tx = i == 0 ? 0 : (i == n ? 2 : 1), ty = j == 0 ? 0 : (j == n ? 2 : 1);
+            const int cls = ty * 3 + tx;
+            const int kind = cls == 4 ? 8 : cls - (cls > 4);
+            const int pi = (j - top) * Wd + i + 1;
+            const Cx<T> bq = ld<T>(bs, pi);
+            const Cx<T> xv = s == 1 ? cmul(kind == 8 ? c.wdinv : c.bdinv[kind], bq)
+                                    : coarse_update2(c, xin, pi, Wd, kind, bq);
+            st<T>(xout, pi, xv);
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    for (int q = threadIdx.x; q < (r1 - r0) * nn; q += blockDim.x) {
+        const int j = r0 + q / nn, i = q - (q / nn) * nn;
+        st<T>(y, (long long)j * nn + i, ld<T>(xs[cur], (j - top) * Wd + i + 1));
+    }
 }
 
 }  // namespace hh

@@ -759,6 +759,9 @@ struct MG {
                 a.y = x;
                 const auto& tab = p->tune[sizeof(T) == 4 ? HH_C64 : HH_C128];
                 a.tile_rows = l < (int)tab.size() ? tab[l][kCoarseMode][0] : 0;
+                a.tile_form = l < (int)tab.size() ? tab[l][kCoarseMode][1] : 0;
+                if (a.tile_rows == 0 && p->o.coarse_kernel == 1) a.tile_rows = hh::coarse_cluster_size();
+                if (a.tile_rows == 0 && p->o.coarse_kernel == 2) a.tile_form = 3;
                 HH_LAUNCH(hh::launch_coarse_solve<T>(a, p->o.nu_coarse, s));
             } else {
                 HH_TRY(smooth_from_zero(l, b, p->o.nu_coarse, &x));
@@ -1403,6 +1406,43 @@ hh_status fetch(hh_problem* p) {
 
 bool finite(double v) { return std::isfinite(v); }
 
+// Column j of the Hessenberg matrix (H[i] for i <= j + 1, stored with stride 1): apply the j
+// earlier Givens rotations, compute rotation j that zeroes H[j + 1] and apply it to H and to the
+// rotated right side g.  Shared by every FGMRES driver, so that their arithmetic is one code.
+void givens_column(zc* H, double* cs, zc* sn, zc* g, int j) {
+    for (int i = 0; i < j; ++i) {
+        const zc t = cs[i] * H[i] + sn[i] * H[i + 1];
+        H[i + 1] = -std::conj(sn[i]) * H[i] + cs[i] * H[i + 1];
+        H[i] = t;
+    }
+    const zc h1 = H[j], h2 = H[j + 1];
+    const double den = std::hypot(std::abs(h1), std::abs(h2));
+    if (std::abs(h1) == 0.0) {
+        cs[j] = 0.0;
+        sn[j] = 1.0;
+    } else {
+        cs[j] = std::abs(h1) / den;
+        sn[j] = (h1 / std::abs(h1)) * std::conj(h2) / den;
+    }
+    H[j] = cs[j] * h1 + sn[j] * h2;
+    H[j + 1] = 0.0;
+    g[j + 1] = -std::conj(sn[j]) * g[j];
+    g[j] = cs[j] * g[j];
+}
+
+// y (m entries) = R^{-1} g over the first jend columns (R: the rotated Hessenberg matrix, column j
+// at Hm + j * (m + 1)), zero beyond; false if a value is not finite.
+bool back_substitute(const zc* Hm, int m, const zc* g, int jend, zc* y) {
+    std::fill(y, y + m, zc(0));
+    for (int i = jend - 1; i >= 0; --i) {
+        zc acc = g[i];
+        for (int c = i + 1; c < jend; ++c) acc -= Hm[(size_t)c * (m + 1) + i] * y[c];
+        y[i] = acc / Hm[(size_t)i * (m + 1) + i];
+        if (!finite(y[i].real()) || !finite(y[i].imag())) return false;
+    }
+    return true;
+}
+
 // Flexible GMRES(m) with classical Gram-Schmidt applied twice (CGS2) and Givens rotations,
 // the nb problems in lockstep: a problem that converges leaves the launches at once.
 hh_status fgmres(hh_problem* p, double tol, hh_info* info) {
@@ -1434,6 +1474,9 @@ hh_status fgmres(hh_problem* p, double tol, hh_info* info) {
         if (bnorm[b] == 0.0) HH_CUDA(cudaMemsetAsync(p->x + (long long)b * N, 0, (size_t)N * 16, p->s));
     std::vector<zc> Hm((size_t)nb * (m + 1) * m), g((size_t)nb * (m + 1)), sn((size_t)nb * m), y((size_t)nb * m);
     std::vector<double> cs((size_t)nb * m);
+    // true residual at the end of every restart cycle, per problem (stall detection)
+    std::vector<std::vector<double>> cycle_rel(nb);
+    for (int b = 0; b < nb; ++b) cycle_rel[b].push_back(rel[b]);
     std::vector<int> jend(nb, 0);
     auto Hc = [&](int b, int i, int j) -> zc& { return Hm[((size_t)b * m + j) * (m + 1) + i]; };
     // Krylov layout [vector][problem][node]: basis vector j of the whole batch is one block
@@ -1479,27 +1522,8 @@ hh_status fgmres(hh_problem* p, double tol, hh_info* info) {
                 const double hn = std::sqrt(H(b, nrm).x);
                 if (!finite(hn)) return fail(HH_ERR_NONFINITE, "Arnoldi produced a non-finite value");
                 Hc(b, j + 1, j) = hn;
-                double* csb = &cs[(size_t)b * m];
-                zc* snb = &sn[(size_t)b * m];
                 zc* gb = &g[(size_t)b * (m + 1)];
-                for (int i = 0; i < j; ++i) {
-                    const zc t = csb[i] * Hc(b, i, j) + snb[i] * Hc(b, i + 1, j);
-                    Hc(b, i + 1, j) = -std::conj(snb[i]) * Hc(b, i, j) + csb[i] * Hc(b, i + 1, j);
-                    Hc(b, i, j) = t;
-                }
-                const zc h1 = Hc(b, j, j), h2 = Hc(b, j + 1, j);
-                const double den = std::hypot(std::abs(h1), std::abs(h2));
-                if (std::abs(h1) == 0.0) {
-                    csb[j] = 0.0;
-                    snb[j] = 1.0;
-                } else {
-                    csb[j] = std::abs(h1) / den;
-                    snb[j] = (h1 / std::abs(h1)) * std::conj(h2) / den;
-                }
-                Hc(b, j, j) = csb[j] * h1 + snb[j] * h2;
-                Hc(b, j + 1, j) = 0.0;
-                gb[j + 1] = -std::conj(snb[j]) * gb[j];
-                gb[j] = csb[j] * gb[j];
+                givens_column(&Hc(b, 0, j), &cs[(size_t)b * m], &sn[(size_t)b * m], gb, j);
                 info[b].outer_its += 1;
                 jend[b] = j + 1;
                 if (std::abs(gb[j + 1]) / bnorm[b] <= tol || info[b].outer_its >= p->o.max_outer || hn == 0.0) {
@@ -1516,14 +1540,8 @@ hh_status fgmres(hh_problem* p, double tol, hh_info* info) {
             ran[b] = jend[b] > 0;
             jmax = std::max(jmax, jend[b]);
             zc* yb = &y[(size_t)b * m];
-            std::fill(yb, yb + m, zc(0));
-            for (int i = jend[b] - 1; i >= 0; --i) {
-                zc acc = g[(size_t)b * (m + 1) + i];
-                for (int c = i + 1; c < jend[b]; ++c) acc -= Hc(b, i, c) * yb[c];
-                yb[i] = acc / Hc(b, i, i);
-                if (!finite(yb[i].real()) || !finite(yb[i].imag()))
-                    return fail(HH_ERR_NONFINITE, "least-squares update is not finite");
-            }
+            if (!back_substitute(&Hc(b, 0, 0), m, &g[(size_t)b * (m + 1)], jend[b], yb))
+                return fail(HH_ERR_NONFINITE, "least-squares update is not finite");
             for (int i = 0; i < m; ++i) p->h_host[(size_t)b * m + i] = make_double2(yb[i].real(), yb[i].imag());
         }
         HH_CUDA(cudaMemcpyAsync(p->ybuf, p->h_host, (size_t)nb * m * 16, cudaMemcpyHostToDevice, p->s));
@@ -1539,6 +1557,10 @@ hh_status fgmres(hh_problem* p, double tol, hh_info* info) {
             if (!finite(beta[b])) return fail(HH_ERR_NONFINITE, "residual is not finite");
             rel[b] = beta[b] / bnorm[b];
             if (rel[b] <= tol || info[b].outer_its >= p->o.max_outer) solving[b] = 0;
+            // stalled: stall_cycles restart cycles did not halve the true residual
+            cycle_rel[b].push_back(rel[b]);
+            const int sc = p->o.stall_cycles, nc = (int)cycle_rel[b].size() - 1;
+            if (sc > 0 && nc >= sc && rel[b] > 0.5 * cycle_rel[b][nc - sc]) solving[b] = 0;
         }
     }
     HH_TRY(set_active(p, nullptr));
@@ -1663,6 +1685,8 @@ hh_status check_args(const hh_grid* grid, int nb, const double* k, const double*
         return fail(HH_ERR_INVALID, "outer must be HH_OUTER_FGMRES or HH_OUTER_RICHARDSON");
     if (o->persistent < 0 || o->persistent > 2) return fail(HH_ERR_INVALID, "persistent must be 0, 1 or 2");
     if (o->sync_spin_limit < 0) return fail(HH_ERR_INVALID, "sync_spin_limit < 0");
+    if (o->stall_cycles < 0) return fail(HH_ERR_INVALID, "stall_cycles < 0");
+    if (o->coarse_kernel < 0 || o->coarse_kernel > 2) return fail(HH_ERR_INVALID, "coarse_kernel must be 0, 1 or 2");
     if (!bc) return fail(HH_ERR_INVALID, "null bc");
     for (int s = 0; s < 2 * grid->dim; ++s)
         if (bc[s] != HH_BC_SOMMERFELD && bc[s] != HH_BC_DIRICHLET) return fail(HH_ERR_INVALID, "bad boundary tag");
@@ -1689,6 +1713,341 @@ void op_role(int op, bool* ok, int* role) {
         case HH_OP_BHAT: *role = R_BHAT; break;
         default: *ok = false; *role = 0;
     }
+}
+
+}  // namespace
+
+// ====================================================================== packs
+// A pack runs the FGMRES solves of several problems of DIFFERENT grids side by side: every
+// outer iteration of every member is the same sequence of operations as in its own solve
+// (fgmres above, one problem), on the member's own stream, except that the preconditioner
+// applications of all members that need one in the same round run as one sequence of packed
+// launches (pack.cu): one launch per pass of the V-cycle covers the tiles of every member, so
+// small problems fill the GPU together instead of one after the other.  Members join and leave
+// between rounds (continuous batching); each result equals the member's own solve bit for bit.
+namespace {
+
+enum PackState {
+    PK_FREE = 0,     // empty slot
+    PK_BNORM,        // waiting for ||b||
+    PK_RES0,         // waiting for the initial residual norm
+    PK_NEED_ITER,    // ready for iteration j (needs a preconditioner application)
+    PK_ITER,         // waiting for iteration j's Arnoldi sums
+    PK_CYCLE_END,    // waiting for the true residual after the update of x
+    PK_DONE          // finished: result written, waiting to be taken
+};
+
+struct PackMember {
+    hh_problem* p = nullptr;
+    int state = PK_FREE;
+    int io = 0;  // 0: device load vector in / device u out; 1: host load vector; 2: host nodal source
+    void* u = nullptr;
+    double tol = 0.0;
+    int j = 0, jend = 0;
+    double bnorm = 0.0, beta = 0.0, rel = 0.0;
+    std::vector<zc> Hm, g, sn, y;
+    std::vector<double> cs, cycle_rel;
+    hh_info info{};
+    hh_status st = HH_OK;
+    std::string err;
+    std::chrono::steady_clock::time_point t0;
+};
+
+// a problem the packed passes can run: 2D primal, one problem, V(2,2) scaled-Jacobi cycles with
+// one cycle per HSS step, complex64 cycles, FGMRES
+bool packable(const hh_problem* p, int levels, std::string* why) {
+    const hh_options& o = p->o;
+    if (p->grid.dim != 2 || p->nb != 1 || p->mixed) return *why = "packs hold 2D primal problems of one member each", false;
+    if (o.smoother != HH_SMOOTH_JACOBI || o.cycle_gamma != 1 || o.cycles_per_hss != 1 || o.nu_pre != 2 ||
+        o.nu_post != 2)
+        return *why = "packs run V(2,2) scaled-Jacobi cycles, one per HSS step", false;
+    if (o.precision != HH_C64 || o.outer != HH_OUTER_FGMRES) return *why = "packs run complex64 cycles inside FGMRES", false;
+    if (o.levels < 2 || o.levels > hh::kPMaxLevels) return *why = "packs need 2..5 levels", false;
+    if (levels && o.levels != levels) return *why = "every member of a pack has the same number of levels", false;
+    return true;
+}
+
+int pack_passes(int L) { return 2 * L - 1; }
+// kind and level of pass q (see launch_pack_pass)
+void pass_kind(int L, int q, int* kind, int* level) {
+    if (q == 0) *kind = 0, *level = 0;
+    else if (q < L - 1) *kind = 1, *level = q;
+    else if (q == L - 1) *kind = 2, *level = L - 1;
+    else *kind = 3, *level = 2 * L - 2 - q;
+}
+int pass_tiles(const hh::HssLoop2<float>& P, const hh_problem* p, int kind, int level) {
+    switch (kind) {
+        case 0:
+        case 1: return P.pre_strips[level] * P.pre_chunks[level];
+        case 2: return (p->lv[level].nn + P.coarse_rows - 1) / P.coarse_rows;
+        default: return P.post_strips[level] * P.post_chunks[level];
+    }
+}
+
+hh_status enqueue_fetch(hh_problem* p) {
+    HH_CUDA(cudaMemcpyAsync(p->h_host, p->hbuf, (size_t)hstride(p) * sizeof(double2), cudaMemcpyDeviceToHost, p->s));
+    return HH_OK;
+}
+
+}  // namespace
+
+struct hh_pack {
+    int device = 0;
+    int capacity = 0;
+    int levels = 0;
+    cudaStream_t s = nullptr;     // the packed preconditioner launches
+    cudaEvent_t ev_prec = nullptr;
+    std::vector<cudaEvent_t> ev_m;
+    std::vector<PackMember> m;
+    hh::HssLoop2<float>* d_plans = nullptr;
+    std::vector<unsigned char> h_plans;
+    int* d_starts = nullptr;      // pass q: capacity + 1 prefix entries at q * (capacity + 1)
+    int* d_live = nullptr;
+    int* h_live = nullptr;        // pinned
+    std::vector<int> totals;
+    size_t coarse_smem = 0;
+    int maxsteps = 0;
+    cudaGraphExec_t graph = nullptr;
+    long long graph_kernels = 0;
+    bool dirty = true;            // membership changed: tables and graph to rebuild
+};
+
+namespace {
+
+hh_status pack_fail(PackMember& x, hh_status st) {
+    x.st = st;
+    x.err = hh_last_error();
+    x.info.rel_residual = NAN;
+    x.state = PK_DONE;
+    return HH_OK;
+}
+
+// the member's result: u and info, then PK_DONE
+hh_status pack_finish(PackMember& x) {
+    hh_problem* p = x.p;
+    const size_t bytes = (size_t)p->N * 16;
+    if (x.io == 0) HH_CUDA(cudaMemcpyAsync(x.u, p->x, bytes, cudaMemcpyDeviceToDevice, p->s));
+    else HH_CUDA(cudaMemcpyAsync(x.u, p->x, bytes, cudaMemcpyDeviceToHost, p->s));
+    HH_CUDA(cudaStreamSynchronize(p->s));
+    x.info.rel_residual = x.rel;
+    x.info.device_bytes = p->bytes;
+    x.info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - x.t0).count();
+    x.st = x.rel <= x.tol ? HH_OK : HH_NOT_CONVERGED;
+    x.state = PK_DONE;
+    return HH_OK;
+}
+
+// start a restart cycle: V_0 = r / beta (the residual norm is still in hbuf)
+hh_status pack_cycle(PackMember& x) {
+    hh_problem* p = x.p;
+    const int m = p->o.restart, nrm = 2 * (m + 1);
+    HH_CUDA(cudaMemcpyAsync(p->V, p->r, (size_t)p->N * 16, cudaMemcpyDeviceToDevice, p->s));
+    HH_CUDA(hh::launch_scale_by_rnorm(p->V, p->hbuf + nrm, p->N, hh::KBatch{1, p->N, p->N, hstride(p), nullptr}, p->s));
+    std::fill(x.g.begin(), x.g.end(), zc(0));
+    x.g[0] = x.beta;
+    x.j = 0;
+    x.jend = 0;
+    x.state = PK_NEED_ITER;
+    return HH_OK;
+}
+
+// x += Z y, then the true residual and its norm
+hh_status pack_cycle_end(PackMember& x) {
+    hh_problem* p = x.p;
+    const int m = p->o.restart, nrm = 2 * (m + 1);
+    if (!back_substitute(x.Hm.data(), m, x.g.data(), x.jend, x.y.data()))
+        return pack_fail(x, fail(HH_ERR_NONFINITE, "least-squares update is not finite"));
+    for (int i = 0; i < m; ++i) p->h_host[i] = make_double2(x.y[i].real(), x.y[i].imag());
+    HH_CUDA(cudaMemcpyAsync(p->ybuf, p->h_host, (size_t)m * 16, cudaMemcpyHostToDevice, p->s));
+    if (x.jend > 0)
+        HH_CUDA(hh::launch_multi_axpy(p->x, p->Z, p->N, x.jend, p->ybuf, 1.0, p->N, hh::KBatch{1, p->N, p->N, m, nullptr},
+                                      p->s));
+    HH_TRY(residual_B(p, p->x, p->r));
+    HH_TRY(norm2_dev(p, p->r, nrm));
+    HH_TRY(enqueue_fetch(p));
+    x.state = PK_CYCLE_END;
+    return HH_OK;
+}
+
+// what a member does after the round's synchronisation
+hh_status pack_after_sync(PackMember& x) {
+    hh_problem* p = x.p;
+    const int m = p->o.restart, nrm = 2 * (m + 1);
+    auto H = [&](int i) -> double2& { return p->h_host[i]; };
+    auto Hc = [&](int i, int j) -> zc& { return x.Hm[(size_t)j * (m + 1) + i]; };
+    switch (x.state) {
+        case PK_BNORM:
+            x.bnorm = std::sqrt(H(nrm).x);
+            if (!finite(x.bnorm)) return pack_fail(x, fail(HH_ERR_NONFINITE, "right-hand side is not finite"));
+            HH_TRY(residual_B(p, p->x, p->r));
+            HH_TRY(norm2_dev(p, p->r, nrm));
+            HH_TRY(enqueue_fetch(p));
+            x.state = PK_RES0;
+            return HH_OK;
+        case PK_RES0:
+            x.beta = std::sqrt(H(nrm).x);
+            if (!finite(x.beta)) return pack_fail(x, fail(HH_ERR_NONFINITE, "initial residual is not finite"));
+            x.rel = x.bnorm > 0 ? x.beta / x.bnorm : 0.0;
+            x.cycle_rel.assign(1, x.rel);
+            if (x.bnorm == 0.0) HH_CUDA(cudaMemsetAsync(p->x, 0, (size_t)p->N * 16, p->s));
+            if (x.bnorm == 0.0 || x.rel <= x.tol || p->o.max_outer == 0) return pack_finish(x);
+            return pack_cycle(x);
+        case PK_ITER: {
+            const int j = x.j;
+            for (int i = 0; i <= j; ++i) Hc(i, j) = zc(H(i).x + H(m + 1 + i).x, H(i).y + H(m + 1 + i).y);
+            const double hn = std::sqrt(H(nrm).x);
+            if (!finite(hn)) return pack_fail(x, fail(HH_ERR_NONFINITE, "Arnoldi produced a non-finite value"));
+            Hc(j + 1, j) = hn;
+            givens_column(&Hc(0, j), x.cs.data(), x.sn.data(), x.g.data(), j);
+            x.info.outer_its += 1;
+            x.jend = j + 1;
+            const bool leave = std::abs(x.g[j + 1]) / x.bnorm <= x.tol || x.info.outer_its >= p->o.max_outer || hn == 0.0;
+            if (leave || j + 1 == m) return pack_cycle_end(x);
+            x.j = j + 1;
+            x.state = PK_NEED_ITER;
+            return HH_OK;
+        }
+        case PK_CYCLE_END: {
+            x.beta = std::sqrt(H(nrm).x);
+            if (!finite(x.beta)) return pack_fail(x, fail(HH_ERR_NONFINITE, "residual is not finite"));
+            x.rel = x.beta / x.bnorm;
+            bool stop = x.rel <= x.tol || x.info.outer_its >= p->o.max_outer;
+            x.cycle_rel.push_back(x.rel);
+            const int sc = p->o.stall_cycles, nc = (int)x.cycle_rel.size() - 1;
+            if (sc > 0 && nc >= sc && x.rel > 0.5 * x.cycle_rel[nc - sc]) stop = true;
+            if (stop) return pack_finish(x);
+            return pack_cycle(x);
+        }
+        default: return HH_OK;
+    }
+}
+
+// member tables, tile prefixes and the graph of one packed preconditioner application
+hh_status pack_rebuild(hh_pack* k) {
+    const int cap = k->capacity, L = k->levels, Q = pack_passes(L);
+    k->h_plans.assign((size_t)cap * sizeof(hh::HssLoop2<float>), 0);
+    auto* plans = reinterpret_cast<hh::HssLoop2<float>*>(k->h_plans.data());
+    std::vector<int> starts((size_t)Q * (cap + 1), 0);
+    k->totals.assign(Q, 0);
+    k->coarse_smem = 0;
+    k->maxsteps = 0;
+    for (int i = 0; i < cap; ++i) {
+        PackMember& x = k->m[i];
+        const bool in = x.state != PK_FREE && x.state != PK_DONE;
+        if (in) {
+            MG<float> mg = make_mg<float>(x.p, HH_C64, x.p->s);
+            mg.loop_plan(&plans[i]);
+            k->maxsteps = std::max(k->maxsteps, plans[i].nsteps);
+            k->coarse_smem = std::max(k->coarse_smem, hh::hss_loop2_smem<float>(x.p->lv[L - 1], x.p->o.nu_coarse,
+                                                                               plans[i].coarse_rows));
+        }
+        for (int q = 0; q < Q; ++q) {
+            int kind, level;
+            pass_kind(L, q, &kind, &level);
+            const int t = in ? pass_tiles(plans[i], x.p, kind, level) : 0;
+            starts[(size_t)q * (cap + 1) + i + 1] = starts[(size_t)q * (cap + 1) + i] + t;
+        }
+    }
+    for (int q = 0; q < Q; ++q) k->totals[q] = starts[(size_t)q * (cap + 1) + cap];
+    if (k->coarse_smem > hh::kLoopSmemMax) return fail(HH_ERR_INVALID, "a member's coarsest level is too wide to pack");
+    HH_CUDA(cudaMemcpyAsync(k->d_plans, k->h_plans.data(), k->h_plans.size(), cudaMemcpyHostToDevice, k->s));
+    HH_CUDA(cudaMemcpyAsync(k->d_starts, starts.data(), starts.size() * sizeof(int), cudaMemcpyHostToDevice, k->s));
+    HH_CUDA(cudaStreamSynchronize(k->s));
+    if (k->graph) {
+        cudaGraphExecDestroy(k->graph);
+        k->graph = nullptr;
+    }
+    if (k->maxsteps > 0) {
+        cudaGraph_t g;
+        const long long k0 = hh::g_kernel_launches;
+        HH_CUDA(cudaStreamBeginCapture(k->s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int it = 0; it < k->maxsteps && e == cudaSuccess; ++it)
+            for (int q = 0; q < Q && e == cudaSuccess; ++q) {
+                int kind, level;
+                pass_kind(L, q, &kind, &level);
+                e = hh::launch_pack_pass<float>(kind, k->d_plans, k->d_starts + (size_t)q * (cap + 1), cap, k->totals[q],
+                                                level, it, k->d_live, k->coarse_smem, k->s);
+            }
+        cudaError_t ec = cudaStreamEndCapture(k->s, &g);
+        if (e != cudaSuccess) {
+            if (ec == cudaSuccess) cudaGraphDestroy(g);
+            return fail(HH_ERR_CUDA, std::string("packed launch: ") + cudaGetErrorString(e));
+        }
+        HH_CUDA(ec);
+        cudaError_t ei = cudaGraphInstantiate(&k->graph, g, 0);
+        cudaGraphDestroy(g);
+        HH_CUDA(ei);
+        k->graph_kernels = hh::g_kernel_launches - k0;
+        hh::g_kernel_launches = k0;
+    }
+    k->dirty = false;
+    return HH_OK;
+}
+
+// one round: every member advances to its next synchronisation point
+hh_status pack_round(hh_pack* k) {
+    hh::g_use_pdl = 1;
+    if (k->dirty) HH_TRY(pack_rebuild(k));
+    const int cap = k->capacity;
+    bool any = false;
+    for (int i = 0; i < cap; ++i) {
+        PackMember& x = k->m[i];
+        k->h_live[i] = 0;
+        if (x.state != PK_NEED_ITER) continue;
+        hh_problem* p = x.p;
+        Hier& H = p->hier[HH_C64];
+        HH_LAUNCH(hh::launch_cast_d2f(p->V + (long long)x.j * p->N, (float2*)H.r_lo, p->N, p->s));
+        HH_CUDA(cudaEventRecord(k->ev_m[i], p->s));
+        HH_CUDA(cudaStreamWaitEvent(k->s, k->ev_m[i], 0));
+        k->h_live[i] = 1;
+        any = true;
+    }
+    if (any) {
+        HH_CUDA(cudaMemcpyAsync(k->d_live, k->h_live, sizeof(int) * cap, cudaMemcpyHostToDevice, k->s));
+        if (k->graph) HH_CUDA(cudaGraphLaunch(k->graph, k->s));
+        HH_CUDA(cudaEventRecord(k->ev_prec, k->s));
+    }
+    for (int i = 0; i < cap; ++i) {
+        PackMember& x = k->m[i];
+        if (x.state != PK_NEED_ITER) continue;
+        hh_problem* p = x.p;
+        Hier& H = p->hier[HH_C64];
+        const int m = p->o.restart, nrm = 2 * (m + 1);
+        HH_CUDA(cudaStreamWaitEvent(p->s, k->ev_prec, 0));
+        double2* zj = p->Z + (long long)x.j * p->N;
+        double2* w = p->V + (long long)(x.j + 1) * p->N;
+        HH_LAUNCH(hh::launch_gather_c128<float>((const float2* const*)H.usrc, zj, p->lv[0].N, 1, nullptr, p->s));
+        x.info.hss_its += p->nhss[0];
+        x.info.vcycles += p->nhss[0];
+        HH_TRY(apply_B(p, zj, w));
+        const hh::KBatch kb{1, p->N, p->N, hstride(p), nullptr};
+        double2* hA = p->hbuf;
+        double2* hB = p->hbuf + (m + 1);
+        HH_CUDA(hh::launch_multidot(p->V, p->N, x.j + 1, w, p->N, p->partials, hA, kb, p->s));
+        HH_CUDA(hh::launch_multi_axpy(w, p->V, p->N, x.j + 1, hA, -1.0, p->N, kb, p->s));
+        HH_CUDA(hh::launch_multidot(p->V, p->N, x.j + 1, w, p->N, p->partials, hB, kb, p->s));
+        HH_CUDA(hh::launch_multi_axpy(w, p->V, p->N, x.j + 1, hB, -1.0, p->N, kb, p->s));
+        HH_CUDA(hh::launch_multidot(w, 0, 1, w, p->N, p->partials, p->hbuf + nrm, kb, p->s));
+        HH_CUDA(hh::launch_scale_by_rnorm(w, p->hbuf + nrm, p->N, kb, p->s));
+        HH_TRY(enqueue_fetch(p));
+        x.state = PK_ITER;
+    }
+    if (any) HH_CUDA(cudaStreamSynchronize(k->s));
+    for (int i = 0; i < cap; ++i) {
+        PackMember& x = k->m[i];
+        if (x.state == PK_FREE || x.state == PK_DONE) continue;
+        cudaError_t e = cudaStreamSynchronize(x.p->s);
+        if (e != cudaSuccess) {
+            pack_fail(x, fail(HH_ERR_CUDA, cudaGetErrorString(e)));
+            k->dirty = true;
+            continue;
+        }
+        const hh_status st = pack_after_sync(x);
+        if (st != HH_OK) pack_fail(x, st);
+        if (x.state == PK_DONE) k->dirty = true;
+    }
+    return HH_OK;
 }
 
 }  // namespace
@@ -1721,6 +2080,8 @@ void hh_options_default(hh_options* o) {
     o->formulation = HH_FORM_PRIMAL;
     o->persistent = 0;
     o->sync_spin_limit = 0;
+    o->stall_cycles = 0;
+    o->coarse_kernel = 0;
 }
 
 size_t hh_footprint_batch_bytes(const hh_grid* grid, const hh_options* o, int nb) {
@@ -2138,5 +2499,149 @@ const char* hh_status_string(hh_status s) {
 }
 
 const char* hh_last_error(void) { return g_last_error.c_str(); }
+
+hh_status hh_pack_create(int capacity, hh_pack** out) {
+    if (!out) return fail(HH_ERR_INVALID, "null out");
+    *out = nullptr;
+    if (capacity < 1 || capacity > 256) return fail(HH_ERR_INVALID, "capacity must be in 1..256");
+    hh_pack* k = new hh_pack();
+    cudaGetDevice(&k->device);
+    k->capacity = capacity;
+    k->m.resize(capacity);
+    k->ev_m.assign(capacity, nullptr);
+    auto bail = [&](hh_status s) {
+        hh_pack_destroy(k);
+        return s;
+    };
+    if (cudaStreamCreateWithFlags(&k->s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&k->ev_prec, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(HH_ERR_CUDA, "stream/event creation failed"));
+    for (int i = 0; i < capacity; ++i)
+        if (cudaEventCreateWithFlags(&k->ev_m[i], cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(HH_ERR_CUDA, "event creation failed"));
+    const size_t Q = 2 * hh::kPMaxLevels - 1;
+    if (cudaMalloc((void**)&k->d_plans, (size_t)capacity * sizeof(hh::HssLoop2<float>)) != cudaSuccess ||
+        cudaMalloc((void**)&k->d_starts, Q * (capacity + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&k->d_live, capacity * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&k->h_live, capacity * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(HH_ERR_OOM, "pack allocation failed"));
+    }
+    if (hh::prepare_pack<float>() != cudaSuccess) return bail(fail(HH_ERR_CUDA, "pack kernel set-up failed"));
+    *out = k;
+    return HH_OK;
+}
+
+void hh_pack_destroy(hh_pack* k) {
+    if (!k) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(k->device);
+    if (k->s) cudaStreamSynchronize(k->s);
+    for (auto& x : k->m)
+        if (x.p) cudaStreamSynchronize(x.p->s);
+    if (k->graph) cudaGraphExecDestroy(k->graph);
+    for (auto e : k->ev_m)
+        if (e) cudaEventDestroy(e);
+    if (k->ev_prec) cudaEventDestroy(k->ev_prec);
+    if (k->d_plans) cudaFree(k->d_plans);
+    if (k->d_starts) cudaFree(k->d_starts);
+    if (k->d_live) cudaFree(k->d_live);
+    if (k->h_live) cudaFreeHost(k->h_live);
+    if (k->s) cudaStreamDestroy(k->s);
+    cudaSetDevice(cur);
+    delete k;
+}
+
+int hh_pack_members(const hh_pack* k) {
+    if (!k) return 0;
+    int n = 0;
+    for (const auto& x : k->m) n += x.state != PK_FREE;
+    return n;
+}
+
+hh_status hh_pack_add(hh_pack* k, hh_problem* p, const void* rhs, int io, double tol, void* u, int* slot) {
+    if (!k || !p || !rhs || !u || !slot) return fail(HH_ERR_INVALID, "null argument");
+    if (!(tol > 0)) return fail(HH_ERR_INVALID, "tol must be > 0");
+    if (io < 0 || io > 2) return fail(HH_ERR_INVALID, "io must be 0 (device), 1 (host load vector) or 2 (host nodal source)");
+    std::string why;
+    if (!packable(p, hh_pack_members(k) ? k->levels : 0, &why)) return fail(HH_ERR_INVALID, why);
+    int i = 0;
+    while (i < k->capacity && k->m[i].state != PK_FREE) ++i;
+    if (i == k->capacity) return fail(HH_ERR_INVALID, "the pack is full");
+    for (const auto& x : k->m)
+        if (x.p == p && x.state != PK_FREE) return fail(HH_ERR_INVALID, "the problem is already in the pack");
+    HH_TRY(ensure_hier(p, HH_C64));
+    Hier& H = p->hier[HH_C64];
+    // the packed passes leave u in xb[0]; a later solve of its own captures its graph anew
+    if (H.graph) {
+        cudaGraphExecDestroy(H.graph);
+        H.graph = nullptr;
+    }
+    H.loop.clear();
+    const long long N0 = p->lv[0].N;
+    void* src = p->nhss[0] > 0 ? H.xb[0] : H.cres;
+    if (p->nhss[0] == 0) HH_CUDA(cudaMemsetAsync(H.cres, 0, (size_t)N0 * sizeof(float2), p->s));
+    HH_CUDA(cudaMemcpyAsync(H.usrc, &src, sizeof(void*), cudaMemcpyHostToDevice, p->s));
+    const size_t bytes = (size_t)p->N * 16;
+    if (io == 0) {
+        HH_TRY(masked_copy(p, (const double2*)rhs, p->bvec));
+    } else {
+        HH_CUDA(cudaMemcpyAsync(p->r, rhs, bytes, cudaMemcpyHostToDevice, p->s));
+        if (io == 2)
+            HH_TRY(op_axpby<double>(p, 0, R_M, p->r, nullptr, p->bvec, Cx<double>{1, 0}, Cx<double>{0, 0}, p->s));
+        else
+            HH_TRY(masked_copy(p, p->r, p->bvec));
+    }
+    HH_CUDA(cudaMemsetAsync(p->x, 0, bytes, p->s));
+    const int m = p->o.restart;
+    HH_TRY(norm2_dev(p, p->bvec, 2 * (m + 1)));
+    HH_TRY(enqueue_fetch(p));
+    HH_CUDA(cudaStreamSynchronize(p->s));  // the source (the address of src, host data) is read
+    PackMember& x = k->m[i];
+    x = PackMember{};
+    x.p = p;
+    x.io = io;
+    x.u = u;
+    x.tol = tol;
+    x.Hm.assign((size_t)(m + 1) * m, zc(0));
+    x.g.assign(m + 1, zc(0));
+    x.sn.assign(m, zc(0));
+    x.y.assign(m, zc(0));
+    x.cs.assign(m, 0.0);
+    x.t0 = std::chrono::steady_clock::now();
+    x.state = PK_BNORM;
+    if (hh_pack_members(k) == 1) k->levels = p->o.levels;
+    k->dirty = true;
+    *slot = i;
+    return HH_OK;
+}
+
+hh_status hh_pack_run(hh_pack* k, int max_rounds, int* done, int* ndone) {
+    if (!k || !done || !ndone) return fail(HH_ERR_INVALID, "null argument");
+    *ndone = 0;
+    for (int round = 0;; ++round) {
+        bool active = false;
+        *ndone = 0;
+        for (int i = 0; i < k->capacity; ++i) {
+            const PackMember& x = k->m[i];
+            if (x.state == PK_DONE) done[(*ndone)++] = i;
+            active = active || (x.state != PK_FREE && x.state != PK_DONE);
+        }
+        if (*ndone > 0 || !active || (max_rounds > 0 && round >= max_rounds)) return HH_OK;
+        HH_TRY(pack_round(k));
+    }
+}
+
+hh_status hh_pack_take(hh_pack* k, int slot, hh_info* info) {
+    if (!k || slot < 0 || slot >= k->capacity) return fail(HH_ERR_INVALID, "bad slot");
+    PackMember& x = k->m[slot];
+    if (x.state != PK_DONE) return fail(HH_ERR_INVALID, "the slot holds no finished solve");
+    if (info) *info = x.info;
+    const hh_status st = x.st;
+    if (st != HH_OK && st != HH_NOT_CONVERGED) g_last_error = x.err;
+    x = PackMember{};
+    return st;
+}
 
 }  // extern "C"

@@ -31,6 +31,8 @@ EXPORTED = (
     "hh_solve_host", "hh_solve_host_nodal", "hh_level_nodes", "hh_apply", "hh_jacobi", "hh_residual_restrict",
     "hh_prolong_correct", "hh_vcycle", "hh_hss_rhs", "hh_precondition", "hh_load_vector", "hh_dot",
     "hh_multidot_noalloc", "hh_server_create", "hh_server_submit", "hh_server_wait", "hh_server_get_stats",
+    "hh_server_set_fallback", "hh_pack_create", "hh_pack_add", "hh_pack_run", "hh_pack_take", "hh_pack_members",
+    "hh_pack_destroy", "hh_server_set_pack",
     "hh_server_destroy", "hh_status_string", "hh_last_error", "hh_sigma_dofs", "hh_vector_length",
     "hh_apply_system", "hh_set_allocation_limit",
 )
@@ -49,7 +51,8 @@ class Options(ctypes.Structure):
         ("coarse_cluster_nodes", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
         ("fuse_sweeps", ctypes.c_int), ("outer", ctypes.c_int), ("cycle_gamma", ctypes.c_int),
         ("tile_form", ctypes.c_int), ("smoother", ctypes.c_int), ("formulation", ctypes.c_int),
-        ("persistent", ctypes.c_int), ("sync_spin_limit", ctypes.c_longlong),
+        ("persistent", ctypes.c_int), ("sync_spin_limit", ctypes.c_longlong), ("stall_cycles", ctypes.c_int),
+        ("coarse_kernel", ctypes.c_int),
     ]
 
 
@@ -57,7 +60,7 @@ class Info(ctypes.Structure):
     _fields_ = [
         ("outer_its", ctypes.c_int), ("hss_its", ctypes.c_longlong), ("vcycles", ctypes.c_longlong),
         ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-        ("kernel_launches", ctypes.c_longlong),
+        ("kernel_launches", ctypes.c_longlong), ("fallback", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -120,6 +123,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "hh_server_submit": (I, [P, ctypes.POINTER(Request), P, P, ctypes.POINTER(ctypes.c_longlong)]),
         "hh_server_wait": (I, [P, ctypes.c_longlong, ctypes.POINTER(Info), ctypes.POINTER(D), ctypes.POINTER(D)]),
         "hh_server_get_stats": (I, [P, ctypes.POINTER(ServerStats)]),
+        "hh_server_set_fallback": (I, [P, ctypes.POINTER(Options), D]),
+        "hh_pack_create": (I, [I, ctypes.POINTER(P)]),
+        "hh_pack_add": (I, [P, P, P, I, D, P, ctypes.POINTER(ctypes.c_int)]),
+        "hh_pack_run": (I, [P, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "hh_server_set_pack": (I, [P, I]),
+        "hh_pack_take": (I, [P, I, ctypes.POINTER(Info)]),
+        "hh_pack_members": (I, [P]),
+        "hh_pack_destroy": (V, [P]),
         "hh_server_destroy": (V, [P]),
         "hh_destroy": (V, [P]),
         "hh_solve": (I, [P, P, D, P, P, ctypes.POINTER(Info)]),
@@ -373,6 +384,73 @@ class Problem:
         return vals if self.batched else vals[0]
 
 
+class Pack:
+    """Problems of different grids whose FGMRES solves share their preconditioner launches
+    (hh_pack_*): add (problem, right side), run until members finish, take their results.
+    Each result equals the member problem's own solve bit for bit."""
+
+    def __init__(self, capacity=16):
+        self._lib = load_library()
+        self.capacity = int(capacity)
+        out = ctypes.c_void_p()
+        _check(self._lib.hh_pack_create(self.capacity, ctypes.byref(out)))
+        self._k = out
+        self._held = {}  # slot -> (problem, rhs, u) kept alive while the member runs
+
+    def add(self, problem: "Problem", rhs, tol=1e-8, nodal=False) -> int:
+        """Add a member: rhs a CUDA complex128 load vector (u returned on the device), or a host
+        numpy array (load vector, or with nodal=True the nodal source f); returns its slot."""
+        slot = ctypes.c_int()
+        if isinstance(rhs, np.ndarray):
+            rhs = np.ascontiguousarray(rhs, dtype=np.complex128)
+            u = np.empty_like(rhs)
+            io, rp, up = (2 if nodal else 1), rhs.ctypes.data_as(ctypes.c_void_p), u.ctypes.data_as(ctypes.c_void_p)
+            if rhs.size != problem.system_size():
+                raise ValueError("right side has the wrong size")
+        else:
+            u = torch.empty_like(rhs)
+            io, rp, up = 0, _ptr(rhs, problem.system_size()), _ptr(u, problem.system_size())
+        _check(self._lib.hh_pack_add(self._k, problem._p, rp, io, float(tol), up, ctypes.byref(slot)))
+        self._held[slot.value] = (problem, rhs, u)
+        return slot.value
+
+    def run(self, max_rounds=0):
+        """Run until at least one member finishes (or max_rounds rounds, if > 0); returns the
+        finished slots."""
+        done = (ctypes.c_int * self.capacity)()
+        nd = ctypes.c_int()
+        _check(self._lib.hh_pack_run(self._k, int(max_rounds), done, ctypes.byref(nd)))
+        return [done[i] for i in range(nd.value)]
+
+    def take(self, slot):
+        """(u, info) of a finished member; frees its slot."""
+        info = Info()
+        st = self._lib.hh_pack_take(self._k, int(slot), ctypes.byref(info))
+        _, _, u = self._held.pop(slot, (None, None, None))
+        _check(st, allow_not_converged=True)
+        return u, info
+
+    def members(self) -> int:
+        return int(self._lib.hh_pack_members(self._k))
+
+    def close(self):
+        if getattr(self, "_k", None):
+            self._lib.hh_pack_destroy(self._k)
+            self._k = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 class Server:
     """Continuous-batching solve server (hh_server_*): submit host right sides of any grid
     and wavenumber, wait for the solutions.  Solves run concurrently on the device, admitted
@@ -411,6 +489,17 @@ class Server:
         _, u = self._pending.pop(ticket, (None, None))
         _check(st, allow_not_converged=True)
         return u, info, lat.value, qs.value
+
+    def set_fallback(self, options: Options | None, delta_hat: float = 2.0):
+        """Solve requests that do not converge once more with these options and delta_hat
+        (None removes the fallback); see hh_server_set_fallback."""
+        self._fallback = options  # kept alive: the server copies it, the binding keeps the original
+        _check(self._lib.hh_server_set_fallback(self._s, ctypes.byref(options) if options is not None else None,
+                                                float(delta_hat)))
+
+    def set_pack(self, capacity=16):
+        """Run the server's 2D requests as members of one pack (hh_server_set_pack)."""
+        _check(self._lib.hh_server_set_pack(self._s, int(capacity)))
 
     def stats(self) -> dict:
         out = ServerStats()

@@ -1,13 +1,16 @@
 """Parity at the full sizes of the benchmark workloads, in the benchmark's launch configuration
 (default options: 4 levels, V(2,2), complex64 V-cycles, CUDA graphs, programmatic launch,
-cluster coarse solve).
+one-launch coarse solve).
 
 2D 512^2, k = 80 (263,169 nodes): everything against the oracle's assembled CSR matrices and
 sparse LU.  3D 128^3, k = 40 (2,146,689 nodes): too large to assemble in the oracle; operator
 applies and the FP64 residual of the solve are recomputed with the oracle's element-by-element
-apply, and the discrete energy identity Im(u^H b) = -k u^H M_Gamma u (delta = 0) is checked
-up to the residual.
+apply, the discrete energy identity Im(u^H b) = -k u^H M_Gamma u (delta = 0) is checked
+up to the residual, and the solution is compared with the oracle's own (FGMRES to a residual
+of 1e-11 by the C oracle, stored at every 11th node in tests/golden/c3_reference.npz).
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -18,7 +21,7 @@ from paper_2506_18694_gb300 import hh, inputs
 
 pytestmark = pytest.mark.gpu
 
-
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 @pytest.fixture(scope="module")
@@ -78,6 +81,22 @@ def test_c3_apply_full_vectors(libhh, c3):
                 assert rel(y, ref) <= tol, (op, dt)
 
 
+def _c3_reference(w, f):
+    """The oracle's solution of the 3D workload sampled at every STRIDE-th node
+    (tests/golden/c3_reference.npz, written by tests/golden/make_c3_reference.py), after checking
+    that it was computed for exactly these inputs."""
+    import importlib.util
+
+    path = os.path.join(GOLDEN, "make_c3_reference.py")
+    spec = importlib.util.spec_from_file_location("make_c3_reference", path)
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    ref = np.load(os.path.join(GOLDEN, "c3_reference.npz"))
+    assert str(ref["key"]) == mk.input_key(w, f), "c3_reference.npz was written for other inputs"
+    assert float(ref["rel_residual"]) <= 2 * float(ref["tol"])
+    return int(ref["stride"]), ref["u"]
+
+
 @pytest.mark.parametrize("dh,cycles,restart", [("k", 1, 60), (2.0, 2, 30)])
 def test_c3_solve_residual_and_energy(libhh, c3, dh, cycles, restart):
     w0, g, f, b = c3
@@ -96,6 +115,11 @@ def test_c3_solve_residual_and_energy(libhh, c3, dh, cycles, restart):
     mg = np.real(np.vdot(u, O.apply_elementwise(g, (0.0, 0.0, 1.0), u)))
     gap = abs(np.imag(np.vdot(u, b)) + w.k * mg)
     assert gap <= 1.01 * np.linalg.norm(u) * np.linalg.norm(r) + 1e-12 * abs(w.k * mg)
+    # solution error against the FP64 oracle's solution (residual 1e-11), on every 11th node
+    stride, u_ref = _c3_reference(w0, f)
+    err = rel(u[::stride], u_ref)
+    print(f"C3 delta_hat={w.delta_hat} cycles={cycles}: solution error {err:.3e} against the oracle")
+    assert err <= 1e-6
 
 
 def test_large_2d_grid_persistent_kernels(libhh):

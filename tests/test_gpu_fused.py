@@ -58,16 +58,34 @@ def test_fused_batch_equals_unfused(libhh):
                                             (256, 3, (D, S, S, D), 8), (128, 3, (S, S, D, S), 7),
                                             (64, 2, (S, D, S, S), 1), (256, 3, (S, S, S, S), 2)])
 def test_coarse_cluster_equals_separate_sweeps(libhh, prec, n, levels, bc, nc):
-    """The coarsest level solved in one thread-block cluster (sweeps in pairs, one-row slabs
-    and odd counts included) equals the same sweeps run as separate kernels, bit for bit."""
+    """The coarsest level solved in one launch, by the thread-block cluster (sweeps in pairs,
+    one-row slabs and odd counts included) or by bands of rows with recomputed halos, equals
+    the same sweeps run as separate kernels, bit for bit."""
     g = O.Grid(2, n, bc)
     r = torch.from_numpy(inputs.random_complex(g.N, 1500 + n) * g.free()).cuda()
     out = {}
-    for cc in (0, 100000):
-        opts = hh.default_options(levels=levels, precision=prec, coarse_cluster_nodes=cc, nu_coarse=nc)
+    for name, cc, kern in (("separate", 0, 0), ("cluster", 100000, 1), ("bands", 100000, 2)):
+        opts = hh.default_options(levels=levels, precision=prec, coarse_cluster_nodes=cc, nu_coarse=nc,
+                                  coarse_kernel=kern)
         with hh.Problem(2, n, 12.0, 0.0, 12.0, bc, opts) as p:
             z = p.precondition(r)
             u, info = p.solve(r, 1e-9)
-            out[cc] = (z.cpu(), u.cpu(), info.outer_its)
-    assert torch.equal(out[0][0], out[100000][0])
-    assert torch.equal(out[0][1], out[100000][1]) and out[0][2] == out[100000][2]
+            out[name] = (z.cpu(), u.cpu(), info.outer_its)
+    for name in ("cluster", "bands"):
+        assert torch.equal(out["separate"][0], out[name][0]), name
+        assert torch.equal(out["separate"][1], out[name][1]) and out["separate"][2] == out[name][2], name
+
+
+@pytest.mark.parametrize("nb", [1, 3])
+def test_coarse_bands_batch(libhh, nb):
+    """Bands of rows and the cluster give the same bits, for a batch too."""
+    n, bc = 128, (S, D, S, S)
+    g = O.Grid(2, n, bc)
+    ks = np.array([9.0, 14.0, 20.0])[:nb]
+    r = torch.from_numpy(np.concatenate([inputs.random_complex(g.N, 1600 + b) * g.free() for b in range(nb)])).cuda()
+    zs = []
+    for kern in (1, 2):
+        with hh.Problem(2, n, ks if nb > 1 else float(ks[0]), 0.0, ks if nb > 1 else float(ks[0]), bc,
+                        hh.default_options(levels=3, coarse_kernel=kern)) as p:
+            zs.append(p.precondition(r).cpu())
+    assert torch.equal(zs[0], zs[1])
