@@ -546,6 +546,12 @@ def measure_extras(hh, inputs, torch, w, prob, b, u_mixed, info_mixed, opts):
     except Exception as e:
         out["serving"] = {"failed": str(e)}
 
+    # uneven grids: packed launches against one solve at a time and against worker streams
+    try:
+        out["pack_uneven"] = measure_pack(hh, inputs, torch)
+    except Exception as e:
+        out["pack_uneven"] = {"failed": str(e)}
+
     # batched: 64 right sides on 2D 256^2, k from {20, 40, 80}, one problem object
     try:
         out["batch64"] = measure_batch(hh, inputs, torch)
@@ -620,20 +626,25 @@ def serving_options(hh):
     return first, fallback
 
 
-def measure_serving(hh, inputs, torch, count, slots=4, load=0.8, tol=1e-8):
+def measure_serving(hh, inputs, torch, count, slots=4, load=0.8, tol=1e-8, pack=16):
     """The serving workload (mixed 2D/3D grids and wavenumbers, nodal Gaussian sources, tol 1e-8)
-    through the solve server with the fallback policy of serving_options.  Pass 1 queues every
-    request at once: the server's capacity (solves/s) and each request's service record.  Pass 2
-    replays them with the seeded Poisson arrival times rescaled to `load` times that capacity:
-    latency p50/p99.  A request that ends above tol counts as failed and not in solves/s."""
+    through the solve server with the fallback policy of serving_options, every request on one of
+    `slots` worker slots (its own stream; kernels of different requests overlap on the device).
+    Pass 1 queues every request at once: the server's capacity (solves/s) and each request's
+    service record.  Pass 2 replays them with the seeded Poisson arrival times rescaled to `load`
+    times that capacity: latency p50/p99.  Pass 3 queues them all at once with the 2D requests
+    as members of one pack of `pack` slots (their V-cycle passes share launches), for
+    comparison.  A request that ends above tol counts as failed and not in solves/s."""
     reqs = inputs.serving_requests(count)
     srcs = [r.source() for r in reqs]
     first, fallback = serving_options(hh)
     budget = int(torch.cuda.mem_get_info()[0] * 0.6)
 
-    def run(arrivals):
+    def run(arrivals, packed=False):
         with hh.Server(slots=slots, budget_bytes=budget, options=first) as srv:
             srv.set_fallback(fallback, 2.0)
+            if packed and pack > 0:
+                srv.set_pack(pack)
             t0 = time.perf_counter()
             tickets = []
             for r, f, a in zip(reqs, srcs, arrivals):
@@ -653,6 +664,8 @@ def measure_serving(hh, inputs, torch, count, slots=4, load=0.8, tol=1e-8):
     arr = [r.arrival / reqs[-1].arrival * (len(reqs) / rate) for r in reqs]  # seeded Poisson times, rescaled
     res, span, st = run(arr)
     ok = [x[1].rel_residual <= tol for x in res]
+    unp, unp_span, unp_st = run([0.0] * len(reqs), packed=True)
+    ok_unp = [x[1].rel_residual <= tol for x in unp]
     lat = [x[2] for x in res]
     work = sum(r.nodes * x[1].vcycles for r, x in zip(reqs, res))
     return {
@@ -660,7 +673,7 @@ def measure_serving(hh, inputs, torch, count, slots=4, load=0.8, tol=1e-8):
                     "k uniform [10,160] capped at 2 pi n/10, tol 1e-8; first solve V(2,2)-Jacobi at delta_hat = k "
                     "(FGMRES(60), given up after 4 restart cycles without halving the residual), fallback the "
                     "paper's multigrid at delta_hat = 2 (W-cycles, GMRES(5) + Jacobi on every level)",
-        "requests": len(reqs), "of_full": 1000, "slots": slots, "budget_bytes": budget,
+        "requests": len(reqs), "of_full": 1000, "slots": slots, "pack_slots": pack, "budget_bytes": budget,
         "capacity_solves_per_s": cap, "arrival_rate_per_s": rate, "load": load,
         "solves_per_s": sum(ok) / span, "failed": len(ok) - sum(ok), "failed_saturated": len(ok_sat) - sum(ok_sat),
         "fallbacks": sum(x[1].fallback for x in res),
@@ -672,9 +685,50 @@ def measure_serving(hh, inputs, torch, count, slots=4, load=0.8, tol=1e-8):
         "problems_created": st["problems_created"], "problems_reused": st["problems_reused"],
         "problems_evicted": st["problems_evicted"],
         "saturated": {"solves_per_s": cap, "span_s": sat_span, "max_concurrent": sat_st["max_concurrent"]},
+        "saturated_with_pack": {"solves_per_s": sum(ok_unp) / unp_span, "span_s": unp_span,
+                                "failed": len(ok_unp) - sum(ok_unp), "max_concurrent": unp_st["max_concurrent"],
+                                "note": "2D requests in one pack: every member advances one FGMRES iteration "
+                                        "per round, so a round lasts as long as the longest HSS loop"},
         "per_request": [[r.dim, r.n, round(r.k, 1), x[1].outer_its, x[1].rel_residual, round(x[1].seconds, 3),
                          x[1].fallback] for r, x in zip(reqs, sat)],
     }
+
+
+def measure_pack(hh, inputs, torch, tol=1e-8):
+    """Problems on uneven 2D grids (inputs.uneven_requests: 48 solves, n from 64 to 256, k 20 or
+    40) through the solve server three ways, all queued at once: one at a time (1 worker slot),
+    on 4 worker slots (their own streams), and as members of one pack (their V-cycle passes share
+    launches; 1 worker slot for nothing else).  Each way must give the same solutions bit for
+    bit; solves/s for each."""
+    reqs = inputs.uneven_requests()
+    srcs = [r.source() for r in reqs]
+    opts = hh.default_options(precision=hh.HH_C64)
+    budget = int(torch.cuda.mem_get_info()[0] * 0.6)
+
+    def run(slots, pack):
+        with hh.Server(slots=slots, budget_bytes=budget, options=opts) as srv:
+            if pack:
+                srv.set_pack(pack)
+            t0 = time.perf_counter()
+            tickets = [srv.submit(r.dim, r.n, r.k, r.delta, r.delta_hat, r.bc, f, tol, nodal=True)
+                       for r, f in zip(reqs, srcs)]
+            res = [srv.wait(t) for t in tickets]
+            return res, time.perf_counter() - t0
+
+    out = {"workload": "48 solves on 2D grids n in {64, 96, ..., 256} (seed 6), k in {20, 40}, delta_hat = k, "
+                       "tol 1e-8, all queued at once", "requests": len(reqs)}
+    ref = None
+    for name, slots, pack in (("sequential", 1, 0), ("workers4", 4, 0), ("pack48", 1, 48)):
+        res, span = run(slots, pack)
+        us = [x[0] for x in res]
+        if ref is None:
+            ref = us
+        out[name] = {"solves_per_s": len(reqs) / span, "span_s": span,
+                     "max_rel_residual": max(x[1].rel_residual for x in res),
+                     "equal_to_sequential_bitwise": all(np.array_equal(a, b) for a, b in zip(us, ref))}
+    out["pack_vs_sequential"] = out["sequential"]["span_s"] / out["pack48"]["span_s"]
+    out["pack_vs_workers4"] = out["workers4"]["span_s"] / out["pack48"]["span_s"]
+    return out
 
 
 def measure_batch(hh, inputs, torch):

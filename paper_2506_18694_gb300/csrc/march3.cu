@@ -42,15 +42,15 @@ __device__ __forceinline__ int bclass3(int tx, int ty, int tz) {
 }
 
 // Value of the stencil field at node (i, j, l) of the grid (offset p), which holds an unknown
-// there.
-template <typename T, int MODE>
+// there (INNER: the node is known to lie inside the cube, off every face).
+template <typename T, int MODE, bool INNER>
 __device__ __forceinline__ Cx<T> field3(const MArgs<T>& a, const PCoef<T>& c, const Cx<T>* bw, const VPtrs<T>& v,
                                         int i, int j, int l, long long p) {
     const int n = a.g.n;
     if (MODE == M_JACOBI2_ZERO) {
         // first sweep from x = 0: x1 = omega D^{-1} b
         const Cx<T> b = ld<T>(v.z, p);
-        if (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1 && l >= 1 && l <= n - 1) return cmul(c.wdinv, b);
+        if (INNER || (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1 && l >= 1 && l <= n - 1)) return cmul(c.wdinv, b);
         const int q = bclass3(type1(i, n), type1(j, n), type1(l, n));
         return cmul(bw[q * kClass3Len + 8], b);
     } else if (MODE == M_PROLONG_JACOBI) {
@@ -91,18 +91,16 @@ constexpr int kWarps3 = 8;  // y-rows per tile, including the two halo rows
 
 }  // namespace
 
-// BATCH = false: a batch of one, coefficients from the kernel parameters, no activity flags.
-template <typename T, int MODE, int R, bool BATCH>
-__global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__ MArgs<T> a, int zt) {
-    pdl_entry();
-    const int b = BATCH ? (int)blockIdx.z / zt : 0;  // problem; blockIdx.z % zt: z-tile
-    if (BATCH && problem_skipped(a, b)) return;
+// One tile.  INNER: every node the tile loads (halos included) lies inside the cube, off every
+// face, so no node is void or on the boundary and no check or boundary-class code is needed;
+// the node arithmetic is the same as on the general path.
+template <typename T, int MODE, int R, bool BATCH, bool INNER>
+__device__ __forceinline__ void march3_tile(const MArgs<T>& a, int zt, int b, unsigned char* smem_raw) {
     const PCoef<T>& cf = BATCH ? a.pc[b] : a.c0;
     const Cx<T>* bw = a.bw3 + (long long)b * kClass3 * kClass3Len;
     const VPtrs<T> v = problem_ptrs(a, b, false);
     constexpr int NP = R + 2;  // planes loaded
     constexpr bool NEEDZ = MODE != M_APPLY;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     // [warp][plane][lane]: field value and x-neighbour sum
     vec2<T>* sv = reinterpret_cast<vec2<T>*>(smem_raw);
     vec2<T>* ss = sv + kWarps3 * NP * 32;
@@ -112,8 +110,8 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__
     const int i = blockIdx.x * 30 + lane - 1;
     const int j = blockIdx.y * (kWarps3 - 2) + w - 1;
     const int l0 = (blockIdx.z - b * zt) * R;
-    const int ic = clampi3(i, 0, n), jc = clampi3(j, 0, n);
-    const bool cvoid = void1(i, n, a.g.dir[0], a.g.dir[1]) || void1(j, n, a.g.dir[2], a.g.dir[3]);
+    const int ic = INNER ? i : clampi3(i, 0, n), jc = INNER ? j : clampi3(j, 0, n);
+    const bool cvoid = !INNER && (void1(i, n, a.g.dir[0], a.g.dir[1]) || void1(j, n, a.g.dir[2], a.g.dir[3]));
     const long long ps = (long long)nn * nn;
     const long long colc = (long long)jc * nn + ic;
 
@@ -122,14 +120,15 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__
     for (int t = 0; t < NP; ++t) {
         const int l = l0 - 1 + t;
         // (a node of a plane that is not void lies inside the cube: no clamp needed)
-        fv[t] = (cvoid || void1(l, n, a.g.dir[4], a.g.dir[5])) ? cx<T>(0, 0)
-                                                               : field3<T, MODE>(a, cf, bw, v, ic, jc, l, colc + l * ps);
+        fv[t] = (!INNER && (cvoid || void1(l, n, a.g.dir[4], a.g.dir[5])))
+                    ? cx<T>(0, 0)
+                    : field3<T, MODE, INNER>(a, cf, bw, v, ic, jc, l, colc + l * ps);
     }
     Cx<T> zv[R];
     const bool out_row = w >= 1 && w <= kWarps3 - 2;
 #pragma unroll
     for (int t = 0; t < R; ++t)
-        zv[t] = (NEEDZ && out_row) ? ld<T>(v.z, colc + clampi3(l0 + t, 0, n) * ps) : cx<T>(0, 0);
+        zv[t] = (NEEDZ && out_row) ? ld<T>(v.z, colc + (INNER ? l0 + t : clampi3(l0 + t, 0, n)) * ps) : cx<T>(0, 0);
 #pragma unroll
     for (int t = 0; t < NP; ++t) {
         xs[t] = shfl_up3(fv[t]) + shfl_dn3(fv[t]);
@@ -137,8 +136,8 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__
         st<T>(ss, (w * NP + t) * 32 + lane, xs[t]);
     }
     __syncthreads();
-    if (!out_row || !(lane >= 1 && lane <= 30) || i > n || j > n) return;
-    const bool colrow_inner = i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1;
+    if (!out_row || !(lane >= 1 && lane <= 30) || (!INNER && (i > n || j > n))) return;
+    const bool colrow_inner = INNER || (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1);
     const int tx = type1(i, n), ty = type1(j, n);
     const int wm = w - 1, wp = w + 1;
     // rows j-1 + j+1 summed (value and x-sum) per plane, in a rolling window of 3 planes
@@ -149,13 +148,13 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__
 #pragma unroll
     for (int t = 0; t < R; ++t) {
         const int l = l0 + t;
-        if (l > n) break;
+        if (!INNER && l > n) break;
         const int tp = t + 1;  // local plane of the output
         const Cx<T> vy2 = ysum(sv, tp + 1), sy2 = ysum(ss, tp + 1);
         const long long p = colc + l * ps;
         Cx<T> ax, dinv_w;
         bool masked = false;
-        if (colrow_inner && l >= 1 && l <= n - 1) {
+        if (INNER || (colrow_inner && l >= 1 && l <= n - 1)) {
             const Cx<T> face = xs[tp] + vy1 + (fv[tp - 1] + fv[tp + 1]);
             const Cx<T> edge = sy1 + (xs[tp - 1] + xs[tp + 1]) + (vy0 + vy2);
             const Cx<T> corner = sy0 + sy2;
@@ -197,6 +196,23 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__
         sy0 = sy1;
         sy1 = sy2;
     }
+}
+
+// BATCH = false: a batch of one, coefficients from the kernel parameters, no activity flags.
+// Each CTA takes the check-free path when its whole tile (halos included) lies inside the cube.
+template <typename T, int MODE, int R, bool BATCH>
+__global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__ MArgs<T> a, int zt) {
+    pdl_entry();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int b = BATCH ? (int)blockIdx.z / zt : 0;  // problem; blockIdx.z % zt: z-tile
+    if (BATCH && problem_skipped(a, b)) return;
+    const int n = a.g.n;
+    const int i0 = blockIdx.x * 30 - 1, j0 = blockIdx.y * (kWarps3 - 2) - 1;
+    const int l0 = (blockIdx.z - b * zt) * R - 1;
+    const bool inner = i0 >= 1 && i0 + 31 <= n - 1 && j0 >= 1 && j0 + kWarps3 - 1 <= n - 1 && l0 >= 1 &&
+                       l0 + R + 1 <= n - 1;
+    if (inner) march3_tile<T, MODE, R, BATCH, true>(a, zt, b, smem_raw);
+    else march3_tile<T, MODE, R, BATCH, false>(a, zt, b, smem_raw);
 }
 
 // Weights of the 3D boundary classes.  1D rows (Q1): stiffness (1/h)(-1, cnt, -1), mass

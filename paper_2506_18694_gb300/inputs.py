@@ -177,3 +177,18 @@ def serving_requests(count: int = 1000, seed: int = 5, rate: float = 1.0, delta_
         dh = k if delta_hat == "k" else float(delta_hat)
         out.append(ServeRequest(dim, n, k, 0.0, dh, bc, centre, amp, t))
     return out
+
+
+def uneven_requests(count: int = 48, seed: int = 6):
+    """Solves on uneven 2D grids (the packed-launch workload): n uniform in {64, 96, ..., 256},
+    k uniform in {20, 40}, delta = 0, delta_hat = k, Sommerfeld on all sides, Gaussian sources
+    at uniform centres with complex normal amplitudes; all arrive at once."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.choice([64, 96, 128, 160, 192, 224, 256]))
+        k = float(rng.choice([20.0, 40.0]))
+        centre = tuple(float(v) for v in rng.uniform(0.0, 1.0, size=2))
+        amp = complex(rng.standard_normal(), rng.standard_normal())
+        out.append(ServeRequest(2, n, k, 0.0, k, (SOMMERFELD,) * 4, centre, amp, 0.0))
+    return out

@@ -31,6 +31,7 @@ CASES = [
     (3, 8, 3, (S, S, S, S, D, S)),
     (3, 12, 3, (D, D, S, S, S, D)),
     (3, 16, 3, (S, S, S, S, S, S)),
+    (3, 64, 3, (S, S, D, S, D, S)),  # 65^3: interior 3D tiles take the check-free path
 ]
 K_, DELTA, DHAT = 7.0, 0.3, 2.5
 
