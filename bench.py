@@ -626,15 +626,15 @@ def serving_options(hh):
     return first, fallback
 
 
-def measure_serving(hh, inputs, torch, count, slots=4, load=0.8, tol=1e-8, pack=16):
+def measure_serving(hh, inputs, torch, count, slots=4, load=0.8, tol=1e-8, pack=16, pack_max_hss=60):
     """The serving workload (mixed 2D/3D grids and wavenumbers, nodal Gaussian sources, tol 1e-8)
     through the solve server with the fallback policy of serving_options, every request on one of
     `slots` worker slots (its own stream; kernels of different requests overlap on the device).
     Pass 1 queues every request at once: the server's capacity (solves/s) and each request's
     service record.  Pass 2 replays them with the seeded Poisson arrival times rescaled to `load`
-    times that capacity: latency p50/p99.  Pass 3 queues them all at once with the 2D requests
-    as members of one pack of `pack` slots (their V-cycle passes share launches), for
-    comparison.  A request that ends above tol counts as failed and not in solves/s."""
+    times that capacity: latency p50/p99.  Pass 3 queues them all at once with the 2D requests of
+    at most `pack_max_hss` HSS steps as members of one pack of `pack` slots (their V-cycle passes
+    share launches), for comparison.  A request that ends above tol counts as failed and not in solves/s."""
     reqs = inputs.serving_requests(count)
     srcs = [r.source() for r in reqs]
     first, fallback = serving_options(hh)
@@ -644,7 +644,7 @@ def measure_serving(hh, inputs, torch, count, slots=4, load=0.8, tol=1e-8, pack=
         with hh.Server(slots=slots, budget_bytes=budget, options=first) as srv:
             srv.set_fallback(fallback, 2.0)
             if packed and pack > 0:
-                srv.set_pack(pack)
+                srv.set_pack(pack, pack_max_hss)
             t0 = time.perf_counter()
             tickets = []
             for r, f, a in zip(reqs, srcs, arrivals):
@@ -687,8 +687,10 @@ def measure_serving(hh, inputs, torch, count, slots=4, load=0.8, tol=1e-8, pack=
         "saturated": {"solves_per_s": cap, "span_s": sat_span, "max_concurrent": sat_st["max_concurrent"]},
         "saturated_with_pack": {"solves_per_s": sum(ok_unp) / unp_span, "span_s": unp_span,
                                 "failed": len(ok_unp) - sum(ok_unp), "max_concurrent": unp_st["max_concurrent"],
-                                "note": "2D requests in one pack: every member advances one FGMRES iteration "
-                                        "per round, so a round lasts as long as the longest HSS loop"},
+                                "pack_max_hss_steps": pack_max_hss,
+                                "note": "2D requests of at most pack_max_hss_steps HSS steps in one pack (every "
+                                        "member advances one FGMRES iteration per round, so a round lasts as "
+                                        "long as the longest member's HSS loop); the others on worker slots"},
         "per_request": [[r.dim, r.n, round(r.k, 1), x[1].outer_its, x[1].rel_residual, round(x[1].seconds, 3),
                          x[1].fallback] for r, x in zip(reqs, sat)],
     }

@@ -461,10 +461,12 @@ HH_API hh_status hh_server_get_stats(hh_server* s, hh_server_stats* out);
 /* Pack the server's 2D requests (before the first request; the server's options must be packable,
  * see hh_pack_create): a dispatcher thread runs up to `capacity` (1..256) of them as members of
  * one pack, so that their preconditioner applications share launches, and admits queued ones
- * between rounds as members finish and device memory frees up (continuous batching); other
- * requests, and fallback solves, run on the worker slots as before.  Results equal the lone
- * solves bit for bit. */
-HH_API hh_status hh_server_set_pack(hh_server* s, int capacity);
+ * between rounds as members finish and device memory frees up (continuous batching).  Only
+ * requests with at most max_hss_steps HSS steps (ceil(k^theta); 0: no limit) join the pack: each
+ * round advances every member by one FGMRES iteration and lasts as long as the longest member's
+ * HSS loop, so long loops are better run apart.  Other requests, and fallback solves, run on the
+ * worker slots as before.  Results equal the lone solves bit for bit. */
+HH_API hh_status hh_server_set_pack(hh_server* s, int capacity, int max_hss_steps);
 
 /* Fallback for requests that do not converge: a request whose solve ends HH_NOT_CONVERGED (its
  * max_outer reached, or stalled under opts.stall_cycles) is solved once more from zero on a

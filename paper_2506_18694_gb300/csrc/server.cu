@@ -80,6 +80,7 @@ struct hh_server {
     hh_options opts{};
     bool has_fallback = false;       // see hh_server_set_fallback
     int pack_capacity = 0;           // > 0: 2D requests run in a pack (hh_server_set_pack)
+    int pack_max_hss = 0;            // only those with at most this many HSS steps (0: all)
     std::thread pack_thread;
     hh_options fb_opts{};
     double fb_dh = 0.0;
@@ -467,7 +468,10 @@ hh_status hh_server_submit(hh_server* S, const hh_request* r, const void* rhs_ho
     q->fallback = S->has_fallback;
     q->fb_opts = S->fb_opts;
     q->fb_dh = S->fb_dh;
-    q->packed = S->pack_capacity > 0 && r->grid.dim == 2;
+    // HSS steps of the request (ceil(k^theta), an integer power counted exactly)
+    const double v = std::pow(r->k, S->opts.theta), vr = std::round(v);
+    const int steps = std::fabs(v - vr) <= 1e-9 * std::max(1.0, v) ? (int)vr : (int)std::ceil(v);
+    q->packed = S->pack_capacity > 0 && r->grid.dim == 2 && (S->pack_max_hss == 0 || steps <= S->pack_max_hss);
     q->id = S->next_id++;
     *ticket = q->id;
     S->queue.push_back(q.get());
@@ -511,9 +515,10 @@ hh_status hh_server_set_fallback(hh_server* S, const hh_options* opts, double de
     return HH_OK;
 }
 
-hh_status hh_server_set_pack(hh_server* S, int capacity) {
+hh_status hh_server_set_pack(hh_server* S, int capacity, int max_hss_steps) {
     if (!S) return invalid("null server");
     if (capacity < 1 || capacity > 256) return invalid("pack capacity must be in 1..256");
+    if (max_hss_steps < 0) return invalid("max_hss_steps must be >= 0");
     const hh_options& o = S->opts;
     if (o.smoother != HH_SMOOTH_JACOBI || o.cycle_gamma != 1 || o.cycles_per_hss != 1 || o.nu_pre != 2 ||
         o.nu_post != 2 || o.precision != HH_C64 || o.outer != HH_OUTER_FGMRES || o.levels < 2 || o.levels > 5)
@@ -523,6 +528,7 @@ hh_status hh_server_set_pack(hh_server* S, int capacity) {
     if (S->pack_capacity > 0) return invalid("the server already packs its requests");
     if (S->st.submitted > 0) return invalid("set the pack before the first request");
     S->pack_capacity = capacity;
+    S->pack_max_hss = max_hss_steps;
     S->pack_thread = std::thread(dispatcher, S);
     return HH_OK;
 }

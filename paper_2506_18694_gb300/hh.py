@@ -127,7 +127,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "hh_pack_create": (I, [I, ctypes.POINTER(P)]),
         "hh_pack_add": (I, [P, P, P, I, D, P, ctypes.POINTER(ctypes.c_int)]),
         "hh_pack_run": (I, [P, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
-        "hh_server_set_pack": (I, [P, I]),
+        "hh_server_set_pack": (I, [P, I, I]),
         "hh_pack_take": (I, [P, I, ctypes.POINTER(Info)]),
         "hh_pack_members": (I, [P]),
         "hh_pack_destroy": (V, [P]),
@@ -497,9 +497,10 @@ class Server:
         _check(self._lib.hh_server_set_fallback(self._s, ctypes.byref(options) if options is not None else None,
                                                 float(delta_hat)))
 
-    def set_pack(self, capacity=16):
-        """Run the server's 2D requests as members of one pack (hh_server_set_pack)."""
-        _check(self._lib.hh_server_set_pack(self._s, int(capacity)))
+    def set_pack(self, capacity=16, max_hss_steps=0):
+        """Run the server's 2D requests with at most max_hss_steps HSS steps (0: all) as members
+        of one pack (hh_server_set_pack)."""
+        _check(self._lib.hh_server_set_pack(self._s, int(capacity), int(max_hss_steps)))
 
     def stats(self) -> dict:
         out = ServerStats()

@@ -158,16 +158,16 @@ def test_stall_detection_stops_early(libhh):
 
 @pytest.mark.timeout(600)
 def test_server_pack_mode_equals_alone(libhh):
-    """With a pack, the server's 2D requests run as members of one pack (shared launches, slots
-    refilled as members finish) and the 3D ones on the worker slots; every result equals its
-    lone solve bit for bit, and the budget still holds."""
+    """With a pack, the server's 2D requests of at most 25 HSS steps run as members of one pack
+    (shared launches, slots refilled as members finish), the longer 2D ones and the 3D ones on
+    the worker slots; every result equals its lone solve bit for bit, and the budget holds."""
     opts = hh.default_options(levels=3)
     fps = [hh.footprint_bytes(d, n, opts) for d, n, *_ in MIX]
     budget = 3 * sorted(fps)[-1]
     rhs = [(_source(d, n, 1900 + i) if i in NODAL else _rhs(d, n, bc, 1900 + i))
            for i, (d, n, k, de, dh, bc) in enumerate(MIX)]
     with hh.Server(slots=2, budget_bytes=budget, options=opts) as srv:
-        srv.set_pack(3)
+        srv.set_pack(3, 25)
         tickets = [srv.submit(d, n, k, de, dh, bc, rhs[i], 1e-9, nodal=i in NODAL)
                    for i, (d, n, k, de, dh, bc) in enumerate(MIX)]
         results = [srv.wait(t) for t in tickets]
