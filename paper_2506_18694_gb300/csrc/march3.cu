@@ -89,13 +89,68 @@ __device__ __forceinline__ Cx<T> field3(const MArgs<T>& a, const PCoef<T>& c, co
 
 constexpr int kWarps3 = 8;  // y-rows per tile, including the two halo rows
 
+// Window of a node: the field value (f*) and x-neighbour sum (x*) of its column on planes
+// l-1, l, l+1, and the sums over rows j-1 and j+1 of the value (vy*) and of the x-sum (sy*).
+template <typename T> struct Win3 {
+    Cx<T> fm, f0, fp, xm, x0, xp, vy0, vy1, vy2, sy0, sy1, sy2;
+};
+
+// The output of one node (offset p) from its window: the 27-point product A x assembled by
+// neighbour group, then the mode's update.  FAST: an interior node (the four weights of the
+// interior stencil); else the eight group weights of the node's boundary class (tx, ty, l).
+template <typename T, int MODE, bool FAST>
+__device__ __forceinline__ void out3(const MArgs<T>& a, const PCoef<T>& cf, const Cx<T>* bw, const VPtrs<T>& v,
+                                     const Win3<T>& q, Cx<T> zq, int tx, int ty, int l, bool cvoid, long long p) {
+    const int n = a.g.n;
+    Cx<T> ax, dinv_w;
+    bool masked = false;
+    if (FAST) {
+        const Cx<T> face = q.x0 + q.vy1 + (q.fm + q.fp);
+        const Cx<T> edge = q.sy1 + (q.xm + q.xp) + (q.vy0 + q.vy2);
+        const Cx<T> corner = q.sy0 + q.sy2;
+        ax = fma_c(cf.iw[3], corner, fma_c(cf.iw[2], edge, fma_c(cf.iw[1], face, cmul(cf.iw[0], q.f0))));
+        dinv_w = cf.wdinv;
+    } else {
+        // neighbour groups: centre; x, y, z faces; xy, xz, yz edges; corners
+        masked = cvoid || void1(l, n, a.g.dir[4], a.g.dir[5]);
+        const Cx<T>* wq = bw + bclass3(tx, ty, type1(l, n)) * kClass3Len;
+        ax = cmul(wq[0], q.f0);
+        ax = fma_c(wq[1], q.x0, ax);
+        ax = fma_c(wq[2], q.vy1, ax);
+        ax = fma_c(wq[3], q.fm + q.fp, ax);
+        ax = fma_c(wq[4], q.sy1, ax);
+        ax = fma_c(wq[5], q.xm + q.xp, ax);
+        ax = fma_c(wq[6], q.vy0 + q.vy2, ax);
+        ax = fma_c(wq[7], q.sy0 + q.sy2, ax);
+        dinv_w = wq[8];
+    }
+    const Cx<T> alpha = a.use_pc_ab ? cf.alpha : a.alpha, beta = a.use_pc_ab ? cf.beta : a.beta;
+    if (masked) {
+        st<T>(v.y, p, cx<T>(0, 0));
+        if (MODE == M_HSS_FIRST) st<T>(v.y2, p, cx<T>(0, 0));
+    } else if (MODE == M_APPLY) {
+        st<T>(v.y, p, ax);
+    } else if (MODE == M_AXPBY) {
+        st<T>(v.y, p, fma_c(alpha, ax, cmul(beta, zq)));
+    } else if (MODE == M_DAXPBY) {
+        st<T>(v.y, p, cmul(dinv_w, fma_c(alpha, ax, cmul(beta, zq))));
+    } else if (MODE == M_HSS_FIRST) {
+        const Cx<T> rhs = fma_c(alpha, ax, cmul(beta, zq));
+        st<T>(v.y, p, rhs);
+        st<T>(v.y2, p, cmul(dinv_w, rhs));
+    } else {
+        st<T>(v.y, p, fma_c(dinv_w, zq - ax, q.f0));
+    }
+}
+
 }  // namespace
 
 // One tile.  INNER: every node the tile loads (halos included) lies inside the cube, off every
 // face, so no node is void or on the boundary and no check or boundary-class code is needed;
 // the node arithmetic is the same as on the general path.
 template <typename T, int MODE, int R, bool BATCH, bool INNER>
-__device__ __forceinline__ void march3_tile(const MArgs<T>& a, int zt, int b, unsigned char* smem_raw) {
+__device__ __forceinline__ void march3_tile(const MArgs<T>& a, int b, int bx, int by, int l0,
+                                            unsigned char* smem_raw) {
     const PCoef<T>& cf = BATCH ? a.pc[b] : a.c0;
     const Cx<T>* bw = a.bw3 + (long long)b * kClass3 * kClass3Len;
     const VPtrs<T> v = problem_ptrs(a, b, false);
@@ -107,9 +162,8 @@ __device__ __forceinline__ void march3_tile(const MArgs<T>& a, int zt, int b, un
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int n = a.g.n, nn = a.g.nn;
-    const int i = blockIdx.x * 30 + lane - 1;
-    const int j = blockIdx.y * (kWarps3 - 2) + w - 1;
-    const int l0 = (blockIdx.z - b * zt) * R;
+    const int i = bx * 30 + lane - 1;
+    const int j = by * (kWarps3 - 2) + w - 1;
     const int ic = INNER ? i : clampi3(i, 0, n), jc = INNER ? j : clampi3(j, 0, n);
     const bool cvoid = !INNER && (void1(i, n, a.g.dir[0], a.g.dir[1]) || void1(j, n, a.g.dir[2], a.g.dir[3]));
     const long long ps = (long long)nn * nn;
@@ -144,58 +198,40 @@ __device__ __forceinline__ void march3_tile(const MArgs<T>& a, int zt, int b, un
     auto ysum = [&](const vec2<T>* arr, int tpl) {
         return ld<T>(arr, (wm * NP + tpl) * 32 + lane) + ld<T>(arr, (wp * NP + tpl) * 32 + lane);
     };
-    Cx<T> vy0 = ysum(sv, 0), vy1 = ysum(sv, 1), sy0 = ysum(ss, 0), sy1 = ysum(ss, 1);
+    Win3<T> q;
+    q.vy0 = ysum(sv, 0);
+    q.vy1 = ysum(sv, 1);
+    q.sy0 = ysum(ss, 0);
+    q.sy1 = ysum(ss, 1);
 #pragma unroll
     for (int t = 0; t < R; ++t) {
         const int l = l0 + t;
         if (!INNER && l > n) break;
         const int tp = t + 1;  // local plane of the output
-        const Cx<T> vy2 = ysum(sv, tp + 1), sy2 = ysum(ss, tp + 1);
+        q.vy2 = ysum(sv, tp + 1);
+        q.sy2 = ysum(ss, tp + 1);
+        q.fm = fv[tp - 1];
+        q.f0 = fv[tp];
+        q.fp = fv[tp + 1];
+        q.xm = xs[tp - 1];
+        q.x0 = xs[tp];
+        q.xp = xs[tp + 1];
         const long long p = colc + l * ps;
-        Cx<T> ax, dinv_w;
-        bool masked = false;
-        if (INNER || (colrow_inner && l >= 1 && l <= n - 1)) {
-            const Cx<T> face = xs[tp] + vy1 + (fv[tp - 1] + fv[tp + 1]);
-            const Cx<T> edge = sy1 + (xs[tp - 1] + xs[tp + 1]) + (vy0 + vy2);
-            const Cx<T> corner = sy0 + sy2;
-            ax = fma_c(cf.iw[3], corner, fma_c(cf.iw[2], edge, fma_c(cf.iw[1], face, cmul(cf.iw[0], fv[tp]))));
-            dinv_w = cf.wdinv;
-        } else {
-            // neighbour groups: centre; x, y, z faces; xy, xz, yz edges; corners
-            masked = cvoid || void1(l, n, a.g.dir[4], a.g.dir[5]);
-            const Cx<T>* wq = bw + bclass3(tx, ty, type1(l, n)) * kClass3Len;
-            ax = cmul(wq[0], fv[tp]);
-            ax = fma_c(wq[1], xs[tp], ax);
-            ax = fma_c(wq[2], vy1, ax);
-            ax = fma_c(wq[3], fv[tp - 1] + fv[tp + 1], ax);
-            ax = fma_c(wq[4], sy1, ax);
-            ax = fma_c(wq[5], xs[tp - 1] + xs[tp + 1], ax);
-            ax = fma_c(wq[6], vy0 + vy2, ax);
-            ax = fma_c(wq[7], sy0 + sy2, ax);
-            dinv_w = wq[8];
-        }
-        const Cx<T> alpha = a.use_pc_ab ? cf.alpha : a.alpha, beta = a.use_pc_ab ? cf.beta : a.beta;
-        if (masked) {
-            st<T>(v.y, p, cx<T>(0, 0));
-            if (MODE == M_HSS_FIRST) st<T>(v.y2, p, cx<T>(0, 0));
-        } else if (MODE == M_APPLY) {
-            st<T>(v.y, p, ax);
-        } else if (MODE == M_AXPBY) {
-            st<T>(v.y, p, fma_c(alpha, ax, cmul(beta, zv[t])));
-        } else if (MODE == M_DAXPBY) {
-            st<T>(v.y, p, cmul(dinv_w, fma_c(alpha, ax, cmul(beta, zv[t]))));
-        } else if (MODE == M_HSS_FIRST) {
-            const Cx<T> rhs = fma_c(alpha, ax, cmul(beta, zv[t]));
-            st<T>(v.y, p, rhs);
-            st<T>(v.y2, p, cmul(dinv_w, rhs));
-        } else {
-            st<T>(v.y, p, fma_c(dinv_w, zv[t] - ax, fv[tp]));
-        }
-        vy0 = vy1;
-        vy1 = vy2;
-        sy0 = sy1;
-        sy1 = sy2;
+        if (INNER || (colrow_inner && l >= 1 && l <= n - 1))
+            out3<T, MODE, true>(a, cf, bw, v, q, zv[t], tx, ty, l, cvoid, p);
+        else
+            out3<T, MODE, false>(a, cf, bw, v, q, zv[t], tx, ty, l, cvoid, p);
+        q.vy0 = q.vy1;
+        q.vy1 = q.vy2;
+        q.sy0 = q.sy1;
+        q.sy1 = q.sy2;
     }
+}
+
+// Whether tile (bx, by, z from l0) with its halos lies inside the cube, off every face.
+__device__ __forceinline__ bool tile_inner3(int n, int bx, int by, int l0, int R) {
+    const int i0 = bx * 30 - 1, j0 = by * (kWarps3 - 2) - 1, z0 = l0 - 1;
+    return i0 >= 1 && i0 + 31 <= n - 1 && j0 >= 1 && j0 + kWarps3 - 1 <= n - 1 && z0 >= 1 && z0 + R + 1 <= n - 1;
 }
 
 // BATCH = false: a batch of one, coefficients from the kernel parameters, no activity flags.
@@ -206,13 +242,11 @@ __global__ void __launch_bounds__(32 * kWarps3) k_march3(const __grid_constant__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int b = BATCH ? (int)blockIdx.z / zt : 0;  // problem; blockIdx.z % zt: z-tile
     if (BATCH && problem_skipped(a, b)) return;
-    const int n = a.g.n;
-    const int i0 = blockIdx.x * 30 - 1, j0 = blockIdx.y * (kWarps3 - 2) - 1;
-    const int l0 = (blockIdx.z - b * zt) * R - 1;
-    const bool inner = i0 >= 1 && i0 + 31 <= n - 1 && j0 >= 1 && j0 + kWarps3 - 1 <= n - 1 && l0 >= 1 &&
-                       l0 + R + 1 <= n - 1;
-    if (inner) march3_tile<T, MODE, R, BATCH, true>(a, zt, b, smem_raw);
-    else march3_tile<T, MODE, R, BATCH, false>(a, zt, b, smem_raw);
+    const int l0 = (blockIdx.z - b * zt) * R;
+    if (tile_inner3(a.g.n, blockIdx.x, blockIdx.y, l0, R))
+        march3_tile<T, MODE, R, BATCH, true>(a, b, blockIdx.x, blockIdx.y, l0, smem_raw);
+    else
+        march3_tile<T, MODE, R, BATCH, false>(a, b, blockIdx.x, blockIdx.y, l0, smem_raw);
 }
 
 // Weights of the 3D boundary classes.  1D rows (Q1): stiffness (1/h)(-1, cnt, -1), mass
@@ -274,8 +308,8 @@ static cudaError_t go3(MArgs<T> a, cudaStream_t s) {
     const size_t smem = 2 * (size_t)kWarps3 * (R + 2) * 32 * sizeof(vec2<T>);
     static_assert(2 * kWarps3 * (R + 2) * 32 * sizeof(vec2<T>) <= 48 * 1024, "tile too large");
     const int zt = (a.g.nn + R - 1) / R;
-    dim3 grd((unsigned)((a.g.nn + 29) / 30), (unsigned)((a.g.nn + kWarps3 - 3) / (kWarps3 - 2)),
-             (unsigned)(zt * a.nb));
+    const int tx = (a.g.nn + 29) / 30, ty = (a.g.nn + kWarps3 - 3) / (kWarps3 - 2);
+    dim3 grd((unsigned)tx, (unsigned)ty, (unsigned)(zt * a.nb));
     if (a.pc) return klaunch(k_march3<T, MODE, R, true>, grd, dim3(32 * kWarps3), smem, s, 1, a, zt);
     if (a.nb != 1) return cudaErrorInvalidValue;
     return klaunch(k_march3<T, MODE, R, false>, grd, dim3(32 * kWarps3), smem, s, 1, a, zt);
