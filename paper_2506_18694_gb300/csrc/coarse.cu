@@ -25,20 +25,36 @@ struct SlabPlan {
     int per;        // slabs owned by each CTA (the last CTAs may own fewer or none)
     long long S;    // nodes per slab
     size_t smem;    // dynamic shared memory per CTA
+    int depth;      // 2D: sweeps between two exchanges of halo rows
 };
+
+// Nodes one CTA can own: the 2D kernel keeps 4 per thread, the 3D kernel 2.
+static long long cta_capacity(const GridDesc& g) {
+    return (long long)(g.dim == 2 ? kCoarseNodesPerThread2 : kCoarseNodesPerThread) * kCoarseThreads;
+}
+
+// 2D: sweeps per exchange, at most kCoarseDepth2.  A CTA computes the first sweep of a group of
+// d on its rows and d - 1 rows of each neighbour, the next on d - 2, ..., the last on its own
+// rows, so it stages d halo rows per side, all from the adjacent CTA (per >= d).
+constexpr int kCoarseDepth2 = 4;
 
 template <typename T>
 static SlabPlan slab_plan(const GridDesc& g, int cs) {
     SlabPlan sp;
     sp.per = (g.nn + cs - 1) / cs;
     sp.S = g.dim == 3 ? (long long)g.nn * g.nn : g.nn;
+    sp.depth = 1;
     if (g.dim == 3) {
         // two iterate buffers with a halo slab on each side
         sp.smem = (size_t)(2 * (sp.per + 2)) * sp.S * sizeof(vec2<T>);
     } else {
-        // three padded buffers (rows padded by a zero column on both sides) with two halo
-        // rows on each side
-        sp.smem = (size_t)(3 * (sp.per + 4)) * (sp.S + 2) * sizeof(vec2<T>);
+        // three padded buffers (rows padded by a zero column on both sides) with `depth` halo
+        // rows on each side; the deepest groups the slab's entries and shared memory allow
+        auto smem2 = [&](int d) { return (size_t)(3 * (sp.per + 2 * d)) * (sp.S + 2) * sizeof(vec2<T>); };
+        int d = std::min(kCoarseDepth2, sp.per);
+        while (d > 1 && ((sp.per + 2LL * (d - 1)) * sp.S > cta_capacity(g) || smem2(d) > kCoarseSmemMax)) --d;
+        sp.depth = std::max(d, 1);
+        sp.smem = smem2(sp.depth);
     }
     return sp;
 }
@@ -172,20 +188,20 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem(const __grid_co
     for (int q = threadIdx.x; q < own; q += blockDim.x) xout[(long long)r0 * S + q] = xs[cur][q + S];
 }
 
-// ---- 2D: padded slabs, boundary classes, two sweeps per cluster barrier ----
-// The 2D form keeps each slab row with a zero column on both sides and two halo rows above
+// ---- 2D: padded slabs, boundary classes, `depth` sweeps per cluster barrier ----
+// The 2D form keeps each slab row with a zero column on both sides and `depth` halo rows above
 // and below, so that every node reads its 8 neighbours unconditionally (Dirichlet nodes and
-// nodes outside the grid stay 0).  Sweeps run in pairs: a CTA computes the first sweep of
-// a pair on its own rows and on the nearest row of each neighbour (recomputed, so no
-// exchange is needed in between), then the second sweep on its own rows, and only then
-// writes its two top and two bottom rows into the neighbours' halo rows: one cluster
-// barrier per two sweeps.  The first sweep (from x = 0) is pointwise and needs no halo.
+// nodes outside the grid stay 0).  Sweeps run in groups of up to `depth`: a CTA computes the
+// first sweep of a group on its own rows and on depth - 1 rows of each neighbour (recomputed,
+// so no exchange is needed in between), each further sweep on one row less per side, the last
+// on its own rows, and only then writes its top and bottom `depth` rows into the neighbours'
+// halo rows: one cluster barrier per group.  The first sweep (from x = 0) is pointwise.
 // Inner nodes use the interior weights and side nodes the weights of their boundary class,
-// exactly as the 2D stencil kernels do, so the result equals nsweeps separate sweeps bit
-// for bit.  Slabs of one row (tiny grids) exchange after every sweep.
+// exactly as the 2D stencil kernels do, so the result equals nsweeps separate sweeps bit for
+// bit.  Slabs of one row (tiny grids) exchange after every sweep (depth 1).
 template <typename T>
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem2(const __grid_constant__ MArgs<T> a, int nsweeps,
-                                                                  int per) {
+                                                                  int per, int depth) {
     pdl_entry();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cl = cg::this_cluster();
@@ -199,85 +215,83 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem2(const __grid_c
     const int r0 = min(rank * per, nn);
     const int r1 = min(r0 + per, nn);
     const int rows = r1 - r0;
-    const bool paired = per >= 2;
-    const int buf = (per + 4) * W;  // one padded buffer: rows -2 .. per + 1 of the slab
+    const int H = depth - 1;                // neighbour rows recomputed on each side
+    const int buf = (per + 2 * depth) * W;  // one padded buffer: rows -depth .. per + depth - 1
     vec2<T>* xs[3];
     for (int q = 0; q < 3; ++q) xs[q] = reinterpret_cast<vec2<T>*>(smem_raw) + (long long)q * buf;
     for (int q = threadIdx.x; q < 3 * buf; q += blockDim.x) st<T>(xs[0], q, cx<T>(0, 0));
 
-    // entries: the slab's rows and, for pairs, the nearest row of each neighbour (rl = -1,
-    // rl = rows).  Per entry: padded index, kind (-1 none, 8 inner, 0..7 boundary class), b,
-    // whether it is an own node, and where its value goes in the neighbours' halo rows.
+    // entries: the slab's rows and H rows of each neighbour (rl = -H .. rows + H - 1).  Per
+    // entry: padded index, kind (-1 none, 8 inner, 0..7 boundary class), b, its distance from
+    // the slab (0: an own node), and where its value goes in the neighbours' halo rows.
     constexpr int K = kCoarseNodesPerThread2;
-    int pidx[K], kind[K], hm[K], hp[K];
-    bool mine[K];
+    int pidx[K], kind[K], dist[K], hm[K], hp[K];
     Cx<T> bq[K];
-    const int first = paired ? -1 : 0, last = paired ? rows : rows - 1;  // entry rows
-    const int ents = (last - first + 1) * nn;
+    const int ents = (rows + 2 * H) * nn;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const int e = threadIdx.x + k * blockDim.x;
         pidx[k] = 0;
         kind[k] = hm[k] = hp[k] = -1;
-        mine[k] = false;
+        dist[k] = depth;
         bq[k] = cx<T>(0, 0);
         if (e >= ents || rows <= 0) continue;
-        const int rl = first + e / nn, i = e % nn, j = r0 + rl;
+        const int rl = -H + e / nn, i = e % nn, j = r0 + rl;
         if (j < 0 || j >= nn) continue;
         const bool vd = (i == 0 && a.g.dir[0]) || (i == n && a.g.dir[1]) || (j == 0 && a.g.dir[2]) ||
                         (j == n && a.g.dir[3]);
         if (vd) continue;
-        pidx[k] = (rl + 2) * W + (i + 1);
+        pidx[k] = (rl + depth) * W + (i + 1);
         const int tx = i == 0 ? 0 : (i == n ? 2 : 1), ty = j == 0 ? 0 : (j == n ? 2 : 1);
         const int cls = ty * 3 + tx;
         kind[k] = cls == 4 ? 8 : cls - (cls > 4);
         bq[k] = ld<T>(b, (long long)j * nn + i);
-        mine[k] = rl >= 0 && rl < rows;
-        if (!mine[k]) continue;
-        // upper neighbour: its halo rows per + 2 (our row 0), per + 3 (our row 1)
-        if (rank > 0 && rl < (paired ? 2 : 1)) hm[k] = (per + 2 + rl) * W + (i + 1);
-        // lower neighbour: its halo rows 0 (our row rows - 2), 1 (our row rows - 1)
-        if (r1 < nn && rl >= rows - (paired ? 2 : 1)) hp[k] = (rl - rows + 2) * W + (i + 1);
+        dist[k] = rl < 0 ? -rl : (rl >= rows ? rl - rows + 1 : 0);
+        if (dist[k] > 0) continue;
+        // upper neighbour (per rows): our row rl < depth is its row per + rl
+        if (rank > 0 && rl < depth) hm[k] = (per + rl + depth) * W + (i + 1);
+        // lower neighbour: our row rl >= rows - depth is its row rl - rows
+        if (r1 < nn && rl >= rows - depth) hp[k] = (rl - rows + depth) * W + (i + 1);
     }
     cl.sync();  // every CTA's buffers are zero before any halo row arrives
     int in = 0;  // buffer holding the current iterate (own rows and valid halo rows)
     int s = 0;
     while (s < nsweeps) {
+        const int g = min(depth, nsweeps - s);  // sweeps in this group
         const int tmp = (in + 1) % 3, out = (in + 2) % 3;
-        const bool pair = paired && s + 1 < nsweeps;
-        // first sweep of the pair (or the single sweep): own rows, and the neighbours'
-        // nearest rows when paired
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            if (kind[k] < 0 || (!pair && !mine[k])) continue;
-            const Cx<T> xv = s == 0 ? cmul(kind[k] == 8 ? c.wdinv : c.bdinv[kind[k]], bq[k])
-                                    : coarse_update2(c, xs[in], pidx[k], W, kind[k], bq[k]);
-            st<T>(pair ? xs[tmp] : xs[out], pidx[k], xv);
-        }
-        if (pair) {
-            __syncthreads();
+        // sweep t reads src and writes dst on the entries within g - 1 - t rows of the slab:
+        // in -> tmp -> in -> ... -> out, so the buffer the neighbours write into (out) holds
+        // only the last sweep's own rows until their halo rows arrive
+        int src = in;
+        for (int t = 0; t < g; ++t) {
+            const int dst = t == g - 1 ? out : ((t & 1) ? in : tmp);
+            const int ext = g - 1 - t;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                if (kind[k] < 0 || !mine[k]) continue;
-                st<T>(xs[out], pidx[k], coarse_update2(c, xs[tmp], pidx[k], W, kind[k], bq[k]));
+                if (kind[k] < 0 || dist[k] > ext) continue;
+                const Cx<T> xv = s + t == 0 ? cmul(kind[k] == 8 ? c.wdinv : c.bdinv[kind[k]], bq[k])
+                                            : coarse_update2(c, xs[src], pidx[k], W, kind[k], bq[k]);
+                st<T>(xs[dst], pidx[k], xv);
             }
-            __syncthreads();
+            src = dst;
+            if (t + 1 < g) __syncthreads();
         }
+        __syncthreads();
         // own boundary rows of the new iterate into the neighbours' halo rows
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            if (kind[k] < 0 || !mine[k] || (hm[k] < 0 && hp[k] < 0)) continue;
+            if (kind[k] < 0 || dist[k] > 0 || (hm[k] < 0 && hp[k] < 0)) continue;
             const Cx<T> xv = ld<T>(xs[out], pidx[k]);
             if (hm[k] >= 0) st<T>(cl.map_shared_rank(xs[out], rank - 1), hm[k], xv);
             if (hp[k] >= 0) st<T>(cl.map_shared_rank(xs[out], rank + 1), hp[k], xv);
         }
         cl.sync();
         in = out;
-        s += pair ? 2 : 1;
+        s += g;
     }
     for (int q = threadIdx.x; q < rows * nn; q += blockDim.x) {
         const int rl = q / nn, i = q - rl * nn;
-        xout[(long long)(r0 + rl) * nn + i] = xs[in][(rl + 2) * W + (i + 1)];
+        xout[(long long)(r0 + rl) * nn + i] = xs[in][(rl + depth) * W + (i + 1)];
     }
 }
 
@@ -335,17 +349,12 @@ int coarse_cluster_size() {
     return 1;
 }
 
-// Nodes one CTA can own: the 2D kernel keeps 4 per thread, the 3D kernel 2.
-static long long cta_capacity(const GridDesc& g) {
-    return (long long)(g.dim == 2 ? kCoarseNodesPerThread2 : kCoarseNodesPerThread) * kCoarseThreads;
-}
-
 template <typename T>
 bool coarse_cluster_ok(const GridDesc& g, int cs) {
     if (cs < 1 || cs > coarse_cluster_size()) return false;
     const SlabPlan sp = slab_plan<T>(g, cs);
-    // 2D CTAs also hold the nearest row of each neighbour
-    const long long rows = g.dim == 2 ? sp.per + 2 : sp.per;
+    // 2D CTAs also hold depth - 1 rows of each neighbour
+    const long long rows = g.dim == 2 ? sp.per + 2LL * (sp.depth - 1) : sp.per;
     return sp.smem <= kCoarseSmemMax && rows * sp.S <= cta_capacity(g);
 }
 
@@ -402,7 +411,8 @@ cudaError_t launch_coarse_solve(const MArgs<T>& a, int nsweeps, cudaStream_t s) 
     if (!coarse_cluster_ok<T>(a.g, cs)) return cudaErrorInvalidValue;
     const SlabPlan sp = slab_plan<T>(a.g, cs);
     if (a.g.dim == 2)
-        return klaunch(k_coarse_dsmem2<T>, dim3(cs * a.nb), dim3(kCoarseThreads), sp.smem, s, cs, a, nsweeps, sp.per);
+        return klaunch(k_coarse_dsmem2<T>, dim3(cs * a.nb), dim3(kCoarseThreads), sp.smem, s, cs, a, nsweeps, sp.per,
+                       sp.depth);
     return klaunch(k_coarse_dsmem<T>, dim3(cs * a.nb), dim3(kCoarseThreads), sp.smem, s, cs, a, nsweeps, sp.per);
 }
 
