@@ -164,7 +164,8 @@ typedef struct {
                          /* residual; 0 (default): only max_outer ends it                       */
     int coarse_kernel;   /* the coarsest level's one-launch solve (see coarse_cluster_nodes): 0    */
                          /* (default) or 1: a thread-block cluster (level in distributed shared  */
-                         /* memory, halos exchanged between sweeps); 2 (2D only): bands of rows, */
+                         /* memory, halos exchanged after each group of sweeps: up to four in   */
+                         /* 2D, one in 3D); 2 (2D only): bands of rows,                          */
                          /* one CTA each, every sweep in shared memory with the halo rows         */
                          /* recomputed, no exchange between CTAs (what packs and the persistent  */
                          /* loop use).  Same result bit for bit                                  */
