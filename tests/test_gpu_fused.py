@@ -58,8 +58,9 @@ def test_fused_batch_equals_unfused(libhh):
                                             (256, 3, (D, S, S, D), 8), (128, 3, (S, S, D, S), 7),
                                             (64, 2, (S, D, S, S), 1), (256, 3, (S, S, S, S), 2)])
 def test_coarse_cluster_equals_separate_sweeps(libhh, prec, n, levels, bc, nc):
-    """The coarsest level solved in one launch, by the thread-block cluster (sweeps in pairs,
-    one-row slabs and odd counts included) or by bands of rows with recomputed halos, equals
+    """The coarsest level solved in one launch, by the thread-block cluster (sweeps in groups
+    of up to four with recomputed halo rows: one-row slabs, groups of three and partial groups
+    included) or by bands of rows with recomputed halos, equals
     the same sweeps run as separate kernels, bit for bit."""
     g = O.Grid(2, n, bc)
     r = torch.from_numpy(inputs.random_complex(g.N, 1500 + n) * g.free()).cuda()
