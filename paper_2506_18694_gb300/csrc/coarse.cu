@@ -208,7 +208,16 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem2(const __grid_c
     const int rank = (int)cl.block_rank();
     const int prob = blockIdx.x / (int)cl.num_blocks();
     if (problem_skipped(a, prob)) return;  // uniform over the cluster: no barrier is left waiting
-    const PCoef<T>& c = coef_of(a, prob);
+    // the coefficients in shared memory: read there at every update, they need neither the
+    // parameter space's nor global memory's latency, nor a reload after each remote store
+    __shared__ PCoef<T> cs;
+    {
+        const PCoef<T>& src = coef_of(a, prob);
+        const unsigned* w = reinterpret_cast<const unsigned*>(&src);
+        unsigned* d = reinterpret_cast<unsigned*>(&cs);
+        for (int q = threadIdx.x; q < (int)(sizeof(PCoef<T>) / sizeof(unsigned)); q += blockDim.x) d[q] = w[q];
+    }
+    const PCoef<T>& c = cs;
     const vec2<T>* __restrict__ b = a.z + (long long)prob * a.bs;
     vec2<T>* __restrict__ xout = a.y + (long long)prob * a.bs;
     const int nn = a.g.nn, n = a.g.n, W = nn + 2;
@@ -217,9 +226,9 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem2(const __grid_c
     const int rows = r1 - r0;
     const int H = depth - 1;                // neighbour rows recomputed on each side
     const int buf = (per + 2 * depth) * W;  // one padded buffer: rows -depth .. per + depth - 1
-    vec2<T>* xs[3];
-    for (int q = 0; q < 3; ++q) xs[q] = reinterpret_cast<vec2<T>*>(smem_raw) + (long long)q * buf;
-    for (int q = threadIdx.x; q < 3 * buf; q += blockDim.x) st<T>(xs[0], q, cx<T>(0, 0));
+    vec2<T>* const xs0 = reinterpret_cast<vec2<T>*>(smem_raw);
+    auto xs = [&](int q) { return xs0 + q * buf; };  // buffer q of 3
+    for (int q = threadIdx.x; q < 3 * buf; q += blockDim.x) st<T>(xs0, q, cx<T>(0, 0));
 
     // entries: the slab's rows and H rows of each neighbour (rl = -H .. rows + H - 1).  Per
     // entry: padded index, kind (-1 none, 8 inner, 0..7 boundary class), b, its distance from
@@ -270,8 +279,8 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem2(const __grid_c
             for (int k = 0; k < K; ++k) {
                 if (kind[k] < 0 || dist[k] > ext) continue;
                 const Cx<T> xv = s + t == 0 ? cmul(kind[k] == 8 ? c.wdinv : c.bdinv[kind[k]], bq[k])
-                                            : coarse_update2(c, xs[src], pidx[k], W, kind[k], bq[k]);
-                st<T>(xs[dst], pidx[k], xv);
+                                            : coarse_update2(c, xs(src), pidx[k], W, kind[k], bq[k]);
+                st<T>(xs(dst), pidx[k], xv);
             }
             src = dst;
             if (t + 1 < g) __syncthreads();
@@ -281,9 +290,9 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem2(const __grid_c
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             if (kind[k] < 0 || dist[k] > 0 || (hm[k] < 0 && hp[k] < 0)) continue;
-            const Cx<T> xv = ld<T>(xs[out], pidx[k]);
-            if (hm[k] >= 0) st<T>(cl.map_shared_rank(xs[out], rank - 1), hm[k], xv);
-            if (hp[k] >= 0) st<T>(cl.map_shared_rank(xs[out], rank + 1), hp[k], xv);
+            const Cx<T> xv = ld<T>(xs(out), pidx[k]);
+            if (hm[k] >= 0) st<T>(cl.map_shared_rank(xs(out), rank - 1), hm[k], xv);
+            if (hp[k] >= 0) st<T>(cl.map_shared_rank(xs(out), rank + 1), hp[k], xv);
         }
         cl.sync();
         in = out;
@@ -291,7 +300,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_dsmem2(const __grid_c
     }
     for (int q = threadIdx.x; q < rows * nn; q += blockDim.x) {
         const int rl = q / nn, i = q - rl * nn;
-        xout[(long long)(r0 + rl) * nn + i] = xs[in][(rl + depth) * W + (i + 1)];
+        xout[(long long)(r0 + rl) * nn + i] = xs(in)[(rl + depth) * W + (i + 1)];
     }
 }
 
