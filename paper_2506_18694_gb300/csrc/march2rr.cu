@@ -27,7 +27,11 @@ static cudaError_t gorr(MArgs<T> a, cudaStream_t s) {
     if (a.pc && !a.pc2) return cudaErrorInvalidValue;
     const int nnc = a.g.n / 2 + 1;
     const int strips = (a.g.nn + G1::S - 1) / G1::S;
-    int cr = ((long long)strips * ((nnc + 1) / 2) * a.nb >= 24LL * num_sms()) ? 2 : 1;
+    // two coarse rows per tile (fewer halo rows recomputed per output) once there are enough tiles
+    // to fill the SMs: 24 warps per SM, 16 for the HSS pass, whose first stage is the widest
+    // (measured on the 513^2 V-cycle: 43.27 us with two rows, 43.52 with one)
+    const long long want = (MODE == M_HSS_FIRST2_RR ? 16LL : 24LL) * num_sms();
+    int cr = ((long long)strips * ((nnc + 1) / 2) * a.nb >= want) ? 2 : 1;
     if (a.tile_rows == 1 || a.tile_rows == 2) cr = a.tile_rows;
     const int chunks = (nnc + cr - 1) / cr;
     const dim3 grd((unsigned)strips, (unsigned)((chunks + 3) / 4), (unsigned)a.nb);
